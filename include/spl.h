@@ -1,0 +1,250 @@
+/*
+ * spl.h -- C ABI of libspl.so: the x-ray transform of a volume expanded in
+ * tensor-product B-splines (SplineSplat, arXiv 2511.11078), its adjoint, the
+ * basis footprint (exact or learned), the learned-footprint MLP and the FP64
+ * reductions of least-squares reconstruction, all as hand-written CUDA
+ * kernels for sm_103a (GB300).
+ *
+ * Model (paper Sec. 1.2, Eq. 1-4):
+ *   f(x) = sum_{k in grid} c_k beta^n(x1-X1(k)) beta^n(x2-X2(k)) beta^n(x3-X3(k))
+ *   with X(k) = origin + k (unit lattice, Sec. 2.1) and beta^n the centred
+ *   B-spline of degree n (Sec. 2.2 uses n = 2; any n in 0..3 here).
+ *   A ray is the line {s + t w}, |w| = 1 (Eq. 1).  Its value is the line
+ *   integral of f (Eq. 2) = sum_k c_k Pphi(w, s - X(k)) (Eq. 4), where the
+ *   footprint Pphi(w, p) = int prod_d beta^n(p_d + t w_d) dt is the
+ *   "contribution" of basis k.  A (ray, basis) pair counts when the line
+ *   meets the open support cube of the basis in a segment of positive length.
+ *
+ * Common conventions
+ *   - Coefficients: float32, C-order c[z][y][x] (x fastest), nx*ny*nz values.
+ *   - Projections: float32, y[view][v][u] for view geometries, y[ray] for
+ *     explicit rays.
+ *   - "_dev" pointers are device pointers owned by the caller; the library
+ *     never frees them and never keeps them after the call returns.
+ *   - Every compute call is asynchronous on the CUDA stream `stream`
+ *     (a cudaStream_t, NULL for the legacy default stream).  Argument errors
+ *     are detected before any launch and returned synchronously; the call
+ *     then launches nothing.
+ *   - spl_forward, spl_adjoint, spl_footprint, spl_dot_f64 and the CG updates
+ *     allocate no memory.  Objects (geometry, MLP) own the device memory they
+ *     allocate at creation and free it on destroy.
+ *   - Errors are returned as spl_status values; the library never aborts.
+ *     spl_last_error() gives a message for the last failing call of the
+ *     calling thread.
+ *   - Kernels never spin on a condition another agent sets; every loop has a
+ *     fixed bound.  A kernel that reaches a bound sets the error flag of the
+ *     geometry it ran on; spl_geometry_status() reads and clears it.
+ */
+#ifndef SPL_H
+#define SPL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPL_OK = 0,
+    SPL_ERR_ARG = 1,         /* null pointer, bad size, bad degree or mode      */
+    SPL_ERR_NONFINITE = 2,   /* non-finite or zero-length direction or position */
+    SPL_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
+    SPL_ERR_STEPCAP = 4,     /* a kernel reached one of its loop bounds         */
+    SPL_ERR_OOM = 5,         /* device allocation failed (object creation only) */
+    SPL_ERR_STATE = 6,       /* object in the wrong state for this call         */
+    SPL_ERR_UNSUPPORTED = 7  /* size or option outside what the kernels handle  */
+} spl_status;
+
+/* geometry kinds (Eq. 1 lines) */
+enum { SPL_RAYS = 0, SPL_PARALLEL = 1, SPL_CONE = 2 };
+/* footprint evaluators: exact quadrature, or the learned f_theta (Sec. 2.2) */
+enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1 };
+
+typedef struct spl_geometry spl_geometry; /* opaque, library-owned */
+typedef struct spl_mlp spl_mlp;           /* opaque, library-owned */
+
+/* Description of a set of lines (Eq. 1) and of the coefficient grid.
+ *   kind SPL_RAYS:     n_rays lines; ray_omega [n_rays][3] (any nonzero
+ *                      length, normalised by the library), ray_s [n_rays][3].
+ *   kind SPL_PARALLEL: n_views views of nu x nv pixels; view_src [n_views][3]
+ *                      is the ray direction of the view.
+ *   kind SPL_CONE:     view_src [n_views][3] is the source position.
+ *   For both view kinds pixel (iu, iv) of view k has centre
+ *     q = det_center[k] + (iu - (nu-1)/2) det_u[k] + (iv - (nv-1)/2) det_v[k]
+ *   (det_u and det_v carry the pixel pitch); the ray is q + t*dir (parallel)
+ *   or the line through the source and q (cone); ray index
+ *   r = (k*nv + iv)*nu + iu.  All arrays are host FP64, read during the call
+ *   and copied to the device; the caller keeps ownership.
+ *   Grid: coefficient (i, j, l) sits at origin + (i, j, l), lattice step 1. */
+typedef struct {
+    int kind;
+    int nx, ny, nz;
+    double origin[3];
+    long long n_rays;
+    const double *ray_omega;
+    const double *ray_s;
+    int n_views;
+    const double *view_src;
+    const double *det_center;
+    const double *det_u;
+    const double *det_v;
+    int nu, nv;
+} spl_geometry_desc;
+
+/* Basis and footprint choice.
+ *   degree: n in 0..3 (B-spline degree of the tensor-product basis).
+ *   mode:   SPL_FP_QUAD (exact piecewise Gauss-Legendre footprint) or
+ *           SPL_FP_MLP (learned footprint f_theta, Algorithm 2's f_theta*);
+ *           SPL_FP_MLP needs `mlp` built for the same degree.
+ *   kahan:  nonzero = compensated (Kahan) FP32 sum of the slab partials along
+ *           each ray; zero = plain FP32 sum. */
+typedef struct {
+    int degree;
+    int mode;
+    const spl_mlp *mlp;
+    int kahan;
+} spl_basis_desc;
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Build a device-resident geometry (Eq. 1) from `desc`.  Validates every
+ * direction and position (finite, nonzero direction) and the grid
+ * (1 <= n <= 2048 per axis, nx*ny*nz < 2^31).  Allocates device memory owned
+ * by the returned object.  Uses the current CUDA device.
+ * Errors: SPL_ERR_ARG, SPL_ERR_NONFINITE, SPL_ERR_UNSUPPORTED, SPL_ERR_OOM,
+ * SPL_ERR_CUDA; *out is NULL on error. */
+spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geometry **out);
+
+/* Free a geometry (NULL is ignored).  No call using it may be in flight. */
+void spl_destroy_geometry(spl_geometry *g);
+
+/* Number of rays (= length of y) and of coefficients (= length of c). */
+long long spl_geometry_rays(const spl_geometry *g);
+long long spl_geometry_coeffs(const spl_geometry *g);
+
+/* Synchronise `stream`, then read and clear the geometry's device error flag.
+ * Returns SPL_ERR_STEPCAP if a kernel that ran on `g` reached a loop bound
+ * since the last call, SPL_ERR_CUDA on a CUDA error, else SPL_OK. */
+spl_status spl_geometry_status(const spl_geometry *g, void *stream);
+
+/* ---------------------------------------------------------------- operators */
+
+/* Forward projection y = A c (Algorithm 2; Eq. 4 summed over all pairs).
+ * One GPU thread per ray marches the slabs of the ray's dominant axis
+ * (Definition 2.1); in each slab it visits the bases whose support the ray
+ * crosses (Algorithm 3's neighbourhood, de-duplicated by construction) and
+ * accumulates c_k * Pphi(w, s - X(k)).
+ *   c_dev: [nz][ny][nx] float32 (read only);  y_dev: n_rays float32,
+ *   overwritten.  Errors: SPL_ERR_ARG (null pointer, degree, mode, missing or
+ *   mismatched MLP), SPL_ERR_CUDA (launch failure). */
+spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *basis, const float *c_dev, float *y_dev,
+                       void *stream);
+
+/* Adjoint (back-projection) c = A^T y: the transpose of the matrix of Eq. 6,
+ * matched exactly to spl_forward (Sec. 2.3): it visits the same
+ * (ray, basis) pairs and evaluates bit-identical footprint values.  View
+ * geometries use a gather form (one thread block per coefficient brick,
+ * looping over views and the detector window of the brick; no global
+ * atomics); explicit rays use a ray-driven scatter with float atomics.
+ *   y_dev: n_rays float32 (read only);  c_dev: [nz][ny][nx] float32,
+ *   overwritten.  Errors as spl_forward. */
+spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *basis, const float *y_dev, float *c_dev,
+                       void *stream);
+
+/* Number of (ray, basis) pairs with a nonzero footprint (the
+ * "contributions" of Eq. 4), added to *count_dev (uint64, device). */
+spl_status spl_count_pairs(const spl_geometry *g, int degree, unsigned long long *count_dev, void *stream);
+
+/* Footprint Pphi(w, p) (Eq. 4's contribution) of the basis at the origin for
+ * `count` (direction, offset) pairs.
+ *   omega_dev [count][3] float32 unit directions, p_dev [count][3] float32
+ *   offsets (only the component in H_w matters), out_dev [count] float32.
+ *   SPL_FP_QUAD: exact knot-split Gauss-Legendre; SPL_FP_MLP: f_theta on the
+ *   canonical features, multiplied by the exact support indicator. */
+spl_status spl_footprint(const spl_basis_desc *basis, long long count, const float *omega_dev, const float *p_dev,
+                         float *out_dev, void *stream);
+
+/* MLP input features of (w, p) (float32 [count][5]): the signed permutation
+ * G that maps w into the chamber 0 <= w1 <= w2 <= w3 (phi is invariant under
+ * it), the frame u = normalize(e1 x Gw), v = u x Gw (Algorithm 2 fixes only
+ * u perpendicular to w and v = u x w), and
+ * (Gw1, Gw2, Gw3, <Gp,u>/(sqrt(3) W), <Gp,v>/(sqrt(3) W)), W = (n+1)/2. */
+spl_status spl_features(int degree, long long count, const float *omega_dev, const float *p_dev, float *feat_dev,
+                        void *stream);
+
+/* ---------------------------------------------------------------- learned footprint (Sec. 2.2, Algorithm 1) */
+
+/* The network is fixed: 5 -> 64 -> 64 -> 64 -> 1, SiLU after the three
+ * hidden layers.  Parameters (float32 master copy) are laid out per layer as
+ * W [out][in] row-major followed by b [out]; SPL_MLP_PARAMS values in all.
+ * Evaluation precision: BF16 weights (rounded from the master copy), BF16
+ * hidden activations into the two 64x64 tensor-core layers, FP32
+ * accumulation, FP32 first and last layers. */
+#define SPL_MLP_PARAMS 8769
+
+/* Create an MLP for B-splines of `degree`, parameters initialised with a
+ * seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) draw; allocates device
+ * memory (weights, Adam state, and training scratch for batches of up to
+ * `max_batch` samples).  Errors: SPL_ERR_ARG, SPL_ERR_OOM, SPL_ERR_CUDA. */
+spl_status spl_mlp_create(int degree, int max_batch, unsigned long long seed, spl_mlp **out);
+void spl_mlp_destroy(spl_mlp *m);
+int spl_mlp_degree(const spl_mlp *m);
+
+/* Copy SPL_MLP_PARAMS float32 master parameters from / to the host
+ * (synchronous).  Setting also refreshes the BF16 copies and resets Adam. */
+spl_status spl_mlp_set_params(spl_mlp *m, const float *host_params);
+spl_status spl_mlp_get_params(const spl_mlp *m, float *host_params);
+
+/* f_theta on `count` feature rows (float32 [count][5]) -> out_dev [count],
+ * with the BF16 tensor-core inference kernel. */
+spl_status spl_mlp_eval(const spl_mlp *m, long long count, const float *feat_dev, float *out_dev, void *stream);
+
+/* Gradient of L = (1/B) sum_b (f_theta(x_b) - y_b)^2 (Algorithm 1's loss)
+ * with respect to the master parameters, float32 [SPL_MLP_PARAMS] into
+ * grad_dev; the loss into loss_dev (float32 [1]).  B <= max_batch. */
+spl_status spl_mlp_grad(spl_mlp *m, int batch, const float *feat_dev, const float *target_dev, float *grad_dev,
+                        float *loss_dev, void *stream);
+
+/* One Adam step (Algorithm 1's update) on a batch: gradient as
+ * spl_mlp_grad, then Adam with learning rate `lr` (beta1 0.9, beta2 0.999,
+ * eps 1e-8) on the FP32 master weights, then the BF16 copies refresh.
+ * loss_dev (nullable) receives the batch loss. */
+spl_status spl_mlp_train_step(spl_mlp *m, int batch, const float *feat_dev, const float *target_dev, float lr,
+                              float *loss_dev, void *stream);
+
+/* ---------------------------------------------------------------- FP64 reductions (Eq. 5 least squares) */
+
+/* out_dev[0] = sum_i a_i b_i accumulated in FP64 (float32 inputs, n >= 0),
+ * deterministic: a fixed grid of blocks writes one FP64 partial each into
+ * the caller's workspace `work_dev` (at least spl_dot_f64_workspace_bytes()
+ * bytes, device memory owned by the caller), then one block adds the
+ * partials in index order.  Calls that share a workspace must not overlap.
+ * Errors: SPL_ERR_ARG (NULL pointer, short workspace), SPL_ERR_CUDA. */
+long long spl_dot_f64_workspace_bytes(void);
+spl_status spl_dot_f64(long long n, const float *a_dev, const float *b_dev, double *out_dev, void *work_dev,
+                       long long work_bytes, void *stream);
+
+/* CGLS updates with FP64 scalars read from device memory (no host sync):
+ *   spl_cg_step_x:  x += alpha p;  r -= alpha q;   alpha = num[0] / den[0]
+ *   spl_cg_step_p:  p = s + beta p;                beta  = num[0] / den[0]
+ * (num, den: FP64 device scalars; den == 0 leaves the vectors unchanged). */
+spl_status spl_cg_step_x(long long nx, float *x_dev, const float *p_dev, long long nr, float *r_dev,
+                         const float *q_dev, const double *num_dev, const double *den_dev, void *stream);
+spl_status spl_cg_step_p(long long n, float *p_dev, const float *s_dev, const double *num_dev,
+                         const double *den_dev, void *stream);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *spl_last_error(void);
+/* Fault injection for tests: lower the loop bound of the per-slab sweep to
+ * `cap` (1..40; any other value restores the default 40).  With a bound that
+ * is too small the kernels stop early, set the geometry's error flag, and
+ * spl_geometry_status() reports SPL_ERR_STEPCAP.  Affects launches issued
+ * after the call, process-wide.  Returns the previous bound. */
+int spl_debug_set_iter_cap(int cap);
+/* Library version string. */
+const char *spl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPL_H */

@@ -1,0 +1,133 @@
+// footprint.cu -- batched footprint Pphi(w, p) (Eq. 4's contribution) and
+// the MLP input features.
+//
+// Exact mode: the basis at the origin is a 1x1x1 grid; the ray {p + t w} is
+// set up and swept with the same slab engine as the projector, and the value
+// of the single basis is kept.  MLP mode: f_theta on the canonical features,
+// times the exact support indicator (the same pair test as the projector).
+#include "spl_host.h"
+#include "spl_mlp.cuh"
+
+namespace spl {
+
+struct PointSink {
+    float v;
+    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    {
+        return a0 <= 0 && a1 >= 0 && b0 <= 0 && b1 >= 0;
+    }
+    __device__ __forceinline__ void flush(int, int la, int lb, float val)
+    {
+        if (la == 0 && lb == 0) v = val;
+    }
+};
+
+__device__ __forceinline__ GridBox unit_box()
+{
+    GridBox gb;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        gb.n[e] = 1;
+        gb.org[e] = 0.0;
+        gb.stride[e] = 1;
+    }
+    return gb;
+}
+
+template <int N>
+__device__ __forceinline__ float footprint_exact(const double (&w)[3], const double (&p)[3], const QuadRule &qr)
+{
+    RaySetup rs;
+    if (!ray_setup<N>(unit_box(), p, w, rs)) return 0.0f;
+    PointSink sk{0.0f};
+#pragma unroll 1
+    for (int j = rs.j0; j <= rs.j1; ++j) slab_sweep<N>(rs, j, qr, sk);
+    return sk.v * rs.inv_wd;
+}
+
+template <int N>
+__global__ void k_footprint_quad(long long count, const float *__restrict__ omega, const float *__restrict__ p,
+                                 float *__restrict__ out, QuadRule qr)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double w[3], q[3];
+    double nrm = 0.0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        w[e] = omega[3 * i + e];
+        q[e] = p[3 * i + e];
+        nrm += w[e] * w[e];
+    }
+    nrm = sqrt(nrm);
+    if (!(nrm > 0.0)) {
+        out[i] = 0.0f;
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) w[e] /= nrm;
+    out[i] = footprint_exact<N>(w, q, qr);
+}
+
+__global__ void k_features(int degree, long long count, const float *__restrict__ omega, const float *__restrict__ p,
+                           float *__restrict__ feat)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double w[3], q[3], f[5];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        w[e] = omega[3 * i + e];
+        q[e] = p[3 * i + e];
+    }
+    canonical_features(degree, w, q, f);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) feat[5 * i + e] = (float)f[e];
+}
+
+}  // namespace spl
+
+using namespace spl;
+
+template <int N>
+static spl_status footprint_quad(long long count, const float *w, const float *p, float *out, cudaStream_t st)
+{
+    const long long blocks = (count + 127) / 128;
+    k_footprint_quad<N><<<(unsigned)blocks, 128, 0, st>>>(count, w, p, out, quad_rule(N));
+    return cuda_check(cudaGetLastError(), "footprint launch");
+}
+
+extern "C" spl_status spl_footprint(const spl_basis_desc *b, long long count, const float *omega_dev,
+                                    const float *p_dev, float *out_dev, void *stream)
+{
+    clear_error();
+    spl_status s = check_basis(b);
+    if (s != SPL_OK) return s;
+    if (count < 0 || count > (1LL << 40)) return fail(SPL_ERR_ARG, "bad count %lld", count);
+    if (count == 0) return SPL_OK;
+    if (!omega_dev || !p_dev || !out_dev) return fail(SPL_ERR_ARG, "NULL array");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->mode == SPL_FP_MLP) {
+        if (spl_mlp_degree(b->mlp) != b->degree) return fail(SPL_ERR_ARG, "MLP degree does not match basis degree");
+        return spl::footprint_mlp(b, count, omega_dev, p_dev, out_dev, st);
+    }
+    switch (b->degree) {
+    case 0: return footprint_quad<0>(count, omega_dev, p_dev, out_dev, st);
+    case 1: return footprint_quad<1>(count, omega_dev, p_dev, out_dev, st);
+    case 2: return footprint_quad<2>(count, omega_dev, p_dev, out_dev, st);
+    default: return footprint_quad<3>(count, omega_dev, p_dev, out_dev, st);
+    }
+}
+
+extern "C" spl_status spl_features(int degree, long long count, const float *omega_dev, const float *p_dev,
+                                   float *feat_dev, void *stream)
+{
+    clear_error();
+    if (degree < 0 || degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", degree);
+    if (count < 0) return fail(SPL_ERR_ARG, "bad count");
+    if (count == 0) return SPL_OK;
+    if (!omega_dev || !p_dev || !feat_dev) return fail(SPL_ERR_ARG, "NULL array");
+    const long long blocks = (count + 127) / 128;
+    k_features<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(degree, count, omega_dev, p_dev, feat_dev);
+    return cuda_check(cudaGetLastError(), "features launch");
+}

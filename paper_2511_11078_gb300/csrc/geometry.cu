@@ -1,0 +1,299 @@
+// geometry.cu -- geometry objects (Eq. 1 lines on the device), error
+// reporting and the Gauss-Legendre rule of libspl.so.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "spl_host.h"
+
+namespace spl {
+
+static thread_local char g_last_error[512] = "";
+
+spl_status fail(spl_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+void clear_error() { g_last_error[0] = '\0'; }
+
+spl_status cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return SPL_OK;
+    return fail(SPL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------- quadrature
+// Roots of the Legendre polynomial P_m by Newton's method from Tricomi's
+// asymptotic initial guess, in long double; weights 2/((1-x^2) P_m'(x)^2).
+static void legendre_rule(int m, double *x, double *w)
+{
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < m; ++i) {
+        const long double th = pi * (4.0L * (i + 1) - 1.0L) / (4.0L * m + 2.0L);
+        long double z = (1.0L - (m - 1.0L) / (8.0L * m * m * m)) * cosl(th);
+        long double dp = 1.0L;
+        for (int it = 0; it < 64; ++it) {
+            long double pk = z, pkm1 = 1.0L;  // P_1, P_0
+            for (int k = 1; k < m; ++k) {
+                const long double pk1 = ((2.0L * k + 1.0L) * z * pk - k * pkm1) / (k + 1.0L);
+                pkm1 = pk;
+                pk = pk1;
+            }
+            if (m == 1) { pk = z; pkm1 = 1.0L; }
+            dp = m * (pkm1 - z * pk) / (1.0L - z * z);
+            const long double step = pk / dp;
+            z -= step;
+            if (fabsl(step) < 1e-19L) break;
+        }
+        x[i] = (double)z;
+        w[i] = (double)(2.0L / ((1.0L - z * z) * dp * dp));
+    }
+}
+
+static QuadRule g_rules[4];
+static int g_iter_cap = kSlabIterCap;
+static std::once_flag g_rules_once;
+
+static void init_rules()
+{
+    for (int n = 0; n < 4; ++n) {
+        const int m = (3 * n + 2) / 2 > 0 ? (3 * n + 2) / 2 : 1;
+        double x[kMaxNodes], w[kMaxNodes];
+        legendre_rule(m, x, w);
+        for (int q = 0; q < kMaxNodes; ++q) {
+            g_rules[n].x[q] = q < m ? (float)x[q] : 0.0f;
+            g_rules[n].w[q] = q < m ? (float)w[q] : 0.0f;
+        }
+    }
+}
+
+QuadRule quad_rule(int degree)
+{
+    std::call_once(g_rules_once, init_rules);
+    QuadRule q = g_rules[degree];
+    q.cap = g_iter_cap;
+    return q;
+}
+
+int set_iter_cap(int cap)
+{
+    const int old = g_iter_cap;
+    g_iter_cap = (cap < 1 || cap > kSlabIterCap) ? kSlabIterCap : cap;
+    return old;
+}
+
+int quad_nodes(int degree) { return (3 * degree + 2) / 2 > 0 ? (3 * degree + 2) / 2 : 1; }
+
+spl_status check_basis(const spl_basis_desc *b)
+{
+    if (!b) return fail(SPL_ERR_ARG, "basis descriptor is NULL");
+    if (b->degree < 0 || b->degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", b->degree);
+    if (b->mode != SPL_FP_QUAD && b->mode != SPL_FP_MLP) return fail(SPL_ERR_ARG, "unknown footprint mode %d", b->mode);
+    if (b->mode == SPL_FP_MLP && !b->mlp) return fail(SPL_ERR_ARG, "SPL_FP_MLP needs an MLP");
+    return SPL_OK;
+}
+
+}  // namespace spl
+
+using namespace spl;
+
+static bool finite3(const double *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geometry **out)
+{
+    clear_error();
+    if (!out) return fail(SPL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(SPL_ERR_ARG, "desc is NULL");
+    const spl_geometry_desc &d = *desc;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1 || d.nx > 2048 || d.ny > 2048 || d.nz > 2048)
+        return fail(SPL_ERR_UNSUPPORTED, "grid %d x %d x %d outside 1..2048 per axis", d.nx, d.ny, d.nz);
+    if ((long long)d.nx * d.ny * d.nz >= (1LL << 31)) return fail(SPL_ERR_UNSUPPORTED, "grid has 2^31 or more coefficients");
+    if (!finite3(d.origin)) return fail(SPL_ERR_NONFINITE, "origin is not finite");
+
+    spl_geometry *g = (spl_geometry *)calloc(1, sizeof(spl_geometry));
+    if (!g) return fail(SPL_ERR_OOM, "host allocation failed");
+    g->desc = d;
+    g->desc.ray_omega = g->desc.ray_s = nullptr;
+    g->desc.view_src = g->desc.det_center = g->desc.det_u = g->desc.det_v = nullptr;
+    DevGeom &dg = g->dev;
+    dg.kind = d.kind;
+    dg.n[0] = d.nx;
+    dg.n[1] = d.ny;
+    dg.n[2] = d.nz;
+    for (int e = 0; e < 3; ++e) dg.org[e] = d.origin[e];
+    size_t payload = 0;
+    double *ray_host = nullptr;
+
+    if (d.kind == SPL_RAYS) {
+        if (d.n_rays < 0 || (d.n_rays > 0 && (!d.ray_omega || !d.ray_s))) {
+            free(g);
+            return fail(SPL_ERR_ARG, "rays: bad count or NULL arrays");
+        }
+        dg.n_rays = d.n_rays;
+        payload = (size_t)d.n_rays * 6 * sizeof(double);
+        ray_host = (double *)malloc(payload > 0 ? payload : 1);
+        if (!ray_host) { free(g); return fail(SPL_ERR_OOM, "host allocation failed"); }
+        for (long long r = 0; r < d.n_rays; ++r) {
+            const double *w = d.ray_omega + 3 * r, *s = d.ray_s + 3 * r;
+            if (!finite3(w) || !finite3(s)) { free(ray_host); free(g); return fail(SPL_ERR_NONFINITE, "ray %lld is not finite", r); }
+            const double nrm = sqrt(dot3(w, w));
+            if (!(nrm > 0.0) || !isfinite(nrm)) { free(ray_host); free(g); return fail(SPL_ERR_NONFINITE, "ray %lld has a zero direction", r); }
+            for (int e = 0; e < 3; ++e) {
+                ray_host[3 * r + e] = w[e] / nrm;                 // directions first
+                ray_host[3 * d.n_rays + 3 * r + e] = s[e];        // then points
+            }
+        }
+    } else if (d.kind == SPL_PARALLEL || d.kind == SPL_CONE) {
+        if (d.n_views < 0 || d.n_views > 65535 || d.nu < 1 || d.nv < 1 || d.nu > 65535 || d.nv > 65535 ||
+            (d.n_views > 0 && (!d.view_src || !d.det_center || !d.det_u || !d.det_v))) {
+            free(g);
+            return fail(SPL_ERR_ARG, "views: bad counts (views <= 65535, pixels >= 1) or NULL arrays");
+        }
+        dg.n_views = d.n_views;
+        dg.nu = d.nu;
+        dg.nv = d.nv;
+        dg.n_rays = (long long)d.n_views * d.nu * d.nv;
+        g->views_host = (ViewPose *)calloc(d.n_views > 0 ? d.n_views : 1, sizeof(ViewPose));
+        if (!g->views_host) { free(g); return fail(SPL_ERR_OOM, "host allocation failed"); }
+        for (int k = 0; k < d.n_views; ++k) {
+            ViewPose &P = g->views_host[k];
+            const double *src = d.view_src + 3 * k;
+            for (int e = 0; e < 3; ++e) {
+                P.src[e] = src[e];
+                P.dc[e] = d.det_center[3 * k + e];
+                P.du[e] = d.det_u[3 * k + e];
+                P.dv[e] = d.det_v[3 * k + e];
+            }
+            if (!finite3(P.src) || !finite3(P.dc) || !finite3(P.du) || !finite3(P.dv)) {
+                free(g->views_host); free(g);
+                return fail(SPL_ERR_NONFINITE, "view %d is not finite", k);
+            }
+            double n[3];
+            cross3(P.du, P.dv, n);
+            const double nn = sqrt(dot3(n, n));
+            if (!(nn > 0.0)) { free(g->views_host); free(g); return fail(SPL_ERR_NONFINITE, "view %d: detector axes are parallel", k); }
+            for (int e = 0; e < 3; ++e) P.nrm[e] = n[e] / nn;
+            // dual axes of (du, dv) in the detector plane: ud = (dv x n)/det, vd = (n x du)/det
+            double t1[3], t2[3];
+            cross3(P.dv, P.nrm, t1);
+            cross3(P.nrm, P.du, t2);
+            const double det = dot3(P.du, t1);
+            for (int e = 0; e < 3; ++e) {
+                P.ud[e] = t1[e] / det;
+                P.vd[e] = t2[e] / det;
+            }
+            if (d.kind == SPL_PARALLEL) {
+                const double l = sqrt(dot3(P.src, P.src));
+                if (!(l > 0.0)) { free(g->views_host); free(g); return fail(SPL_ERR_NONFINITE, "view %d: zero direction", k); }
+                for (int e = 0; e < 3; ++e) P.src[e] /= l;
+                if (fabs(dot3(P.src, P.nrm)) < 1e-12) {
+                    free(g->views_host); free(g);
+                    return fail(SPL_ERR_ARG, "view %d: ray direction lies in the detector plane", k);
+                }
+            } else {
+                // every pixel must be at a positive distance from the source
+                double rel[3];
+                for (int e = 0; e < 3; ++e) rel[e] = P.dc[e] - P.src[e];
+                if (!(fabs(dot3(rel, P.nrm)) > 0.0)) {
+                    free(g->views_host); free(g);
+                    return fail(SPL_ERR_ARG, "view %d: source lies in the detector plane", k);
+                }
+            }
+        }
+        payload = (size_t)d.n_views * sizeof(ViewPose);
+    } else {
+        free(g);
+        return fail(SPL_ERR_ARG, "unknown geometry kind %d", d.kind);
+    }
+
+    cudaGetDevice(&g->device);
+    const size_t flag_off = (payload + 255) & ~(size_t)255;
+    void *blk = nullptr;
+    cudaError_t ce = cudaMalloc(&blk, flag_off + 256);
+    if (ce != cudaSuccess) {
+        free(ray_host);
+        free(g->views_host);
+        free(g);
+        cudaGetLastError();
+        return fail(SPL_ERR_OOM, "cudaMalloc(%zu) failed: %s", flag_off + 256, cudaGetErrorString(ce));
+    }
+    g->dev_block = blk;
+    const void *src = d.kind == SPL_RAYS ? (const void *)ray_host : (const void *)g->views_host;
+    if (payload > 0) ce = cudaMemcpy(blk, src, payload, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset((char *)blk + flag_off, 0, 256);
+    free(ray_host);
+    if (ce != cudaSuccess) {
+        cudaFree(blk);
+        free(g->views_host);
+        free(g);
+        return cuda_check(ce, "geometry upload");
+    }
+    if (d.kind == SPL_RAYS) {
+        dg.ray_w = (const double *)blk;
+        dg.ray_s = (const double *)blk + 3 * d.n_rays;
+    } else {
+        dg.views = (const ViewPose *)blk;
+    }
+    dg.err = (int *)((char *)blk + flag_off);
+    *out = g;
+    return SPL_OK;
+}
+
+extern "C" void spl_destroy_geometry(spl_geometry *g)
+{
+    if (!g) return;
+    if (g->dev_block) cudaFree(g->dev_block);
+    free(g->views_host);
+    free(g);
+}
+
+extern "C" long long spl_geometry_rays(const spl_geometry *g) { return g ? g->dev.n_rays : -1; }
+
+extern "C" long long spl_geometry_coeffs(const spl_geometry *g)
+{
+    return g ? (long long)g->dev.n[0] * g->dev.n[1] * g->dev.n[2] : -1;
+}
+
+extern "C" spl_status spl_geometry_status(const spl_geometry *g, void *stream)
+{
+    clear_error();
+    if (!g) return fail(SPL_ERR_ARG, "geometry is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int flag = 0;
+    spl_status s = cuda_check(cudaMemcpyAsync(&flag, g->dev.err, sizeof(int), cudaMemcpyDeviceToHost, st), "status read");
+    if (s != SPL_OK) return s;
+    s = cuda_check(cudaStreamSynchronize(st), "status sync");
+    if (s != SPL_OK) return s;
+    if (flag) {
+        s = cuda_check(cudaMemsetAsync(g->dev.err, 0, sizeof(int), st), "status clear");
+        if (s != SPL_OK) return s;
+        cudaStreamSynchronize(st);
+        return fail(SPL_ERR_STEPCAP, "a kernel reached a loop bound (flag 0x%x)", flag);
+    }
+    return SPL_OK;
+}
+
+extern "C" const char *spl_last_error(void) { return spl::g_last_error; }
+
+extern "C" int spl_debug_set_iter_cap(int cap) { return spl::set_iter_cap(cap); }
+
+extern "C" const char *spl_version(void) { return "libspl 0.1 (sm_103a)"; }

@@ -1,0 +1,464 @@
+// project.cu -- forward projection A (Algorithm 2, Eq. 4) and its matched
+// adjoint A^T (Sec. 2.3: the adjoint is matched exactly to the forward),
+// exact quadrature footprint.
+//
+// Forward: one thread per ray; the 128 threads of a block cover a 16 x 8
+// detector tile of one view (a warp is an 8 x 4 sub-tile), so neighbouring
+// lanes walk neighbouring lines and gather neighbouring coefficients (L1
+// hits).  The slab partial sums are added along the ray with Kahan
+// compensation.
+//
+// Adjoint (view geometries): gather form, one block per 16^3 coefficient
+// brick.  For every view the block projects the brick's support box onto the
+// detector, walks the rays of that pixel window through the brick's slabs
+// with the same set-up and slab sweep as the forward (identical pairs and
+// footprint values), and accumulates y_r * P into shared memory; after each
+// view the per-view partials are folded into FP64 totals.  No global
+// atomics; each coefficient is written once.
+// Adjoint (explicit rays): no view structure to gather over, so a
+// ray-driven scatter with float atomics into a zeroed output.
+#include <stdio.h>
+
+#include "spl_host.h"
+#include "spl_mlp.cuh"
+
+namespace spl {
+
+// ---------------------------------------------------------------- sinks
+struct FwdSink {
+    const float *__restrict__ c;
+    int S0, S1, S2;
+    int loa, hia, lob, hib;
+    float acc;
+    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    {
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+    }
+    __device__ __forceinline__ void flush(int j, int la, int lb, float v)
+    {
+        if (la >= loa && la <= hia && lb >= lob && lb <= hib) acc = fmaf(__ldg(c + (j * S0 + la * S1 + lb * S2)), v, acc);
+    }
+};
+
+struct CountSink {
+    int loa, hia, lob, hib;
+    unsigned int n;
+    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    {
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+    }
+    __device__ __forceinline__ void flush(int, int la, int lb, float v)
+    {
+        n += (la >= loa && la <= hia && lb >= lob && lb <= hib && v > 0.0f) ? 1u : 0u;
+    }
+};
+
+struct AtomicSink {
+    float *__restrict__ c;
+    int S0, S1, S2;
+    int loa, hia, lob, hib;
+    float yv;
+    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    {
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+    }
+    __device__ __forceinline__ void flush(int j, int la, int lb, float v)
+    {
+        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(c + (j * S0 + la * S1 + lb * S2), yv * v);
+    }
+};
+
+// brick of the gather adjoint: bounds in mirrored (d, a, b) coordinates and
+// the mirrored strides of the shared-memory brick array
+struct BrickSink {
+    float *part;
+    int L0, L1, L2, Loff;
+    int loa, hia, lob, hib;
+    float yv;
+    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    {
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+    }
+    __device__ __forceinline__ void flush(int j, int la, int lb, float v)
+    {
+        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(part + (j * L0 + la * L1 + lb * L2 + Loff), yv * v);
+    }
+};
+
+// ---------------------------------------------------------------- forward
+__device__ __forceinline__ void tile_pixel(int &iu, int &iv)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    iu = blockIdx.x * 16 + (wid & 1) * 8 + (lane & 7);
+    iv = blockIdx.y * 8 + (wid >> 1) * 4 + (lane >> 3);
+}
+
+template <int N>
+__device__ __forceinline__ float march_forward(const GridBox &gb, const double (&s)[3], const double (&w)[3],
+                                               const float *__restrict__ c, const QuadRule &qr, bool kahan, int *err)
+{
+    RaySetup rs;
+    if (!ray_setup<N>(gb, s, w, rs)) return 0.0f;
+    float sum = 0.0f, comp = 0.0f;
+    bool ok = true;
+#pragma unroll 1
+    for (int j = rs.j0; j <= rs.j1; ++j) {
+        FwdSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0.0f};
+        ok &= slab_sweep<N>(rs, j, qr, sk);
+        const float v = sk.acc * rs.inv_wd;
+        if (kahan) kahan_add(sum, comp, v);
+        else sum += v;
+    }
+    if (!ok) atomicOr(err, 1);
+    return sum;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y,
+                                                       QuadRule qr, int kahan)
+{
+    int iu, iv;
+    tile_pixel(iu, iv);
+    const int k = blockIdx.z;
+    if (iu >= g.nu || iv >= g.nv) return;
+    double s[3], w[3];
+    view_ray(g, k, iu, iv, s, w);
+    const GridBox gb = grid_of(g);
+    y[((long long)k * g.nv + iv) * g.nu + iu] = march_forward<N>(gb, s, w, c, qr, kahan != 0, g.err);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__restrict__ c, float *__restrict__ y,
+                                                      QuadRule qr, int kahan)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.n_rays) return;
+    double s[3], w[3];
+    explicit_ray(g, r, s, w);
+    const GridBox gb = grid_of(g);
+    y[r] = march_forward<N>(gb, s, w, c, qr, kahan != 0, g.err);
+}
+
+// ---------------------------------------------------------------- pair count
+template <int N>
+__device__ __forceinline__ unsigned int march_count(const GridBox &gb, const double (&s)[3], const double (&w)[3],
+                                                    const QuadRule &qr, int *err)
+{
+    RaySetup rs;
+    if (!ray_setup<N>(gb, s, w, rs)) return 0u;
+    CountSink sk{rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0u};
+    bool ok = true;
+#pragma unroll 1
+    for (int j = rs.j0; j <= rs.j1; ++j) ok &= slab_sweep<N>(rs, j, qr, sk);
+    if (!ok) atomicOr(err, 1);
+    return sk.n;
+}
+
+__device__ __forceinline__ void add_count(unsigned long long *count, unsigned int v)
+{
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(count, x);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_count_views(DevGeom g, unsigned long long *count, QuadRule qr)
+{
+    int iu, iv;
+    tile_pixel(iu, iv);
+    const int k = blockIdx.z;
+    unsigned int v = 0;
+    if (iu < g.nu && iv < g.nv) {
+        double s[3], w[3];
+        view_ray(g, k, iu, iv, s, w);
+        v = march_count<N>(grid_of(g), s, w, qr, g.err);
+    }
+    add_count(count, v);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long long *count, QuadRule qr)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int v = 0;
+    if (r < g.n_rays) {
+        double s[3], w[3];
+        explicit_ray(g, r, s, w);
+        v = march_count<N>(grid_of(g), s, w, qr, g.err);
+    }
+    add_count(count, v);
+}
+
+// ---------------------------------------------------------------- adjoint: ray-driven scatter (explicit rays)
+template <int N>
+__global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__restrict__ y, float *__restrict__ c,
+                                                      QuadRule qr)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.n_rays) return;
+    const float yr = y[r];
+    if (yr == 0.0f) return;
+    double s[3], w[3];
+    explicit_ray(g, r, s, w);
+    RaySetup rs;
+    if (!ray_setup<N>(grid_of(g), s, w, rs)) return;
+    bool ok = true;
+#pragma unroll 1
+    for (int j = rs.j0; j <= rs.j1; ++j) {
+        AtomicSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], yr * rs.inv_wd};
+        ok &= slab_sweep<N>(rs, j, qr, sk);
+    }
+    if (!ok) atomicOr(g.err, 1);
+}
+
+// ---------------------------------------------------------------- adjoint: brick gather (view geometries)
+constexpr int kBrick = 16;                        // brick edge (coefficients)
+constexpr int kBrickVol = kBrick * kBrick * kBrick;
+constexpr int kAdjThreads = 256;
+
+// detector pixel window of the box [lo, hi] (world) for view k: projection
+// of its 8 corners (parallel: along the direction; cone: from the source)
+__device__ __forceinline__ bool pixel_window(const DevGeom &g, int k, const double (&lo)[3], const double (&hi)[3],
+                                             int &u0, int &u1, int &v0, int &v1)
+{
+    const ViewPose &P = g.views[k];
+    double amin = 1e300, amax = -1e300, bmin = 1e300, bmax = -1e300;
+    const double cu = 0.5 * (g.nu - 1), cv = 0.5 * (g.nv - 1);
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        double x[3] = {(corner & 1) ? hi[0] : lo[0], (corner & 2) ? hi[1] : lo[1], (corner & 4) ? hi[2] : lo[2]};
+        double pt[3];
+        if (g.kind == 1) {
+            // move x along the direction onto the detector plane
+            double rel[3] = {x[0] - P.dc[0], x[1] - P.dc[1], x[2] - P.dc[2]};
+            const double t = (rel[0] * P.nrm[0] + rel[1] * P.nrm[1] + rel[2] * P.nrm[2]) /
+                             (P.src[0] * P.nrm[0] + P.src[1] * P.nrm[1] + P.src[2] * P.nrm[2]);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) pt[e] = rel[e] - t * P.src[e];
+        } else {
+            double dx[3] = {x[0] - P.src[0], x[1] - P.src[1], x[2] - P.src[2]};
+            double sd[3] = {P.dc[0] - P.src[0], P.dc[1] - P.src[1], P.dc[2] - P.src[2]};
+            const double num = sd[0] * P.nrm[0] + sd[1] * P.nrm[1] + sd[2] * P.nrm[2];
+            const double den = dx[0] * P.nrm[0] + dx[1] * P.nrm[1] + dx[2] * P.nrm[2];
+            if (!(den * num > 0.0)) return true;  // corner behind the source: keep the whole detector
+            const double lam = num / den;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) pt[e] = P.src[e] + lam * dx[e] - P.dc[e];
+        }
+        const double a = pt[0] * P.ud[0] + pt[1] * P.ud[1] + pt[2] * P.ud[2];
+        const double b = pt[0] * P.vd[0] + pt[1] * P.vd[1] + pt[2] * P.vd[2];
+        amin = fmin(amin, a);
+        amax = fmax(amax, a);
+        bmin = fmin(bmin, b);
+        bmax = fmax(bmax, b);
+    }
+    // clamp to the detector before converting (far corners stay in range)
+    const double eps = 1e-3;
+    u0 = (int)fmin(fmax(0.0, ceil(amin + cu - eps)), (double)g.nu);
+    u1 = (int)fmax(fmin((double)(g.nu - 1), floor(amax + cu + eps)), -1.0);
+    v0 = (int)fmin(fmax(0.0, ceil(bmin + cv - eps)), (double)g.nv);
+    v1 = (int)fmax(fmin((double)(g.nv - 1), floor(bmax + cv + eps)), -1.0);
+    return false;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const float *__restrict__ y,
+                                                                float *__restrict__ c, QuadRule qr, int bx, int by)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *tot = (double *)smem;                       // kBrickVol FP64 totals
+    float *part = (float *)(smem + kBrickVol * sizeof(double));  // kBrickVol per-view partials
+    constexpr double W = 0.5 * (N + 1);
+    const int bid = blockIdx.x;
+    const int b0[3] = {(bid % bx) * kBrick, ((bid / bx) % by) * kBrick, (bid / (bx * by)) * kBrick};
+    int bn[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) bn[e] = min(kBrick, g.n[e] - b0[e]);
+    for (int i = threadIdx.x; i < kBrickVol; i += kAdjThreads) {
+        tot[i] = 0.0;
+        part[i] = 0.0f;
+    }
+    // support box of the brick's bases (world)
+    double lo[3], hi[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        lo[e] = g.org[e] + b0[e] - W;
+        hi[e] = g.org[e] + b0[e] + bn[e] - 1 + W;
+    }
+    const GridBox gb = grid_of(g);
+    const int lstride[3] = {1, kBrick, kBrick * kBrick};
+    bool ok = true;
+    __syncthreads();
+    for (int k = 0; k < g.n_views; ++k) {
+        int u0, u1, v0, v1;
+        if (pixel_window(g, k, lo, hi, u0, u1, v0, v1)) {
+            u0 = 0;
+            u1 = g.nu - 1;
+            v0 = 0;
+            v1 = g.nv - 1;
+        }
+        const int wu = u1 - u0 + 1, wv = v1 - v0 + 1;
+        const int npix = (wu > 0 && wv > 0) ? wu * wv : 0;
+        for (int p = threadIdx.x; p < npix; p += kAdjThreads) {
+            const int iu = u0 + p % wu, iv = v0 + p / wu;
+            const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
+            if (yr == 0.0f) continue;
+            double s[3], w[3];
+            view_ray(g, k, iu, iv, s, w);
+            RaySetup rs;
+            if (!ray_setup<N>(gb, s, w, rs)) continue;
+            // brick bounds in the ray's mirrored (d, a, b) coordinates
+            int blo[3], bhi[3], L[3], Loff = 0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int e = rs.ax[q];
+                const int r0 = b0[e], r1 = b0[e] + bn[e] - 1;
+                blo[q] = rs.sg[q] > 0 ? r0 : -r1;
+                bhi[q] = rs.sg[q] > 0 ? r1 : -r0;
+                L[q] = rs.sg[q] * lstride[e];
+                Loff -= b0[e] * lstride[e];
+            }
+            const int jlo = max(rs.j0, blo[0]), jhi = min(rs.j1, bhi[0]);
+            const float yv = yr * rs.inv_wd;
+#pragma unroll 1
+            for (int j = jlo; j <= jhi; ++j) {
+                BrickSink sk{part, L[0], L[1], L[2], Loff, blo[1], bhi[1], blo[2], bhi[2], yv};
+                ok &= slab_sweep<N>(rs, j, qr, sk);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kBrickVol; i += kAdjThreads) {
+            tot[i] += (double)part[i];
+            part[i] = 0.0f;
+        }
+        __syncthreads();
+    }
+    if (!ok) atomicOr(g.err, 1);
+    for (int i = threadIdx.x; i < kBrickVol; i += kAdjThreads) {
+        const int lx = i % kBrick, ly = (i / kBrick) % kBrick, lz = i / (kBrick * kBrick);
+        if (lx < bn[0] && ly < bn[1] && lz < bn[2])
+            c[((long long)(b0[2] + lz) * g.n[1] + (b0[1] + ly)) * g.n[0] + (b0[0] + lx)] = (float)tot[i];
+    }
+}
+
+constexpr size_t kAdjSmem = kBrickVol * (sizeof(double) + sizeof(float));
+
+}  // namespace spl
+
+using namespace spl;
+
+static spl_status launch_status(const char *what)
+{
+    return cuda_check(cudaGetLastError(), what);
+}
+
+template <int N>
+static spl_status forward_quad(const spl_geometry *g, const float *c, float *y, cudaStream_t st, int kahan)
+{
+    const DevGeom &dg = g->dev;
+    const QuadRule qr = quad_rule(N);
+    if (dg.n_rays == 0) return SPL_OK;
+    if (dg.kind == SPL_RAYS) {
+        const long long blocks = (dg.n_rays + 127) / 128;
+        k_forward_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, c, y, qr, kahan);
+    } else {
+        dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
+        k_forward_views<N><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan);
+    }
+    return launch_status("forward launch");
+}
+
+template <int N>
+static spl_status adjoint_quad(const spl_geometry *g, const float *y, float *c, cudaStream_t st)
+{
+    const DevGeom &dg = g->dev;
+    const QuadRule qr = quad_rule(N);
+    const long long nc = (long long)dg.n[0] * dg.n[1] * dg.n[2];
+    if (dg.kind == SPL_RAYS) {
+        spl_status s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
+        if (s != SPL_OK || dg.n_rays == 0) return s;
+        const long long blocks = (dg.n_rays + 127) / 128;
+        k_adjoint_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, y, c, qr);
+        return launch_status("adjoint launch");
+    }
+    static bool attr_set[4] = {false, false, false, false};
+    if (!attr_set[N]) {
+        spl_status s = cuda_check(cudaFuncSetAttribute(k_adjoint_bricks<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)kAdjSmem),
+                                  "adjoint smem attribute");
+        if (s != SPL_OK) return s;
+        attr_set[N] = true;
+    }
+    const int bx = (dg.n[0] + kBrick - 1) / kBrick, by = (dg.n[1] + kBrick - 1) / kBrick,
+              bz = (dg.n[2] + kBrick - 1) / kBrick;
+    k_adjoint_bricks<N><<<bx * by * bz, kAdjThreads, kAdjSmem, st>>>(dg, y, c, qr, bx, by);
+    return launch_status("adjoint launch");
+}
+
+template <int N>
+static spl_status count_pairs(const spl_geometry *g, unsigned long long *count, cudaStream_t st)
+{
+    const DevGeom &dg = g->dev;
+    const QuadRule qr = quad_rule(N);
+    if (dg.n_rays == 0) return SPL_OK;
+    if (dg.kind == SPL_RAYS) {
+        const long long blocks = (dg.n_rays + 127) / 128;
+        k_count_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, count, qr);
+    } else {
+        dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
+        k_count_views<N><<<grid, 128, 0, st>>>(dg, count, qr);
+    }
+    return launch_status("count launch");
+}
+
+static spl_status check_call(const spl_geometry *g, const spl_basis_desc *b, const void *in, const void *out)
+{
+    clear_error();
+    if (!g) return fail(SPL_ERR_ARG, "geometry is NULL");
+    spl_status s = check_basis(b);
+    if (s != SPL_OK) return s;
+    if (!in || !out) return fail(SPL_ERR_ARG, "input or output pointer is NULL");
+    if (b->mode == SPL_FP_MLP) {
+        if (spl_mlp_degree(b->mlp) != b->degree)
+            return fail(SPL_ERR_ARG, "MLP degree %d does not match basis degree %d", spl_mlp_degree(b->mlp), b->degree);
+        if (g->dev.kind == SPL_RAYS) return fail(SPL_ERR_UNSUPPORTED, "MLP footprint needs a view geometry");
+    }
+    return SPL_OK;
+}
+
+#define SPL_DISPATCH(deg, fn, ...)                                                                                   \
+    switch (deg) {                                                                                                   \
+    case 0: return fn<0>(__VA_ARGS__);                                                                               \
+    case 1: return fn<1>(__VA_ARGS__);                                                                               \
+    case 2: return fn<2>(__VA_ARGS__);                                                                               \
+    default: return fn<3>(__VA_ARGS__);                                                                              \
+    }
+
+extern "C" spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *b, const float *c_dev, float *y_dev,
+                                  void *stream)
+{
+    spl_status s = check_call(g, b, c_dev, y_dev);
+    if (s != SPL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->mode == SPL_FP_MLP) return spl::forward_mlp(g, b, c_dev, y_dev, st);
+    SPL_DISPATCH(b->degree, forward_quad, g, c_dev, y_dev, st, b->kahan)
+}
+
+extern "C" spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *b, const float *y_dev, float *c_dev,
+                                  void *stream)
+{
+    spl_status s = check_call(g, b, y_dev, c_dev);
+    if (s != SPL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->mode == SPL_FP_MLP) return spl::adjoint_mlp(g, b, y_dev, c_dev, st);
+    SPL_DISPATCH(b->degree, adjoint_quad, g, y_dev, c_dev, st)
+}
+
+extern "C" spl_status spl_count_pairs(const spl_geometry *g, int degree, unsigned long long *count_dev, void *stream)
+{
+    clear_error();
+    if (!g || !count_dev) return fail(SPL_ERR_ARG, "NULL argument");
+    if (degree < 0 || degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", degree);
+    SPL_DISPATCH(degree, count_pairs, g, count_dev, (cudaStream_t)stream)
+}

@@ -1,0 +1,410 @@
+// spl_march.cuh -- device core of the B-spline x-ray transform (SplineSplat,
+// arXiv 2511.11078): ray set-up, the dominant-axis slab march and the exact
+// footprint engine shared by every kernel that walks a ray.
+//
+// Paper mapping
+//   * Definition 2.1 (dominant axis d*): a ray is marched slab by slab along
+//     d* = argmax |w_d| (ties: lowest index).  Every slab l_{d*} = j is
+//     crossed exactly once.
+//   * Algorithm 2 / Algorithm 3: at each DDA cell the bases l with
+//     l_{d*} = k_{d*} and |l - k|_inf <= R are visited, minus the bases of the
+//     two previous steps.  Their union over the (at most three) cells of one
+//     slab is exactly the set of slab bases whose support the ray crosses.
+//     Here that union is produced directly: inside slab j a second DDA runs
+//     over the knot planes of all three axes, and a rolling
+//     (n+1) x (n+1) window holds the bases whose support contains the
+//     current point of the ray.  A basis enters the window when the ray
+//     enters its support and is flushed (c_l * P) exactly once when it
+//     leaves, so no basis is visited twice and none is missed.
+//   * Eq. 4 contribution Pphi(w, s - l): with xi = x_{d*} - j the local
+//     coordinate in the slab and r_e = |w_e| / |w_{d*}|,
+//       Pphi = (1/|w_{d*}|) int_{-W}^{W} beta(xi) beta(A + r_a xi - l_a)
+//                                         beta(B + r_b xi - l_b) dxi,
+//     (A, B) = the ray's transverse coordinates on the plane x_{d*} = j.
+//     Between consecutive knot-plane crossings every factor of every window
+//     basis is one polynomial of degree n, the product has degree 3n, and
+//     m = ceil((3n+1)/2) Gauss-Legendre nodes integrate it exactly.  All
+//     (n+1)^2 window bases share the nodes of a piece: each node costs
+//     3 x (n+1) B-spline weights and one (n+1) x (n+1) outer product.
+//
+// Coordinates: index coordinates u = x - origin (bases at integers) are
+// mirrored per axis so that the ray direction is componentwise >= 0
+// (beta is even, so phi_l(x) = phi_{l'}(x') with l'_e = sign_e * l_e).
+// The ray's transverse coordinate on slab j is carried as an unevaluated
+// float pair (double-float) so that positions far from the origin keep
+// ~1e-7 absolute accuracy without FP64 arithmetic in the hot loop.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace spl {
+
+constexpr int kMaxNodes = 8;
+// loop bound of one slab sweep: (n+1) d-pieces plus at most n+3 events on
+// each transverse axis (r <= 1), with margin
+constexpr int kSlabIterCap = 40;
+
+struct QuadRule {
+    float x[kMaxNodes];  // Gauss-Legendre nodes on [-1, 1]
+    float w[kMaxNodes];  // weights
+    int cap;             // loop bound of one slab sweep (kSlabIterCap)
+};
+
+// Per-view pose in FP64 (one entry per view of a view geometry).
+struct ViewPose {
+    double src[3];       // parallel: unit ray direction; cone: source position
+    double dc[3];        // detector centre
+    double du[3], dv[3]; // detector axes (include the pixel pitch)
+    double nrm[3];       // unit normal of the detector plane
+    double ud[3], vd[3]; // dual axes: a = <P - dc, ud>, b = <P - dc, vd> for P on the plane
+};
+
+struct DevGeom {
+    int kind;            // SPL_RAYS / SPL_PARALLEL / SPL_CONE
+    int n[3];            // nx, ny, nz
+    double org[3];       // world position of coefficient (0,0,0)
+    int n_views, nu, nv;
+    long long n_rays;
+    const ViewPose *views;
+    const double *ray_w; // [n_rays][3] unit directions
+    const double *ray_s; // [n_rays][3]
+    int *err;            // device error flag (bit 0: a loop bound was reached)
+};
+
+// ------------------------------------------------------------------ B-splines
+// B_{n,i}(g) = beta^n(g + n - i - W), g in [0,1): weight of the i-th of the
+// n+1 bases whose support contains a point, in power-basis coefficients.
+template <int N> struct BSpl;
+template <> struct BSpl<0> {
+    __device__ static constexpr float c(int i, int k) { return 1.0f; }
+};
+template <> struct BSpl<1> {
+    __device__ static constexpr float c(int i, int k)
+    {
+        return i == 0 ? (k == 0 ? 1.0f : -1.0f) : (k == 0 ? 0.0f : 1.0f);
+    }
+};
+template <> struct BSpl<2> {
+    __device__ static constexpr float c(int i, int k)
+    {
+        return i == 0   ? (k == 0 ? 0.5f : (k == 1 ? -1.0f : 0.5f))
+               : i == 1 ? (k == 0 ? 0.5f : (k == 1 ? 1.0f : -1.0f))
+                        : (k == 2 ? 0.5f : 0.0f);
+    }
+};
+template <> struct BSpl<3> {
+    __device__ static constexpr float c(int i, int k)
+    {
+        return i == 0   ? (k == 0 ? 1.0f / 6.0f : (k == 1 ? -0.5f : (k == 2 ? 0.5f : -1.0f / 6.0f)))
+               : i == 1 ? (k == 0 ? 2.0f / 3.0f : (k == 1 ? 0.0f : (k == 2 ? -1.0f : 0.5f)))
+               : i == 2 ? (k == 0 ? 1.0f / 6.0f : (k == 1 ? 0.5f : (k == 2 ? 0.5f : -0.5f)))
+                        : (k == 3 ? 1.0f / 6.0f : 0.0f);
+    }
+};
+
+template <int N> struct GL { static constexpr int M = (3 * N + 2) / 2 > 0 ? (3 * N + 2) / 2 : 1; };
+
+template <int N>
+__device__ __forceinline__ void bweights(float g, float (&w)[N + 1])
+{
+#pragma unroll
+    for (int i = 0; i <= N; ++i) {
+        float v = BSpl<N>::c(i, N);
+#pragma unroll
+        for (int k = N - 1; k >= 0; --k) v = fmaf(v, g, BSpl<N>::c(i, k));
+        w[i] = v;
+    }
+}
+
+// coefficients of B_{N,idx}(g) for a runtime idx (per piece, not per node)
+template <int N>
+__device__ __forceinline__ void piece_coeffs(int idx, float (&pc)[N + 1])
+{
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        float v = BSpl<N>::c(N, k);
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) v = (idx == i) ? BSpl<N>::c(i, k) : v;
+        pc[k] = v;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ float horner(const float (&pc)[N + 1], float g)
+{
+    float v = pc[N];
+#pragma unroll
+    for (int k = N - 1; k >= 0; --k) v = fmaf(v, g, pc[k]);
+    return v;
+}
+
+// ------------------------------------------------------------------ ray set-up
+struct GridBox {
+    int n[3];
+    double org[3];
+    int stride[3];   // linear-index strides of x, y, z
+};
+
+struct RaySetup {
+    int ax[3];       // axis index of (d, a, b)
+    int sg[3];       // mirror sign of (d, a, b)
+    float ra, rb;    // |w_a|/|w_d|, |w_b|/|w_d|  in [0, 1]
+    float inv_ra, inv_rb;
+    float inv_wd;    // 1 / |w_d|
+    int j0, j1;      // mirrored slab range (inclusive), reference slab j0
+    int lo[3], hi[3];  // mirrored grid bounds of (d, a, b)
+    int S[3];        // signed linear strides of (d, a, b) in mirrored coordinates
+    float Ah, Al, Bh, Bl;  // transverse coordinates at slab j0 (double-float)
+    float rah, ral, rbh, rbl;
+};
+
+// Ray in world coordinates -> slab-march set-up.  Returns false when the
+// ray meets no basis support of the grid.  Pure FP64, shared by every kernel
+// so that all of them enumerate the same pairs with the same values.
+template <int N>
+__device__ __forceinline__ bool ray_setup(const GridBox &gb, const double (&s)[3], const double (&w)[3], RaySetup &rs)
+{
+    constexpr double W = 0.5 * (N + 1);
+    double sp[3], wp[3];
+    int sg[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        sg[e] = (w[e] < 0.0) ? -1 : 1;
+        sp[e] = sg[e] * (s[e] - gb.org[e]);
+        wp[e] = fabs(w[e]);
+    }
+    int d = 0;
+    if (wp[1] > wp[d]) d = 1;
+    if (wp[2] > wp[d]) d = 2;
+    const int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+    const int axs[3] = {d, a, b};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int e = axs[q];
+        rs.ax[q] = e;
+        rs.sg[q] = sg[e];
+        rs.lo[q] = sg[e] > 0 ? 0 : -(gb.n[e] - 1);
+        rs.hi[q] = sg[e] > 0 ? gb.n[e] - 1 : 0;
+        rs.S[q] = sg[e] * gb.stride[e];
+    }
+    const double ra = wp[a] / wp[d], rb = wp[b] / wp[d];
+    double jmin = rs.lo[0], jmax = rs.hi[0];
+    const double r2[2] = {ra, rb};
+#pragma unroll
+    for (int q = 1; q < 3; ++q) {
+        const int e = axs[q];
+        const double r = r2[q - 1];
+        if (r > 0.0) {
+            const double m = W * (1.0 + r);
+            jmin = fmax(jmin, sp[d] + (rs.lo[q] - m - sp[e]) / r);
+            jmax = fmin(jmax, sp[d] + (rs.hi[q] + m - sp[e]) / r);
+        } else if (!(sp[e] > rs.lo[q] - W && sp[e] < rs.hi[q] + W)) {
+            return false;
+        }
+    }
+    if (!(jmax >= jmin - 1.0)) return false;
+    // one slab of margin on both ends; extra slabs only add empty windows
+    const double jl = fmax(floor(jmin) - 1.0, (double)rs.lo[0]);
+    const double jh = fmin(ceil(jmax) + 1.0, (double)rs.hi[0]);
+    if (jl > jh) return false;
+    rs.j0 = (int)jl;
+    rs.j1 = (int)jh;
+    const double A = sp[a] + (rs.j0 - sp[d]) * ra;
+    const double B = sp[b] + (rs.j0 - sp[d]) * rb;
+    rs.Ah = (float)A;
+    rs.Al = (float)(A - (double)rs.Ah);
+    rs.Bh = (float)B;
+    rs.Bl = (float)(B - (double)rs.Bh);
+    rs.rah = (float)ra;
+    rs.ral = (float)(ra - (double)rs.rah);
+    rs.rbh = (float)rb;
+    rs.rbl = (float)(rb - (double)rs.rbh);
+    rs.ra = rs.rah;
+    rs.rb = rs.rbh;
+    rs.inv_ra = ra > 0.0 ? (float)(1.0 / ra) : INFINITY;
+    rs.inv_rb = rb > 0.0 ? (float)(1.0 / rb) : INFINITY;
+    rs.inv_wd = (float)(1.0 / wp[d]);
+    return true;
+}
+
+// A + k r as integer + fraction in [0, 1], with A and r double-floats:
+// TwoProduct (FMA) and TwoSum error-free transforms keep ~1e-7 absolute
+// accuracy for |A| up to a few thousand.
+__device__ __forceinline__ void df_coord(float Ah, float Al, float rh, float rl, int k, int &I, float &f)
+{
+    const float kf = (float)k;
+    const float p = __fmul_rn(kf, rh);
+    float pe = fmaf(kf, rh, -p);
+    pe = fmaf(kf, rl, pe);
+    const float s = __fadd_rn(Ah, p);
+    const float bb = __fsub_rn(s, Ah);
+    const float err = __fadd_rn(__fsub_rn(Ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    const float lo = __fadd_rn(__fadd_rn(err, pe), Al);
+    const float fl = floorf(s);
+    const float fr = __fadd_rn(__fsub_rn(s, fl), lo);
+    const float adj = floorf(fr);
+    I = (int)fl + (int)adj;
+    f = __fsub_rn(fr, adj);
+}
+
+// ------------------------------------------------------------------ slab sweep
+// Integrate one piece [x0, x1] of slab-local xi with M Gauss-Legendre nodes
+// into the (N+1) x (N+1) window accumulators.
+template <int N>
+__device__ __forceinline__ void integrate_piece(float x0, float x1, int id, float Ka, float Kb, float ra, float rb,
+                                                const QuadRule &qr, float (&acc)[N + 1][N + 1])
+{
+    constexpr int M = GL<N>::M;
+    constexpr float W = 0.5f * (N + 1);
+    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
+    float pc[N + 1];
+    piece_coeffs<N>(N - id, pc);  // beta^N on d-piece id is B_{N, N-id}(xi + W - id)
+    const float Kd = W - (float)id;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const float xi = fmaf(half, qr.x[q], mid);
+        const float bd = horner<N>(pc, xi + Kd);
+        float wa[N + 1], wb[N + 1];
+        bweights<N>(fmaf(ra, xi, Ka), wa);
+        bweights<N>(fmaf(rb, xi, Kb), wb);
+        const float cw = (half * qr.w[q]) * bd;
+#pragma unroll
+        for (int i = 0; i <= N; ++i) {
+            const float t = cw * wa[i];
+#pragma unroll
+            for (int k = 0; k <= N; ++k) acc[i][k] = fmaf(t, wb[k], acc[i][k]);
+        }
+    }
+}
+
+// Sweep slab j of a ray: every basis l' = (j, la, lb) whose support the ray
+// crosses in this slab is handed to sink.flush(j, la, lb, F) exactly once,
+// with F = |w_d| * Pphi(w, s - l).  sink.relevant(...) tells whether any
+// basis of the current window matters (skips the nodes of pieces that
+// cannot reach the sink).  Returns false if the loop bound was reached.
+template <int N, class Sink>
+__device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const QuadRule &qr, Sink &sink)
+{
+    constexpr float W = 0.5f * (N + 1);
+    int IA, IB;
+    float fa, fb;
+    df_coord(rs.Ah, rs.Al, rs.rah, rs.ral, j - rs.j0, IA, fa);
+    df_coord(rs.Bh, rs.Bl, rs.rbh, rs.rbl, j - rs.j0, IB, fb);
+    const float Ca = fa + W, Cb = fb + W;
+    int qa = (int)floorf(fmaf(-W, rs.ra, Ca));
+    int qb = (int)floorf(fmaf(-W, rs.rb, Cb));
+    float na = rs.ra > 0.0f ? ((float)(qa + 1) - Ca) * rs.inv_ra : INFINITY;
+    float nb = rs.rb > 0.0f ? ((float)(qb + 1) - Cb) * rs.inv_rb : INFINITY;
+    float acc[N + 1][N + 1];
+#pragma unroll
+    for (int i = 0; i <= N; ++i)
+#pragma unroll
+        for (int k = 0; k <= N; ++k) acc[i][k] = 0.0f;
+    float x0 = -W;
+    int id = 0;
+#pragma unroll 1
+    for (int it = 0; it < qr.cap; ++it) {
+        const float nd = (float)(id + 1) - W;
+        const float x1r = fminf(nd, fminf(na, nb));
+        const int ev = (x1r == nd) ? 0 : ((x1r == na) ? 1 : 2);
+        const float x1 = fmaxf(x1r, x0);
+        const int la0 = IA + qa - N, lb0 = IB + qb - N;
+        if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N))
+            integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
+        x0 = x1;
+        if (ev == 0) {
+            if (++id > N) {
+#pragma unroll
+                for (int i = 0; i <= N; ++i)
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) sink.flush(j, la0 + i, lb0 + k, acc[i][k]);
+                return true;
+            }
+        } else if (ev == 1) {
+#pragma unroll
+            for (int k = 0; k <= N; ++k) sink.flush(j, la0, lb0 + k, acc[0][k]);
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+                for (int k = 0; k <= N; ++k) acc[i][k] = acc[i + 1][k];
+#pragma unroll
+            for (int k = 0; k <= N; ++k) acc[N][k] = 0.0f;
+            ++qa;
+            na = ((float)(qa + 1) - Ca) * rs.inv_ra;
+        } else {
+#pragma unroll
+            for (int i = 0; i <= N; ++i) sink.flush(j, la0 + i, lb0, acc[i][0]);
+#pragma unroll
+            for (int i = 0; i <= N; ++i) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) acc[i][k] = acc[i][k + 1];
+                acc[i][N] = 0.0f;
+            }
+            ++qb;
+            nb = ((float)(qb + 1) - Cb) * rs.inv_rb;
+        }
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ rays of a geometry
+__device__ __forceinline__ void view_ray(const DevGeom &g, int k, int iu, int iv, double (&s)[3], double (&w)[3])
+{
+    const ViewPose &P = g.views[k];
+    const double a = iu - 0.5 * (g.nu - 1), b = iv - 0.5 * (g.nv - 1);
+    double q[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) q[e] = fma(b, P.dv[e], fma(a, P.du[e], P.dc[e]));
+    if (g.kind == 1) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            s[e] = q[e];
+            w[e] = P.src[e];
+        }
+    } else {
+        double dd[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) dd[e] = q[e] - P.src[e];
+        const double nrm = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            s[e] = P.src[e];
+            w[e] = dd[e] / nrm;
+        }
+    }
+}
+
+__device__ __forceinline__ void explicit_ray(const DevGeom &g, long long r, double (&s)[3], double (&w)[3])
+{
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        s[e] = g.ray_s[3 * r + e];
+        w[e] = g.ray_w[3 * r + e];
+    }
+}
+
+__device__ __forceinline__ GridBox grid_of(const DevGeom &g)
+{
+    GridBox gb;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        gb.n[e] = g.n[e];
+        gb.org[e] = g.org[e];
+    }
+    gb.stride[0] = 1;
+    gb.stride[1] = g.n[0];
+    gb.stride[2] = g.n[0] * g.n[1];
+    return gb;
+}
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
+{
+    const float yv = __fsub_rn(v, comp);
+    const float t = __fadd_rn(sum, yv);
+    comp = __fsub_rn(__fsub_rn(t, sum), yv);
+    sum = t;
+}
+
+}  // namespace spl

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libspl.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; PyTorch only provides
+device memory and streams.  If the library is missing, ``lib()`` raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SPL_OK = 0
+SPL_RAYS, SPL_PARALLEL, SPL_CONE = 0, 1, 2
+SPL_FP_QUAD, SPL_FP_MLP = 0, 1
+MLP_PARAMS = 8769
+STATUS_NAMES = {0: "SPL_OK", 1: "SPL_ERR_ARG", 2: "SPL_ERR_NONFINITE", 3: "SPL_ERR_CUDA", 4: "SPL_ERR_STEPCAP",
+                5: "SPL_ERR_OOM", 6: "SPL_ERR_STATE", 7: "SPL_ERR_UNSUPPORTED"}
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_vp = C.c_void_p
+
+
+class SplError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class GeometryDesc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("origin", C.c_double * 3),
+        ("n_rays", C.c_longlong), ("ray_omega", _dp), ("ray_s", _dp),
+        ("n_views", C.c_int), ("view_src", _dp), ("det_center", _dp), ("det_u", _dp), ("det_v", _dp),
+        ("nu", C.c_int), ("nv", C.c_int),
+    ]
+
+
+class BasisDesc(C.Structure):
+    _fields_ = [("degree", C.c_int), ("mode", C.c_int), ("mlp", _vp), ("kahan", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/spl.h
+_SIGS = {
+    "spl_make_geometry": (C.c_int, [C.POINTER(GeometryDesc), C.POINTER(_vp)]),
+    "spl_destroy_geometry": (None, [_vp]),
+    "spl_geometry_rays": (C.c_longlong, [_vp]),
+    "spl_geometry_coeffs": (C.c_longlong, [_vp]),
+    "spl_geometry_status": (C.c_int, [_vp, _vp]),
+    "spl_forward": (C.c_int, [_vp, C.POINTER(BasisDesc), _vp, _vp, _vp]),
+    "spl_adjoint": (C.c_int, [_vp, C.POINTER(BasisDesc), _vp, _vp, _vp]),
+    "spl_count_pairs": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "spl_footprint": (C.c_int, [C.POINTER(BasisDesc), C.c_longlong, _vp, _vp, _vp, _vp]),
+    "spl_features": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp, _vp, _vp]),
+    "spl_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_ulonglong, C.POINTER(_vp)]),
+    "spl_mlp_destroy": (None, [_vp]),
+    "spl_mlp_degree": (C.c_int, [_vp]),
+    "spl_mlp_set_params": (C.c_int, [_vp, _fp]),
+    "spl_mlp_get_params": (C.c_int, [_vp, _fp]),
+    "spl_mlp_eval": (C.c_int, [_vp, C.c_longlong, _vp, _vp, _vp]),
+    "spl_mlp_grad": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "spl_mlp_train_step": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_float, _vp, _vp]),
+    "spl_dot_f64_workspace_bytes": (C.c_longlong, []),
+    "spl_dot_f64": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp, C.c_longlong, _vp]),
+    "spl_cg_step_x": (C.c_int, [C.c_longlong, _vp, _vp, C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
+    "spl_cg_step_p": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
+    "spl_debug_set_iter_cap": (C.c_int, [C.c_int]),
+    "spl_last_error": (C.c_char_p, []),
+    "spl_version": (C.c_char_p, []),
+}
+
+
+def exported_names():
+    return sorted(_SIGS)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load libspl.so (raises if it is absent and not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if build_if_missing:
+                    _build.build()
+                else:
+                    raise RuntimeError("libspl.so is not built (%s); run __graft_entry__.build()" % path)
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status):
+    if status != SPL_OK:
+        msg = lib().spl_last_error()
+        raise SplError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device pointer of a contiguous CUDA tensor (marshalling only)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Geometry:
+    """Device geometry (spl_make_geometry) for a coefficient grid and a set of
+    lines: an inputs.ViewGeometry (parallel / cone views) or an
+    inputs.RayGeometry (explicit rays)."""
+
+    def __init__(self, dims, origin, geometry):
+        self.dims = tuple(int(v) for v in dims)
+        self.origin = np.asarray(origin, dtype=np.float64).reshape(3)
+        d = GeometryDesc()
+        d.nx, d.ny, d.nz = self.dims
+        for e in range(3):
+            d.origin[e] = float(self.origin[e])
+        keep = []
+        if geometry.kind == "rays":
+            w = np.ascontiguousarray(geometry.omega, dtype=np.float64)
+            s = np.ascontiguousarray(geometry.s, dtype=np.float64)
+            keep += [w, s]
+            d.kind, d.n_rays, d.ray_omega, d.ray_s = SPL_RAYS, w.shape[0], _dptr(w), _dptr(s)
+            self.shape = (w.shape[0],)
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                    (geometry.src, geometry.det_center, geometry.det_u, geometry.det_v)]
+            keep += arrs
+            d.kind = SPL_PARALLEL if geometry.kind == "parallel" else SPL_CONE
+            d.n_views = arrs[0].shape[0]
+            d.view_src, d.det_center, d.det_u, d.det_v = (_dptr(a) for a in arrs)
+            d.nu, d.nv = int(geometry.nu), int(geometry.nv)
+            self.shape = (d.n_views, d.nv, d.nu)
+        self.kind = geometry.kind
+        h = _vp()
+        check(lib().spl_make_geometry(C.byref(d), C.byref(h)))
+        self._h = h
+        self.n_rays = int(lib().spl_geometry_rays(h))
+        self.n_coeffs = int(lib().spl_geometry_coeffs(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def coeff_shape(self):
+        return (self.dims[2], self.dims[1], self.dims[0])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().spl_destroy_geometry(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, stream=None):
+        check(lib().spl_geometry_status(self._h, _stream(stream)))
+
+
+def basis(degree: int, mode: int = SPL_FP_QUAD, mlp=None, kahan: bool = True) -> BasisDesc:
+    b = BasisDesc()
+    b.degree, b.mode, b.kahan = int(degree), int(mode), 1 if kahan else 0
+    b.mlp = mlp.handle if mlp is not None else None
+    return b
+
+
+def forward(geom: Geometry, c, y, bas: BasisDesc, stream=None):
+    """y = A c (Algorithm 2).  c: float32 CUDA [nz,ny,nx]; y: float32 CUDA (n_rays)."""
+    _check_sizes(geom, c, y)
+    check(lib().spl_forward(geom.handle, C.byref(bas), _ptr(c), _ptr(y), _stream(stream)))
+
+
+def adjoint(geom: Geometry, y, c, bas: BasisDesc, stream=None):
+    """c = A^T y (matched adjoint)."""
+    _check_sizes(geom, c, y)
+    check(lib().spl_adjoint(geom.handle, C.byref(bas), _ptr(y), _ptr(c), _stream(stream)))
+
+
+def count_pairs(geom: Geometry, degree: int, stream=None) -> int:
+    import torch
+
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    check(lib().spl_count_pairs(geom.handle, int(degree), _ptr(cnt), _stream(stream)))
+    return int(cnt.item())
+
+
+def footprint(bas: BasisDesc, omega, p, out, stream=None):
+    n = omega.shape[0]
+    check(lib().spl_footprint(C.byref(bas), n, _ptr(omega), _ptr(p), _ptr(out), _stream(stream)))
+
+
+def features(degree: int, omega, p, feat, stream=None):
+    check(lib().spl_features(int(degree), omega.shape[0], _ptr(omega), _ptr(p), _ptr(feat), _stream(stream)))
+
+
+def dot_workspace(device=None):
+    import torch
+
+    nbytes = int(lib().spl_dot_f64_workspace_bytes())
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def dot_f64(a, b, out, work, stream=None):
+    """out[0] = sum a_i b_i in FP64 (deterministic)."""
+    if a.numel() != b.numel():
+        raise ValueError("length mismatch")
+    check(lib().spl_dot_f64(a.numel(), _ptr(a), _ptr(b), _ptr(out), _ptr(work), work.numel(), _stream(stream)))
+
+
+def cg_step_x(x, p, r, q, num, den, stream=None):
+    check(lib().spl_cg_step_x(x.numel(), _ptr(x), _ptr(p), r.numel(), _ptr(r), _ptr(q), _ptr(num), _ptr(den),
+                              _stream(stream)))
+
+
+def cg_step_p(p, s, num, den, stream=None):
+    check(lib().spl_cg_step_p(p.numel(), _ptr(p), _ptr(s), _ptr(num), _ptr(den), _stream(stream)))
+
+
+def _check_sizes(geom, c, y):
+    import torch
+
+    for t in (c, y):
+        if t.dtype != torch.float32:
+            raise TypeError("expected float32 tensors")
+    if c.numel() != geom.n_coeffs or y.numel() != geom.n_rays:
+        raise ValueError("c has %d values (need %d), y has %d (need %d)" % (c.numel(), geom.n_coeffs, y.numel(),
+                                                                             geom.n_rays))

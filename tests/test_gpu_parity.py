@@ -1,0 +1,356 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Element-by-element comparisons on seeded inputs at sizes the oracle finishes
+in seconds (several 16x8 detector tiles and 16^3 coefficient bricks with
+ragged tails), plus sampled comparisons at the full size of the 128^3
+tilt-series workload in the launch configuration the benchmark times.
+Tolerance: relative L2 error <= 1e-5 for FP32 forward and adjoint against
+the FP64 oracle (the target the method is held to); footprints within
+2e-6 of the footprint peak (FP32 node arithmetic).
+"""
+import numpy as np
+import pytest
+
+from paper_2511_11078_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2511_11078_gb300 import build as B
+    from paper_2511_11078_gb300 import spl
+
+    B.build()
+    spl.lib()
+    assert torch.cuda.is_available()
+    return torch, spl
+
+
+def oracle_geom(orc, geo):
+    if geo.kind == "rays":
+        return orc.Geometry("rays", omega=geo.omega, s=geo.s)
+    if geo.kind == "parallel":
+        return orc.Geometry("parallel", direction=geo.src, det_center=geo.det_center, det_u=geo.det_u,
+                            det_v=geo.det_v, nu=geo.nu, nv=geo.nv)
+    return orc.Geometry("cone", source=geo.src, det_center=geo.det_center, det_u=geo.det_u, det_v=geo.det_v,
+                        nu=geo.nu, nv=geo.nv)
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def gpu_forward(env, dims, origin, geo, c, degree, kahan=True):
+    torch, spl = env
+    g = spl.Geometry(dims, origin, geo)
+    ct = torch.tensor(np.asarray(c, dtype=np.float32), device="cuda")
+    y = torch.empty(g.n_rays, dtype=torch.float32, device="cuda")
+    spl.forward(g, ct, y, spl.basis(degree, kahan=kahan))
+    g.status()
+    return y.cpu().numpy().astype(np.float64)
+
+
+def gpu_adjoint(env, dims, origin, geo, y, degree):
+    torch, spl = env
+    g = spl.Geometry(dims, origin, geo)
+    yt = torch.tensor(np.asarray(y, dtype=np.float32), device="cuda")
+    c = torch.full(g.coeff_shape, float("nan"), dtype=torch.float32, device="cuda")
+    spl.adjoint(g, yt, c, spl.basis(degree))
+    g.status()
+    return c.cpu().numpy().astype(np.float64)
+
+
+DIMS = (20, 18, 17)  # two 16-bricks per axis with ragged tails
+
+
+def parallel_geometry(rng, nu=21, nv=19, shift=(0.137, -0.271, 0.093)):
+    dirs = np.concatenate([
+        I.random_directions(rng, 4),
+        np.array([[1.0, 0, 0], [0, -1.0, 0], [0, 0, 1.0],
+                  [np.cos(0.5), np.sin(0.5), 0.0],
+                  [1.0, 1.0, 1.0], [1.0, -1.0, 0.0], [-1.0, 1.0, 1.0]]),
+    ])
+    return I.parallel_views(dirs, nu, nv, 1.0, center=shift)
+
+
+def cone_geometry(nu=23, nv=17):
+    return I.helical_cone(4, 60.0, 90.0, nu, nv, 1.3, turns=0.8, table_feed=5.0)
+
+
+def ray_geometry(rng, dims, origin):
+    w = I.random_directions(rng, 150)
+    ctr = origin + (np.asarray(dims) - 1) / 2.0
+    s = ctr + rng.uniform(-8, 8, (150, 3)) + rng.uniform(-30, 30, (150, 1)) * w
+    extra_w = np.array([[0, 0, 1.0], [0, 1.0, 0], [1.0, 0, 0], [1, 1, 0.0], [1, 1, 1.0], [0, 1, -1.0], [1e-9, 0, 1.0]])
+    extra_s = ctr + np.array([[0.3, 0.2, 0], [1.1, 0, -0.4], [0, 2.5, 1.5], [0, 0, 0.7], [0.2, -0.1, 0.3],
+                              [-3.0, 0.4, 0.4], [0.5, 0.5, 0]])
+    # rays that miss the volume entirely
+    miss_w = np.array([[0, 0, 1.0], [1.0, 0, 0]])
+    miss_s = ctr + np.array([[40.0, 0, 0], [0, 0, 35.0]])
+    return I.RayGeometry(np.concatenate([w, extra_w, miss_w]), np.concatenate([s, extra_s, miss_s]))
+
+
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_forward_parallel(env, orc, degree):
+    rng = np.random.default_rng(1000 + degree)
+    origin = I.centred_origin(DIMS)
+    c = rng.normal(size=DIMS[::-1]).astype(np.float32).astype(np.float64)
+    geo = parallel_geometry(rng)
+    y = gpu_forward(env, DIMS, origin, geo, c, degree)
+    yref = orc.forward(degree, DIMS, origin, c, oracle_geom(orc, geo))
+    assert rel_l2(y, yref) <= TOL, rel_l2(y, yref)
+    assert np.max(np.abs(y - yref)) <= 1e-4 * np.max(np.abs(yref))
+
+
+@pytest.mark.parametrize("degree", [1, 3])
+def test_forward_cone(env, orc, degree):
+    rng = np.random.default_rng(1100 + degree)
+    origin = I.centred_origin(DIMS)
+    c = rng.uniform(0, 1, size=DIMS[::-1]).astype(np.float32).astype(np.float64)
+    geo = cone_geometry()
+    y = gpu_forward(env, DIMS, origin, geo, c, degree)
+    yref = orc.forward(degree, DIMS, origin, c, oracle_geom(orc, geo))
+    assert rel_l2(y, yref) <= TOL, rel_l2(y, yref)
+
+
+@pytest.mark.parametrize("degree", [0, 2, 3])
+def test_forward_explicit_rays(env, orc, degree):
+    rng = np.random.default_rng(1200 + degree)
+    origin = I.centred_origin(DIMS) + np.array([0.25, -0.5, 3.0])
+    c = rng.normal(size=DIMS[::-1]).astype(np.float32).astype(np.float64)
+    geo = ray_geometry(rng, DIMS, origin)
+    y = gpu_forward(env, DIMS, origin, geo, c, degree)
+    yref = orc.forward(degree, DIMS, origin, c, oracle_geom(orc, geo))
+    assert rel_l2(y, yref) <= TOL, rel_l2(y, yref)
+    assert y[-1] == 0.0 and y[-2] == 0.0  # rays that miss the grid
+
+
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_adjoint_parallel(env, orc, degree):
+    rng = np.random.default_rng(1300 + degree)
+    origin = I.centred_origin(DIMS)
+    geo = parallel_geometry(rng)
+    y = rng.normal(size=geo.n_rays).astype(np.float32).astype(np.float64)
+    c = gpu_adjoint(env, DIMS, origin, geo, y, degree)
+    cref = orc.adjoint(degree, DIMS, origin, y, oracle_geom(orc, geo))
+    assert np.all(np.isfinite(c))
+    assert rel_l2(c, cref) <= TOL, rel_l2(c, cref)
+
+
+@pytest.mark.parametrize("degree", [1, 3])
+def test_adjoint_cone(env, orc, degree):
+    rng = np.random.default_rng(1400 + degree)
+    origin = I.centred_origin(DIMS)
+    geo = cone_geometry()
+    y = rng.uniform(-1, 1, size=geo.n_rays).astype(np.float32).astype(np.float64)
+    c = gpu_adjoint(env, DIMS, origin, geo, y, degree)
+    cref = orc.adjoint(degree, DIMS, origin, y, oracle_geom(orc, geo))
+    assert rel_l2(c, cref) <= TOL, rel_l2(c, cref)
+
+
+@pytest.mark.parametrize("degree", [0, 3])
+def test_adjoint_explicit_rays(env, orc, degree):
+    rng = np.random.default_rng(1500 + degree)
+    origin = I.centred_origin(DIMS)
+    geo = ray_geometry(rng, DIMS, origin)
+    y = rng.normal(size=geo.n_rays).astype(np.float32).astype(np.float64)
+    c = gpu_adjoint(env, DIMS, origin, geo, y, degree)
+    cref = orc.adjoint(degree, DIMS, origin, y, oracle_geom(orc, geo))
+    assert rel_l2(c, cref) <= TOL, rel_l2(c, cref)
+
+
+@pytest.mark.parametrize("kind", ["parallel", "cone", "rays"])
+def test_dot_product_adjointness(env, kind):
+    """<A c, y> = <c, A^T y> for the GPU operators (FP32 arithmetic, FP64
+    inner products of the outputs)."""
+    rng = np.random.default_rng(1600)
+    origin = I.centred_origin(DIMS)
+    geo = {"parallel": parallel_geometry(rng), "cone": cone_geometry(), "rays": ray_geometry(rng, DIMS, origin)}[kind]
+    c = rng.normal(size=DIMS[::-1]).astype(np.float32)
+    y = rng.normal(size=geo.n_rays).astype(np.float32)
+    Ac = gpu_forward(env, DIMS, origin, geo, c, 3)
+    ATy = gpu_adjoint(env, DIMS, origin, geo, y, 3)
+    lhs = float(Ac @ y.astype(np.float64))
+    rhs = float(np.sum(c.astype(np.float64) * ATy))
+    scale = np.linalg.norm(Ac) * np.linalg.norm(y)
+    assert abs(lhs - rhs) <= 1e-6 * scale, (lhs, rhs)
+
+
+def test_axis_aligned_rays_on_voxel_faces(env, orc):
+    """Degree 0 with rays lying in voxel faces (half-open cells): same
+    convention as the oracle."""
+    dims = (6, 5, 4)
+    origin = np.zeros(3)
+    rng = np.random.default_rng(1700)
+    c = rng.uniform(0, 1, size=(4, 5, 6)).astype(np.float32).astype(np.float64)
+    w = np.array([[0, 0, 1.0], [0, 1.0, 0], [1.0, 0, 0], [0, 0, 1.0]])
+    s = np.array([[2.5, 1.5, 0.0], [0.5, 0.0, 1.5], [0.0, 3.5, 2.5], [-0.5, 1.0, 0]])
+    geo = I.RayGeometry(w, s)
+    y = gpu_forward(env, dims, origin, geo, c, 0)
+    yref = orc.forward(0, dims, origin, c, oracle_geom(orc, geo))
+    np.testing.assert_allclose(y, yref, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_footprint_exact(env, orc, degree):
+    torch, spl = env
+    rng = np.random.default_rng(1800 + degree)
+    w, p = I.footprint_samples(rng, 4096, degree)
+    p = p + rng.uniform(-3, 3, (4096, 1)) * w  # shift along the line
+    w32 = w.astype(np.float32)
+    p32 = p.astype(np.float32)
+    out = torch.empty(4096, dtype=torch.float32, device="cuda")
+    spl.footprint(spl.basis(degree), torch.tensor(w32, device="cuda"), torch.tensor(p32, device="cuda"), out)
+    ref = orc.footprint_batch(degree, w32.astype(np.float64), p32.astype(np.float64))
+    err = np.max(np.abs(out.cpu().numpy() - ref))
+    assert err <= 2e-6 * ref.max(), err
+
+
+@pytest.mark.parametrize("degree", [0, 3])
+def test_pair_count(env, orc, degree):
+    torch, spl = env
+    rng = np.random.default_rng(1900 + degree)
+    origin = I.centred_origin(DIMS)
+    geo = parallel_geometry(rng)
+    g = spl.Geometry(DIMS, origin, geo)
+    got = spl.count_pairs(g, degree)
+    ref = orc.count_pairs(degree, DIMS, origin, oracle_geom(orc, geo))
+    assert abs(got - ref) <= 1e-5 * ref, (got, ref)
+
+
+def test_kahan_off_still_accurate(env, orc):
+    rng = np.random.default_rng(2000)
+    origin = I.centred_origin(DIMS)
+    c = rng.uniform(0, 1, size=DIMS[::-1]).astype(np.float32).astype(np.float64)
+    geo = parallel_geometry(rng)
+    yref = orc.forward(3, DIMS, origin, c, oracle_geom(orc, geo))
+    y0 = gpu_forward(env, DIMS, origin, geo, c, 3, kahan=False)
+    y1 = gpu_forward(env, DIMS, origin, geo, c, 3, kahan=True)
+    assert rel_l2(y0, yref) <= TOL and rel_l2(y1, yref) <= TOL
+
+
+def test_empty_and_single_coefficient_grids(env, orc):
+    torch, spl = env
+    # a grid of one coefficient: A c is the footprint of that basis
+    dims = (1, 1, 1)
+    origin = np.array([0.2, -0.1, 0.3])
+    rng = np.random.default_rng(2100)
+    geo = ray_geometry(rng, dims, origin)
+    c = np.array([[[1.5]]])
+    y = gpu_forward(env, dims, origin, geo, c, 3)
+    yref = orc.forward(3, dims, origin, c, oracle_geom(orc, geo))
+    assert rel_l2(y, yref) <= TOL
+    # a geometry with no views: launches nothing, succeeds
+    g = spl.Geometry((4, 4, 4), np.zeros(3), I.ViewGeometry("parallel", np.zeros((0, 3)), np.zeros((0, 3)),
+                                                            np.zeros((0, 3)), np.zeros((0, 3)), 4, 4))
+    assert g.n_rays == 0
+    yt = torch.empty(0, dtype=torch.float32, device="cuda")
+    ct = torch.zeros((4, 4, 4), dtype=torch.float32, device="cuda")
+    spl.forward(g, ct, yt, spl.basis(3))
+    spl.adjoint(g, yt, ct, spl.basis(3))
+    torch.cuda.synchronize()
+    assert float(ct.abs().sum()) == 0.0
+
+
+def test_stepcap_flag_reports_error(env):
+    """Lower the per-slab loop bound: kernels stop early (bounded loops, no
+    hang), set the geometry's error flag, and the status call reports it."""
+    torch, spl = env
+    rng = np.random.default_rng(2200)
+    origin = I.centred_origin(DIMS)
+    geo = parallel_geometry(rng)
+    g = spl.Geometry(DIMS, origin, geo)
+    ct = torch.ones(DIMS[::-1], dtype=torch.float32, device="cuda")
+    y = torch.empty(g.n_rays, dtype=torch.float32, device="cuda")
+    L = spl.lib()
+    old = L.spl_debug_set_iter_cap(2)
+    try:
+        spl.forward(g, ct, y, spl.basis(3))
+        with pytest.raises(spl.SplError) as ei:
+            g.status()
+        assert ei.value.status == 4
+    finally:
+        L.spl_debug_set_iter_cap(old)
+    spl.forward(g, ct, y, spl.basis(3))
+    g.status()  # flag was cleared, normal bound restored
+
+
+def test_dot_f64_and_cg_steps(env):
+    torch, spl = env
+    rng = np.random.default_rng(2300)
+    work = spl.dot_workspace()
+    for n in (0, 1, 7, 1000003):
+        a = rng.normal(size=n).astype(np.float32)
+        b = rng.normal(size=n).astype(np.float32)
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        at, bt = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+        spl.dot_f64(at, bt, out, work)
+        v1 = float(out.item())
+        spl.dot_f64(at, bt, out, work)
+        assert float(out.item()) == v1  # deterministic
+        ref = float(np.dot(a.astype(np.float64), b.astype(np.float64)))
+        assert abs(v1 - ref) <= 1e-12 * max(1.0, np.sum(np.abs(a.astype(np.float64) * b)))
+    n, m = 1000, 777
+    x = rng.normal(size=n).astype(np.float32)
+    p = rng.normal(size=n).astype(np.float32)
+    r = rng.normal(size=m).astype(np.float32)
+    q = rng.normal(size=m).astype(np.float32)
+    T = lambda v: torch.tensor(v, device="cuda")
+    xt, pt, rt, qt = T(x), T(p), T(r), T(q)
+    num = torch.tensor([3.0], dtype=torch.float64, device="cuda")
+    den = torch.tensor([4.0], dtype=torch.float64, device="cuda")
+    spl.cg_step_x(xt, pt, rt, qt, num, den)
+    np.testing.assert_allclose(xt.cpu().numpy(), x + 0.75 * p, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(rt.cpu().numpy(), r - 0.75 * q, rtol=1e-6, atol=1e-6)
+    st = T(q[:n] if m >= n else rng.normal(size=n).astype(np.float32))
+    spl.cg_step_p(pt, st, num, den)
+    np.testing.assert_allclose(pt.cpu().numpy(), st.cpu().numpy() + 0.75 * p, rtol=1e-6, atol=1e-6)
+
+
+# ---------------------------------------------------------------- full size, sampled
+@pytest.fixture(scope="module")
+def tilt128():
+    return I.workload_tilt(3)
+
+
+def test_full_size_forward_sampled(env, orc, tilt128):
+    """128^3 cubic, 244 parallel views of 192x192 (the benchmark's launch
+    configuration): sampled rays against the oracle."""
+    torch, spl = env
+    wl = tilt128
+    g = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    ct = torch.tensor(wl.coeffs, device="cuda")
+    y = torch.empty(g.n_rays, dtype=torch.float32, device="cuda")
+    spl.forward(g, ct, y, spl.basis(3))
+    g.status()
+    rng = np.random.default_rng(2400)
+    rays = np.sort(rng.choice(g.n_rays, 48, replace=False))
+    # include a few rays of the axis-aligned first view
+    rays = np.unique(np.concatenate([rays, [96 * 192 + 96, 100 * 192 + 7]]))
+    yref, pairs = orc.forward_subset(3, wl.dims, wl.origin, wl.coeffs.astype(np.float64),
+                                     oracle_geom(orc, wl.geometry), rays)
+    got = y.cpu().numpy()[rays].astype(np.float64)
+    assert rel_l2(got, yref) <= TOL, rel_l2(got, yref)
+    assert pairs.sum() > 0
+
+
+def test_full_size_adjoint_sampled(env, orc, tilt128):
+    torch, spl = env
+    wl = tilt128
+    g = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    rng = np.random.default_rng(2500)
+    y = rng.uniform(0, 1, size=g.n_rays).astype(np.float32)
+    c = torch.empty(g.coeff_shape, dtype=torch.float32, device="cuda")
+    spl.adjoint(g, torch.tensor(y, device="cuda"), c, spl.basis(3))
+    g.status()
+    k = np.sort(rng.choice(g.n_coeffs, 24, replace=False))
+    k = np.unique(np.concatenate([k, [0, g.n_coeffs - 1, 64 * 128 * 128 + 64 * 128 + 64]]))
+    ref, _ = orc.adjoint_at(3, wl.dims, wl.origin, y.astype(np.float64), oracle_geom(orc, wl.geometry), k)
+    got = c.cpu().numpy().reshape(-1)[k].astype(np.float64)
+    assert rel_l2(got, ref) <= TOL, rel_l2(got, ref)
