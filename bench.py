@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the B-spline x-ray transform (SplineSplat, arXiv 2511.11078).
+
+Workload (one GPU): 128^3 FP32 cubic B-spline coefficients of a 6-ellipsoid
+phantom, parallel beam, 180 single-axis tilt views over [0, 180 deg) plus 64
+random directions, 192x192 detector, pitch 1; data y = A c_true + Gaussian
+noise (sigma = 1% of max).  One step = one CGLS iteration of the
+least-squares problem of Eq. 5: one forward projection A, one matched
+adjoint A^T, two FP64 inner products and the two CG vector updates, all on
+the GPU with the exact quadrature footprint.
+
+Metric: contributions (ray, basis pairs of Eq. 4) processed per second by
+A and A^T, in G-contributions/s; also seconds per reconstruction iteration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (as it stands) on the host cores,
+each step a bounded sample of the same workload.  Under torchrun (N > 1)
+every rank runs an independent replica of the workload on its own GPU
+(weak scaling; the operators need no exchange between replicas); rank 0
+prints the JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "A/A^T G-contributions/s (exact quadrature footprint, one CGLS iteration per step)"
+UNIT = "Gcontrib/s"
+WORKLOAD = "tilt-128^3-cubic-parallel-244x192^2"
+
+# FP32 arithmetic per Gauss node and per flushed contribution of the cubic
+# slab sweep ("roofline"): 86 FLOP / node, 2 FLOP / flush.
+FLOP_PER_NODE = {0: 12, 1: 26, 2: 52, 3: 86}
+FLOP_PER_PAIR = 2
+NODES_PER_PIECE = {0: 1, 1: 2, 2: 4, 3: 5}
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--degree", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            t = [x.strip() for x in ln.split(",")]
+            if len(t) < 8:
+                continue
+            try:
+                sm.append(float(t[0]))
+                smax.append(float(t[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, t[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded ray sample of the workload
+# --------------------------------------------------------------------------
+def oracle_geometry(oracle, geo):
+    return oracle.Geometry("parallel", direction=geo.src, det_center=geo.det_center, det_u=geo.det_u,
+                           det_v=geo.det_v, nu=geo.nu, nv=geo.nv)
+
+
+def oracle_step(oracle, wl, og, rays, y_sample, threads):
+    """Oracle A on the sampled rays and A^T of y restricted to them; returns
+    (seconds, contributions of A + A^T)."""
+    t0 = time.perf_counter()
+    _, pairs = oracle.forward_subset(wl.degree, wl.dims, wl.origin, wl.coeffs, og, rays, nthreads=threads)
+    _, pairs_t = oracle.adjoint_subset(wl.degree, wl.dims, wl.origin, y_sample, og, rays, nthreads=threads)
+    return time.perf_counter() - t0, int(pairs.sum()) + int(pairs_t)
+
+
+def oracle_sample(oracle, wl, og, seconds, threads, seed=11):
+    """Ray sample sized so one oracle step (A + A^T) takes about `seconds`."""
+    rng = np.random.default_rng(seed)
+    n_rays = wl.geometry.n_rays
+    probe = np.sort(rng.choice(n_rays, 256, replace=False))
+    t, _ = oracle_step(oracle, wl, og, probe, np.ones(probe.size), threads)
+    count = int(min(n_rays, max(256, 256 * seconds / max(t, 1e-3))))
+    rays = np.sort(rng.choice(n_rays, count, replace=False))
+    return rays, rng.uniform(0, 1, count)
+
+
+def cpu_baseline(wl, seconds):
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    og = oracle_geometry(oracle, wl.geometry)
+    rays, ys = oracle_sample(oracle, wl, og, seconds, threads)
+    t, pairs = oracle_step(oracle, wl, og, rays, ys, threads)
+    return {"value": pairs / t / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of %d rays (seeded uniform sample) of the %s workload: oracle A on them plus A^T of a "
+                      "random y on them; %.1f s" % (rays.size, wl.geometry.n_rays, WORKLOAD, t)}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle timed as the benchmark step
+# --------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2511_11078_gb300 import inputs as I
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    wl = I.workload_tilt(args.degree)
+    wl.coeffs = wl.coeffs.astype(np.float64)
+    og = oracle_geometry(oracle, wl.geometry)
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    rays, ys = oracle_sample(oracle, wl, og, per_step, threads)
+    for _ in range(args.warmup):
+        oracle_step(oracle, wl, og, rays, ys, threads)
+    tt, pp = 0.0, 0
+    for _ in range(args.steps):
+        t, p = oracle_step(oracle, wl, og, rays, ys, threads)
+        tt += t
+        pp += p
+    value = pp / tt / 1e9
+    sample = "%d of %d rays (seeded uniform sample) per step: oracle A on them plus A^T of a random y on them" % (
+        rays.size, wl.geometry.n_rays)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "degree": args.degree, "footprint": "exact quadrature (FP64)",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2511_11078_gb300 import build as B
+    from paper_2511_11078_gb300 import inputs as I
+    from paper_2511_11078_gb300 import spl
+    from paper_2511_11078_gb300.recon import CGLS, Projector
+
+    B.build()
+    spl.lib()
+    n = args.degree
+    wl = I.workload_tilt(n)
+    geom = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    proj = Projector(geom, n)
+    c_true = torch.tensor(wl.coeffs, device=dev)
+    y_clean = proj.forward(c_true)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(I.SEED_BASE + 2)
+    sigma = 0.01 * float(y_clean.max())
+    y = y_clean + sigma * torch.randn(y_clean.shape, generator=gen, device=dev)
+    pairs, pieces = spl.count_work(geom, n)
+    geom.status()
+
+    cg = CGLS(proj, y)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def l2_flush():
+        flush.fill_(1.0)
+
+    for _ in range(args.warmup):
+        cg.step()
+    torch.cuda.synchronize()
+    geom.status()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                           int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        l2_flush()
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        proj.forward(cg.p, out=cg.q)          # A (timed separately below)
+        e1.record(stream)
+        spl.dot_f64(cg.q, cg.q, cg.qq, cg.work)
+        spl.cg_step_x(cg.x, cg.p, cg.r, cg.q, cg.gamma, cg.qq)
+        proj.adjoint(cg.r, out=cg.s)
+        spl.dot_f64(cg.s, cg.s, cg.gamma_new, cg.work)
+        spl.cg_step_p(cg.p, cg.s, cg.gamma_new, cg.gamma)
+        cg.gamma, cg.gamma_new = cg.gamma_new, cg.gamma
+        e2.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler.stop()
+    geom.status()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    fwd_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    ms = sum(step_ms) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # adjoint alone (events around one launch, after an L2 flush)
+    adj_ms = []
+    for _ in range(3):
+        l2_flush()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        proj.adjoint(cg.r, out=cg.s)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        adj_ms.append(a0.elapsed_time(a1))
+    fwd = statistics.median(fwd_ms)
+    adj = statistics.median(adj_ms)
+
+    contrib_step = 2 * pairs  # A and A^T visit the same pairs
+    value = ws * contrib_step / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: H2D of c and y from
+    # pinned memory, A c and A^T y, D2H of both results
+    c_host = torch.tensor(wl.coeffs).pin_memory()
+    y_host = y.cpu().pin_memory()
+    out_y = torch.empty_like(y_host).pin_memory()
+    out_c = torch.empty_like(c_host).pin_memory()
+    c_dev = torch.empty_like(c_true)
+    y_dev = torch.empty_like(y)
+    e2e_steps = max(3, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(e2e_steps):
+        c_dev.copy_(c_host, non_blocking=True)
+        y_dev.copy_(y_host, non_blocking=True)
+        proj.forward(c_dev, out=cg.q)
+        proj.adjoint(y_dev, out=cg.s)
+        out_y.copy_(cg.q, non_blocking=True)
+        out_c.copy_(cg.s, non_blocking=True)
+    e_stop.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e_start.elapsed_time(e_stop) / e2e_steps
+    h2d = c_host.numel() * 4 + y_host.numel() * 4
+    d2h = out_y.numel() * 4 + out_c.numel() * 4
+
+    clocks = sampler.summary()
+    peaks = measured_peaks()
+    max_mhz = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
+    fp32_peak_tflops = SMS * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
+    flops_fwd = pieces * NODES_PER_PIECE[n] * FLOP_PER_NODE[n] + pairs * FLOP_PER_PAIR
+    dominant = "k_forward_views" if fwd >= adj else "k_adjoint_bricks"
+    dom_ms = max(fwd, adj)
+    achieved = flops_fwd / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz max SM clock" % max_mhz,
+                "algorithmic_flop_per_launch": flops_fwd}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "degree": n, "footprint": "exact quadrature",
+                       "coeffs": list(wl.dims), "views": wl.geometry.n_views, "detector": [wl.geometry.nu,
+                                                                                          wl.geometry.nv],
+                       "contributions_per_A": pairs, "pieces_per_A": pieces,
+                       "l2": "256 MB buffer written between timed steps (outside the step events)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "s_per_recon_iter": ms / 1e3,
+            "A_ms": fwd, "AT_ms": adj,
+            "A_gcontrib_s": pairs / (fwd * 1e-3) / 1e9, "AT_gcontrib_s": pairs / (adj * 1e-3) / 1e9,
+            "e2e": {"value": ws * contrib_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": args.steps * 8,
+            "clocks": clocks,
+            "roofline": roofline,
+            "wall_s_timed_region": t_wall}
+
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        wl.coeffs = wl.coeffs.astype(np.float64)
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -87,6 +87,7 @@ def _load():
             lib.orc_count_pairs.argtypes = [C.c_int, _ip, _dp, G, _llp]
             lib.orc_adjoint.argtypes = [C.c_int, _ip, _dp, _dp, G, _dp]
             lib.orc_adjoint_at.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_longlong, _llp, _dp, _llp, C.c_int]
+            lib.orc_adjoint_subset.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_longlong, _llp, _dp, _llp, C.c_int]
             lib.orc_forward_segmented.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_longlong, _llp, _dp, C.c_int]
             lib.orc_eval_spline.restype = C.c_double
             lib.orc_eval_spline.argtypes = [C.c_int, _ip, _dp, _dp, _dp]
@@ -264,6 +265,19 @@ def adjoint_at(n, dims, origin, y, geom: Geometry, kidx, nthreads: int = 0):
     _load().orc_adjoint_at(int(n), dp, op, yp, geom.ptr, k.shape[0], kp, out.ctypes.data_as(_dp),
                            pairs.ctypes.data_as(_llp), int(nthreads))
     return out, pairs
+
+
+def adjoint_subset(n, dims, origin, y, geom: Geometry, rays, nthreads: int = 0):
+    """sum over the listed rays of y_i times their rows of Eq. 6 (transpose):
+    returns (c [nz,ny,nx], number of pairs)."""
+    keep, dp, op = _grid(dims, origin)
+    yy, yp = _d(np.asarray(y).reshape(-1))
+    r, rp = _ll(rays)
+    c = np.zeros(int(np.prod(dims)))
+    np_ = np.zeros(1, dtype=np.int64)
+    _load().orc_adjoint_subset(int(n), dp, op, yp, geom.ptr, r.shape[0], rp, c.ctypes.data_as(_dp),
+                               np_.ctypes.data_as(_llp), int(nthreads))
+    return c.reshape(int(dims[2]), int(dims[1]), int(dims[0])), int(np_[0])
 
 
 def forward_segmented(n, dims, origin, c, geom: Geometry, rays=None, nthreads: int = 0):

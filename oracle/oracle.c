@@ -404,6 +404,42 @@ void orc_adjoint(int n, const int *dims, const double *org, const double *y, con
     }
 }
 
+/* Adjoint restricted to a subset of rays: c_k = sum_{i} y_i Pphi(w_{r_i},
+ * s_{r_i} - k) over the listed rays (the rows of Eq. 6 they index); same
+ * definition as orc_adjoint, parallel over rays with one private
+ * accumulation buffer per thread.  Overwrites c; pairs[0] = pair count. */
+void orc_adjoint_subset(int n, const int *dims, const double *org, const double *y, const orc_geom *g,
+                        long long count, const long long *rays, double *c, long long *pairs, int nthreads)
+{
+    long long nk = (long long)dims[0] * dims[1] * dims[2];
+    memset(c, 0, sizeof(double) * nk);
+    long long np = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel reduction(+ : np)
+    {
+        double *priv = (double *)calloc(nk, sizeof(double));
+        fwd_ctx cnt = {n, NULL, NULL, 0.0, 0};
+#pragma omp for schedule(dynamic, 4)
+        for (long long i = 0; i < count; ++i) {
+            double s[3], w[3];
+            orc_geom_ray(g, rays[i], s, w);
+            adj_ctx x = {n, w, y[i], priv};
+            for_each_pair(n, dims, org, s, w, adj_visit, &x);
+            cnt.w = w;
+            for_each_pair(n, dims, org, s, w, count_visit, &cnt);
+        }
+        np += cnt.count;
+#pragma omp critical
+        for (long long k = 0; k < nk; ++k) c[k] += priv[k];
+        free(priv);
+    }
+    if (pairs) pairs[0] = np;
+}
+
 /* Adjoint at selected coefficients: c_k = sum over every ray of the geometry
  * whose line meets the support cube of k.  Used for sampled checks at sizes
  * where the full scatter is too slow. */

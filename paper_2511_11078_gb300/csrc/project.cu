@@ -30,6 +30,7 @@ struct FwdSink {
     int S0, S1, S2;
     int loa, hia, lob, hib;
     float acc;
+    __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
@@ -42,7 +43,9 @@ struct FwdSink {
 
 struct CountSink {
     int loa, hia, lob, hib;
-    unsigned int n;
+    unsigned int n;       // bases with a nonzero footprint
+    unsigned int pieces;  // integrated pieces (m Gauss nodes each)
+    __device__ __forceinline__ void piece() { ++pieces; }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
@@ -58,6 +61,7 @@ struct AtomicSink {
     int S0, S1, S2;
     int loa, hia, lob, hib;
     float yv;
+    __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
@@ -75,6 +79,7 @@ struct BrickSink {
     int L0, L1, L2, Loff;
     int loa, hia, lob, hib;
     float yv;
+    __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
@@ -141,17 +146,19 @@ __global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__
 
 // ---------------------------------------------------------------- pair count
 template <int N>
-__device__ __forceinline__ unsigned int march_count(const GridBox &gb, const double (&s)[3], const double (&w)[3],
-                                                    const QuadRule &qr, int *err)
+__device__ __forceinline__ void march_count(const GridBox &gb, const double (&s)[3], const double (&w)[3],
+                                            const QuadRule &qr, int *err, unsigned int &pairs, unsigned int &pieces)
 {
     RaySetup rs;
-    if (!ray_setup<N>(gb, s, w, rs)) return 0u;
-    CountSink sk{rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0u};
+    pairs = pieces = 0u;
+    if (!ray_setup<N>(gb, s, w, rs)) return;
+    CountSink sk{rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0u, 0u};
     bool ok = true;
 #pragma unroll 1
     for (int j = rs.j0; j <= rs.j1; ++j) ok &= slab_sweep<N>(rs, j, qr, sk);
     if (!ok) atomicOr(err, 1);
-    return sk.n;
+    pairs = sk.n;
+    pieces = sk.pieces;
 }
 
 __device__ __forceinline__ void add_count(unsigned long long *count, unsigned int v)
@@ -168,26 +175,28 @@ __global__ void __launch_bounds__(128) k_count_views(DevGeom g, unsigned long lo
     int iu, iv;
     tile_pixel(iu, iv);
     const int k = blockIdx.z;
-    unsigned int v = 0;
+    unsigned int v = 0, pc = 0;
     if (iu < g.nu && iv < g.nv) {
         double s[3], w[3];
         view_ray(g, k, iu, iv, s, w);
-        v = march_count<N>(grid_of(g), s, w, qr, g.err);
+        march_count<N>(grid_of(g), s, w, qr, g.err, v, pc);
     }
     add_count(count, v);
+    add_count(count + 1, pc);
 }
 
 template <int N>
 __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long long *count, QuadRule qr)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned int v = 0;
+    unsigned int v = 0, pc = 0;
     if (r < g.n_rays) {
         double s[3], w[3];
         explicit_ray(g, r, s, w);
-        v = march_count<N>(grid_of(g), s, w, qr, g.err);
+        march_count<N>(grid_of(g), s, w, qr, g.err, v, pc);
     }
     add_count(count, v);
+    add_count(count + 1, pc);
 }
 
 // ---------------------------------------------------------------- adjoint: ray-driven scatter (explicit rays)
@@ -412,13 +421,16 @@ static spl_status count_pairs(const spl_geometry *g, unsigned long long *count, 
     return launch_status("count launch");
 }
 
-static spl_status check_call(const spl_geometry *g, const spl_basis_desc *b, const void *in, const void *out)
+// c: coefficient array (never empty); y: projection array (may be empty, and
+// then NULL)
+static spl_status check_call(const spl_geometry *g, const spl_basis_desc *b, const void *c, const void *y)
 {
     clear_error();
     if (!g) return fail(SPL_ERR_ARG, "geometry is NULL");
     spl_status s = check_basis(b);
     if (s != SPL_OK) return s;
-    if (!in || !out) return fail(SPL_ERR_ARG, "input or output pointer is NULL");
+    if (!c) return fail(SPL_ERR_ARG, "coefficient pointer is NULL");
+    if (!y && g->dev.n_rays > 0) return fail(SPL_ERR_ARG, "projection pointer is NULL");
     if (b->mode == SPL_FP_MLP) {
         if (spl_mlp_degree(b->mlp) != b->degree)
             return fail(SPL_ERR_ARG, "MLP degree %d does not match basis degree %d", spl_mlp_degree(b->mlp), b->degree);
@@ -448,7 +460,7 @@ extern "C" spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *b
 extern "C" spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *b, const float *y_dev, float *c_dev,
                                   void *stream)
 {
-    spl_status s = check_call(g, b, y_dev, c_dev);
+    spl_status s = check_call(g, b, c_dev, y_dev);
     if (s != SPL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (b->mode == SPL_FP_MLP) return spl::adjoint_mlp(g, b, y_dev, c_dev, st);

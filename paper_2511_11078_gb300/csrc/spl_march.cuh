@@ -106,22 +106,52 @@ template <> struct BSpl<3> {
 
 template <int N> struct GL { static constexpr int M = (3 * N + 2) / 2 > 0 ? (3 * N + 2) / 2 : 1; };
 
+// The two outer weights vanish at an end of [0, 1]; they are evaluated in
+// factored form g^N/N! and (1-g)^N/N! so that they keep full relative
+// accuracy near the support edge (the expanded power form would cancel).
 template <int N>
 __device__ __forceinline__ void bweights(float g, float (&w)[N + 1])
 {
+    if constexpr (N == 0) {
+        w[0] = 1.0f;
+    } else if constexpr (N == 1) {
+        w[0] = 1.0f - g;
+        w[1] = g;
+    } else {
+        constexpr float inv_fact = (N == 2) ? 0.5f : 1.0f / 6.0f;
+        const float h = 1.0f - g;
+        float gp = g, hp = h;
 #pragma unroll
-    for (int i = 0; i <= N; ++i) {
-        float v = BSpl<N>::c(i, N);
+        for (int k = 1; k < N; ++k) {
+            gp *= g;
+            hp *= h;
+        }
+        w[0] = hp * inv_fact;
+        w[N] = gp * inv_fact;
 #pragma unroll
-        for (int k = N - 1; k >= 0; --k) v = fmaf(v, g, BSpl<N>::c(i, k));
-        w[i] = v;
+        for (int i = 1; i < N; ++i) {
+            float v = BSpl<N>::c(i, N);
+#pragma unroll
+            for (int k = N - 1; k >= 0; --k) v = fmaf(v, g, BSpl<N>::c(i, k));
+            w[i] = v;
+        }
     }
 }
 
-// coefficients of B_{N,idx}(g) for a runtime idx (per piece, not per node)
+// Polynomial of the d-factor beta^N(xi) on d-piece id (xi in
+// [id - W, id + 1 - W)), as coefficients pc of B_{N,idx}(arg) with
+// arg = sgn * xi + K.  Pieces in the upper half use the mirror image
+// beta(xi) = beta(-xi) = B_{N,id}(1 - g), so that the polynomial evaluated is
+// always one that is accurate where it approaches zero.
 template <int N>
-__device__ __forceinline__ void piece_coeffs(int idx, float (&pc)[N + 1])
+__device__ __forceinline__ void piece_coeffs(int id, float (&pc)[N + 1], float &sgn, float &K)
 {
+    constexpr float W = 0.5f * (N + 1);
+    const bool low = 2 * id <= N;
+    const int idx = low ? N - id : id;
+    const float g0 = W - (float)id;  // g = xi + g0
+    sgn = low ? 1.0f : -1.0f;
+    K = low ? g0 : 1.0f - g0;
 #pragma unroll
     for (int k = 0; k <= N; ++k) {
         float v = BSpl<N>::c(N, k);
@@ -200,7 +230,9 @@ __device__ __forceinline__ bool ray_setup(const GridBox &gb, const double (&s)[3
             const double m = W * (1.0 + r);
             jmin = fmax(jmin, sp[d] + (rs.lo[q] - m - sp[e]) / r);
             jmax = fmin(jmax, sp[d] + (rs.hi[q] + m - sp[e]) / r);
-        } else if (!(sp[e] > rs.lo[q] - W && sp[e] < rs.hi[q] + W)) {
+        } else if (!(sp[e] >= rs.lo[q] - W && sp[e] < rs.hi[q] + W)) {
+            // constant transverse coordinate outside every support; the lower
+            // end is inclusive for the half-open box of degree 0
             return false;
         }
     }
@@ -259,13 +291,12 @@ __device__ __forceinline__ void integrate_piece(float x0, float x1, int id, floa
     constexpr int M = GL<N>::M;
     constexpr float W = 0.5f * (N + 1);
     const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
-    float pc[N + 1];
-    piece_coeffs<N>(N - id, pc);  // beta^N on d-piece id is B_{N, N-id}(xi + W - id)
-    const float Kd = W - (float)id;
+    float pc[N + 1], sgn, Kd;
+    piece_coeffs<N>(id, pc, sgn, Kd);
 #pragma unroll
     for (int q = 0; q < M; ++q) {
         const float xi = fmaf(half, qr.x[q], mid);
-        const float bd = horner<N>(pc, xi + Kd);
+        const float bd = horner<N>(pc, fmaf(sgn, xi, Kd));
         float wa[N + 1], wb[N + 1];
         bweights<N>(fmaf(ra, xi, Ka), wa);
         bweights<N>(fmaf(rb, xi, Kb), wb);
@@ -311,8 +342,10 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
         const int ev = (x1r == nd) ? 0 : ((x1r == na) ? 1 : 2);
         const float x1 = fmaxf(x1r, x0);
         const int la0 = IA + qa - N, lb0 = IB + qb - N;
-        if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N))
+        if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
             integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
+            sink.piece();
+        }
         x0 = x1;
         if (ev == 0) {
             if (++id > N) {

@@ -213,12 +213,19 @@ def adjoint(geom: Geometry, y, c, bas: BasisDesc, stream=None):
     check(lib().spl_adjoint(geom.handle, C.byref(bas), _ptr(y), _ptr(c), _stream(stream)))
 
 
-def count_pairs(geom: Geometry, degree: int, stream=None) -> int:
+def count_work(geom: Geometry, degree: int, stream=None):
+    """(pairs, pieces) of one forward projection: contributions with a
+    nonzero footprint, and integrated pieces (Gauss rules)."""
     import torch
 
-    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
     check(lib().spl_count_pairs(geom.handle, int(degree), _ptr(cnt), _stream(stream)))
-    return int(cnt.item())
+    v = cnt.cpu().tolist()
+    return int(v[0]), int(v[1])
+
+
+def count_pairs(geom: Geometry, degree: int, stream=None) -> int:
+    return count_work(geom, degree, stream)[0]
 
 
 def footprint(bas: BasisDesc, omega, p, out, stream=None):
