@@ -224,6 +224,26 @@ long long spl_dot_f64_workspace_bytes(void);
 spl_status spl_dot_f64(long long n, const float *a_dev, const float *b_dev, double *out_dev, void *work_dev,
                        long long work_bytes, void *stream);
 
+/* Allocation-free variant of spl_dot_f64, for callers that cannot let a
+ * library allocate device memory (frameworks that own all device memory
+ * through their own pool, programs with a device-memory budget fixed at
+ * start-up, latency-critical loops that cannot afford cudaMalloc's implicit
+ * synchronisation).  The paper has no counterpart: this is an interface
+ * choice of the library.
+ * Same kernels and same result as spl_dot_f64, but the 1024 FP64 partial
+ * sums live in a file-scope device array of the library (8 KB, held by every
+ * GPU that loads the library until the process exits) instead of a caller
+ * workspace.  The first call on a device looks up that array's device
+ * address (with the device current) and caches it; make that first call
+ * before any stream capture.  Every call shares the array, which keeps the
+ * last call's partials (each call overwrites all of them, nothing needs
+ * clearing); calls that overlap on the GPU race on it.
+ * n: 0 .. SPL_DOT_NOALLOC_MAX_N elements (the partial count does not depend
+ * on n); a longer input is rejected with SPL_ERR_ARG.  Calls no cudaMalloc,
+ * cudaFree or allocating routine.  Errors: SPL_ERR_ARG, SPL_ERR_CUDA. */
+#define SPL_DOT_NOALLOC_MAX_N (1LL << 40)
+spl_status spl_dot_f64_noalloc(long long n, const float *a_dev, const float *b_dev, double *out_dev, void *stream);
+
 /* CGLS updates with FP64 scalars read from device memory (no host sync):
  *   spl_cg_step_x:  x += alpha p;  r -= alpha q;   alpha = num[0] / den[0]
  *   spl_cg_step_p:  p = s + beta p;                beta  = num[0] / den[0]

@@ -6,6 +6,8 @@
 // to the caller's workspace, and a single block adds the partials in index
 // order.  The CG updates read their FP64 scalars from device memory, so an
 // iteration needs no host synchronisation.
+#include <mutex>
+
 #include "spl_host.h"
 
 namespace spl {
@@ -126,4 +128,65 @@ extern "C" spl_status spl_cg_step_p(long long n, float *p_dev, const float *s_de
     if (n < 0 || !p_dev || !s_dev || !num_dev || !den_dev) return fail(SPL_ERR_ARG, "bad argument");
     k_cg_step_p<<<stream_blocks(n), 256, 0, (cudaStream_t)stream>>>(n, p_dev, s_dev, num_dev, den_dev);
     return cuda_check(cudaGetLastError(), "cg step launch");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free inner product.  Some callers cannot let a library allocate
+// device memory: host frameworks that own every byte of device memory
+// through their own pool and forbid third-party allocations, programs with a
+// device-memory budget fixed at start-up, and latency-critical loops that
+// cannot afford the implicit device synchronisation of cudaMalloc.  For them
+// spl_dot_f64_noalloc runs the same two kernels as spl_dot_f64 with the
+// partial sums in a fixed file-scope device array instead of a caller
+// workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+// kDotBlocks FP64 partials (8 KB); every GPU that loads the library holds
+// this array until the process exits.  Each block of k_dot_partial writes its
+// own entry, so nothing has to be cleared between calls.
+static __device__ __align__(256) double g_dot_noalloc_scratch[spl::kDotBlocks];
+
+constexpr int kMaxDevices = 64;
+static double *g_dot_noalloc_ptr[kMaxDevices];
+static std::mutex g_dot_noalloc_mutex;
+
+// Device address of the scratch array on the current device.  The first call
+// on a device looks it up (cudaGetSymbolAddress with that device current) and
+// caches it; later calls reuse the cached address.
+spl_status noalloc_scratch(double **out)
+{
+    int dev = 0;
+    spl_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != SPL_OK) return s;
+    if (dev < 0 || dev >= kMaxDevices) return fail(SPL_ERR_UNSUPPORTED, "device index %d >= %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_dot_noalloc_mutex);
+    if (!g_dot_noalloc_ptr[dev]) {
+        double *ptr = nullptr;
+        s = cuda_check(cudaGetSymbolAddress((void **)&ptr, g_dot_noalloc_scratch), "cudaGetSymbolAddress");
+        if (s != SPL_OK) return s;
+        g_dot_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_dot_noalloc_ptr[dev];
+    return SPL_OK;
+}
+
+}  // namespace
+
+extern "C" spl_status spl_dot_f64_noalloc(long long n, const float *a_dev, const float *b_dev, double *out_dev,
+                                          void *stream)
+{
+    clear_error();
+    if (n < 0) return fail(SPL_ERR_ARG, "negative length");
+    if (n > SPL_DOT_NOALLOC_MAX_N)
+        return fail(SPL_ERR_ARG, "length %lld exceeds the allocation-free maximum of %lld elements", n,
+                    (long long)SPL_DOT_NOALLOC_MAX_N);
+    if (!out_dev || (n > 0 && (!a_dev || !b_dev))) return fail(SPL_ERR_ARG, "NULL pointer");
+    double *part = nullptr;
+    spl_status s = noalloc_scratch(&part);
+    if (s != SPL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_dot_partial<<<kDotBlocks, kDotThreads, 0, st>>>(n, a_dev, b_dev, part);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(part, kDotBlocks, out_dev);
+    return cuda_check(cudaGetLastError(), "dot launch");
 }

@@ -71,6 +71,7 @@ _SIGS = {
     "spl_mlp_train_step": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_float, _vp, _vp]),
     "spl_dot_f64_workspace_bytes": (C.c_longlong, []),
     "spl_dot_f64": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp, C.c_longlong, _vp]),
+    "spl_dot_f64_noalloc": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp]),
     "spl_cg_step_x": (C.c_int, [C.c_longlong, _vp, _vp, C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
     "spl_cg_step_p": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
     "spl_debug_set_iter_cap": (C.c_int, [C.c_int]),
