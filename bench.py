@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=3)
+    ap.add_argument("--adjoint", default="gather", choices=["gather", "scatter"],
+                    help="form of A^T: brick gather (deterministic) or ray-driven scatter (float atomics)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU-baseline sample")
     return ap.parse_args()
@@ -241,7 +243,9 @@ def run_ours(args):
     n = args.degree
     wl = I.workload_tilt(n)
     geom = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    form = spl.SPL_ADJ_GATHER if args.adjoint == "gather" else spl.SPL_ADJ_SCATTER
     proj = Projector(geom, n)
+    proj.basis = spl.basis(n, adjoint=form)
     c_true = torch.tensor(wl.coeffs, device=dev)
     y_clean = proj.forward(c_true)
     gen = torch.Generator(device=dev)
@@ -345,7 +349,8 @@ def run_ours(args):
     max_mhz = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
     fp32_peak_tflops = SMS * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
     flops_fwd = pieces * NODES_PER_PIECE[n] * FLOP_PER_NODE[n] + pairs * FLOP_PER_PAIR
-    dominant = "k_forward_views" if fwd >= adj else "k_adjoint_bricks"
+    dominant = "k_forward_views" if fwd >= adj else (
+        "k_adjoint_bricks" if args.adjoint == "gather" else "k_adjoint_views_scatter")
     dom_ms = max(fwd, adj)
     achieved = flops_fwd / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
@@ -357,6 +362,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "degree": n, "footprint": "exact quadrature",
+                       "adjoint": args.adjoint,
                        "coeffs": list(wl.dims), "views": wl.geometry.n_views, "detector": [wl.geometry.nu,
                                                                                           wl.geometry.nv],
                        "contributions_per_A": pairs, "pieces_per_A": pieces,

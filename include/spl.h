@@ -57,6 +57,10 @@ typedef enum {
 enum { SPL_RAYS = 0, SPL_PARALLEL = 1, SPL_CONE = 2 };
 /* footprint evaluators: exact quadrature, or the learned f_theta (Sec. 2.2) */
 enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1 };
+/* adjoint forms for view geometries: brick gather (no global atomics,
+ * deterministic) or ray-driven scatter (float atomics, order-dependent
+ * rounding); both visit the same pairs with the same footprint values */
+enum { SPL_ADJ_GATHER = 0, SPL_ADJ_SCATTER = 1 };
 
 typedef struct spl_geometry spl_geometry; /* opaque, library-owned */
 typedef struct spl_mlp spl_mlp;           /* opaque, library-owned */
@@ -95,12 +99,14 @@ typedef struct {
  *           SPL_FP_MLP (learned footprint f_theta, Algorithm 2's f_theta*);
  *           SPL_FP_MLP needs `mlp` built for the same degree.
  *   kahan:  nonzero = compensated (Kahan) FP32 sum of the slab partials along
- *           each ray; zero = plain FP32 sum. */
+ *           each ray; zero = plain FP32 sum.
+ *   adjoint: form of spl_adjoint on view geometries (see SPL_ADJ_*). */
 typedef struct {
     int degree;
     int mode;
     const spl_mlp *mlp;
     int kahan;
+    int adjoint;  /* SPL_ADJ_GATHER (0) or SPL_ADJ_SCATTER (1); view geometries only */
 } spl_basis_desc;
 
 /* ---------------------------------------------------------------- geometry */

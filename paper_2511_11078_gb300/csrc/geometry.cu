@@ -205,6 +205,7 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
                 const double l = sqrt(dot3(P.src, P.src));
                 if (!(l > 0.0)) { free(g->views_host); free(g); return fail(SPL_ERR_NONFINITE, "view %d: zero direction", k); }
                 for (int e = 0; e < 3; ++e) P.src[e] /= l;
+                dir_setup(P.src, P.dir);
                 if (fabs(dot3(P.src, P.nrm)) < 1e-12) {
                     free(g->views_host); free(g);
                     return fail(SPL_ERR_ARG, "view %d: ray direction lies in the detector plane", k);

@@ -99,11 +99,9 @@ __device__ __forceinline__ void tile_pixel(int &iu, int &iv)
 }
 
 template <int N>
-__device__ __forceinline__ float march_forward(const GridBox &gb, const double (&s)[3], const double (&w)[3],
-                                               const float *__restrict__ c, const QuadRule &qr, bool kahan, int *err)
+__device__ __forceinline__ float march_forward(const RaySetup &rs, const float *__restrict__ c, const QuadRule &qr,
+                                               bool kahan, int *err)
 {
-    RaySetup rs;
-    if (!ray_setup<N>(gb, s, w, rs)) return 0.0f;
     float sum = 0.0f, comp = 0.0f;
     bool ok = true;
 #pragma unroll 1
@@ -126,10 +124,10 @@ __global__ void __launch_bounds__(128) k_forward_views(DevGeom g, const float *_
     tile_pixel(iu, iv);
     const int k = blockIdx.z;
     if (iu >= g.nu || iv >= g.nv) return;
-    double s[3], w[3];
-    view_ray(g, k, iu, iv, s, w);
-    const GridBox gb = grid_of(g);
-    y[((long long)k * g.nv + iv) * g.nu + iu] = march_forward<N>(gb, s, w, c, qr, kahan != 0, g.err);
+    RaySetup rs;
+    float v = 0.0f;
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) v = march_forward<N>(rs, c, qr, kahan != 0, g.err);
+    y[((long long)k * g.nv + iv) * g.nu + iu] = v;
 }
 
 template <int N>
@@ -140,18 +138,17 @@ __global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__
     if (r >= g.n_rays) return;
     double s[3], w[3];
     explicit_ray(g, r, s, w);
-    const GridBox gb = grid_of(g);
-    y[r] = march_forward<N>(gb, s, w, c, qr, kahan != 0, g.err);
+    RaySetup rs;
+    float v = 0.0f;
+    if (ray_setup<N>(grid_of(g), s, w, rs)) v = march_forward<N>(rs, c, qr, kahan != 0, g.err);
+    y[r] = v;
 }
 
 // ---------------------------------------------------------------- pair count
 template <int N>
-__device__ __forceinline__ void march_count(const GridBox &gb, const double (&s)[3], const double (&w)[3],
-                                            const QuadRule &qr, int *err, unsigned int &pairs, unsigned int &pieces)
+__device__ __forceinline__ void march_count(const RaySetup &rs, const QuadRule &qr, int *err, unsigned int &pairs,
+                                            unsigned int &pieces)
 {
-    RaySetup rs;
-    pairs = pieces = 0u;
-    if (!ray_setup<N>(gb, s, w, rs)) return;
     CountSink sk{rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0u, 0u};
     bool ok = true;
 #pragma unroll 1
@@ -176,11 +173,8 @@ __global__ void __launch_bounds__(128) k_count_views(DevGeom g, unsigned long lo
     tile_pixel(iu, iv);
     const int k = blockIdx.z;
     unsigned int v = 0, pc = 0;
-    if (iu < g.nu && iv < g.nv) {
-        double s[3], w[3];
-        view_ray(g, k, iu, iv, s, w);
-        march_count<N>(grid_of(g), s, w, qr, g.err, v, pc);
-    }
+    RaySetup rs;
+    if (iu < g.nu && iv < g.nv && view_setup<N>(g, grid_of(g), k, iu, iv, rs)) march_count<N>(rs, qr, g.err, v, pc);
     add_count(count, v);
     add_count(count + 1, pc);
 }
@@ -193,13 +187,27 @@ __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long lon
     if (r < g.n_rays) {
         double s[3], w[3];
         explicit_ray(g, r, s, w);
-        march_count<N>(grid_of(g), s, w, qr, g.err, v, pc);
+        RaySetup rs;
+        if (ray_setup<N>(grid_of(g), s, w, rs)) march_count<N>(rs, qr, g.err, v, pc);
     }
     add_count(count, v);
     add_count(count + 1, pc);
 }
 
-// ---------------------------------------------------------------- adjoint: ray-driven scatter (explicit rays)
+// ---------------------------------------------------------------- adjoint: ray-driven scatter
+template <int N>
+__device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float *__restrict__ c, const QuadRule &qr,
+                                            int *err)
+{
+    bool ok = true;
+#pragma unroll 1
+    for (int j = rs.j0; j <= rs.j1; ++j) {
+        AtomicSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], yr * rs.inv_wd};
+        ok &= slab_sweep<N>(rs, j, qr, sk);
+    }
+    if (!ok) atomicOr(err, 1);
+}
+
 template <int N>
 __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__restrict__ y, float *__restrict__ c,
                                                       QuadRule qr)
@@ -211,20 +219,29 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
     double s[3], w[3];
     explicit_ray(g, r, s, w);
     RaySetup rs;
-    if (!ray_setup<N>(grid_of(g), s, w, rs)) return;
-    bool ok = true;
-#pragma unroll 1
-    for (int j = rs.j0; j <= rs.j1; ++j) {
-        AtomicSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], yr * rs.inv_wd};
-        ok &= slab_sweep<N>(rs, j, qr, sk);
-    }
-    if (!ok) atomicOr(g.err, 1);
+    if (ray_setup<N>(grid_of(g), s, w, rs)) scatter_ray<N>(rs, yr, c, qr, g.err);
+}
+
+// view geometries, scatter form: the forward's thread mapping, float atomics
+template <int N>
+__global__ void __launch_bounds__(128) k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y,
+                                                               float *__restrict__ c, QuadRule qr)
+{
+    int iu, iv;
+    tile_pixel(iu, iv);
+    const int k = blockIdx.z;
+    if (iu >= g.nu || iv >= g.nv) return;
+    const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
+    if (yr == 0.0f) return;
+    RaySetup rs;
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N>(rs, yr, c, qr, g.err);
 }
 
 // ---------------------------------------------------------------- adjoint: brick gather (view geometries)
 constexpr int kBrick = 16;                        // brick edge (coefficients)
 constexpr int kBrickVol = kBrick * kBrick * kBrick;
 constexpr int kAdjThreads = 256;
+constexpr int kViewBatch = 8;                     // views per shared-memory fold
 
 // detector pixel window of the box [lo, hi] (world) for view k: projection
 // of its 8 corners (parallel: along the direction; cone: from the source)
@@ -271,13 +288,39 @@ __device__ __forceinline__ bool pixel_window(const DevGeom &g, int k, const doub
     return false;
 }
 
+// Clip the slab range [jlo, jhi] of a ray to the slabs whose window can
+// reach the brick's transverse bounds (conservative by one slab).
+__device__ __forceinline__ void clip_to_brick(const RaySetup &rs, int W2, const int (&blo)[3], const int (&bhi)[3],
+                                              int &jlo, int &jhi)
+{
+    const float A0 = rs.Ah + rs.Al, B0 = rs.Bh + rs.Bl;
+    const float base[2] = {A0, B0};
+    const float r[2] = {rs.ra, rs.rb}, ir[2] = {rs.inv_ra, rs.inv_rb};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        // window of slab j covers (A(j) - m, A(j) + m), A(j) = base + (j - j0) r
+        const float m = 0.5f * W2 * (1.0f + r[q]);
+        if (r[q] > 0.0f) {
+            const float jl = rs.j0 + (blo[q + 1] - m - base[q]) * ir[q];
+            const float jh = rs.j0 + (bhi[q + 1] + m - base[q]) * ir[q];
+            jlo = max(jlo, (int)fmaxf(floorf(jl) - 1.0f, -1e9f));
+            jhi = min(jhi, (int)fminf(ceilf(jh) + 1.0f, 1e9f));
+        } else if (!(base[q] + m > blo[q + 1] && base[q] - m < bhi[q + 1])) {
+            jhi = jlo - 1;
+        }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const float *__restrict__ y,
                                                                 float *__restrict__ c, QuadRule qr, int bx, int by)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    double *tot = (double *)smem;                       // kBrickVol FP64 totals
-    float *part = (float *)(smem + kBrickVol * sizeof(double));  // kBrickVol per-view partials
+    double *tot = (double *)smem;                                // kBrickVol FP64 totals
+    float *part = (float *)(smem + kBrickVol * sizeof(double));  // kBrickVol partials of a view batch
+    __shared__ int win[kViewBatch][3];                           // u0, wu, v0 of each view of the batch
+    __shared__ int woff[kViewBatch + 1];                         // prefix sums of the window sizes
+    __shared__ int next_item;
     constexpr double W = 0.5 * (N + 1);
     const int bid = blockIdx.x;
     const int b0[3] = {(bid % bx) * kBrick, ((bid / bx) % by) * kBrick, (bid / (bx * by)) * kBrick};
@@ -298,25 +341,42 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
     const GridBox gb = grid_of(g);
     const int lstride[3] = {1, kBrick, kBrick * kBrick};
     bool ok = true;
-    __syncthreads();
-    for (int k = 0; k < g.n_views; ++k) {
-        int u0, u1, v0, v1;
-        if (pixel_window(g, k, lo, hi, u0, u1, v0, v1)) {
-            u0 = 0;
-            u1 = g.nu - 1;
-            v0 = 0;
-            v1 = g.nv - 1;
+    for (int k0 = 0; k0 < g.n_views; k0 += kViewBatch) {
+        const int nb = min(kViewBatch, g.n_views - k0);
+        if (threadIdx.x < nb) {
+            int u0, u1, v0, v1;
+            if (pixel_window(g, k0 + threadIdx.x, lo, hi, u0, u1, v0, v1)) {
+                u0 = 0;
+                u1 = g.nu - 1;
+                v0 = 0;
+                v1 = g.nv - 1;
+            }
+            const int wu = u1 - u0 + 1, wv = v1 - v0 + 1;
+            win[threadIdx.x][0] = u0;
+            win[threadIdx.x][1] = wu > 0 ? wu : 0;
+            win[threadIdx.x][2] = v0;
+            woff[threadIdx.x + 1] = (wu > 0 && wv > 0) ? wu * wv : 0;
         }
-        const int wu = u1 - u0 + 1, wv = v1 - v0 + 1;
-        const int npix = (wu > 0 && wv > 0) ? wu * wv : 0;
-        for (int p = threadIdx.x; p < npix; p += kAdjThreads) {
-            const int iu = u0 + p % wu, iv = v0 + p / wu;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            woff[0] = 0;
+            for (int t = 1; t <= nb; ++t) woff[t] += woff[t - 1];
+            next_item = 0;
+        }
+        __syncthreads();
+        const int total = woff[nb];
+        // rays are taken one at a time from a shared counter: their costs
+        // differ a lot (a ray may cross one slab of the brick or sixteen)
+        for (int item = atomicAdd(&next_item, 1); item < total; item = atomicAdd(&next_item, 1)) {
+            int t = 0;
+            while (item >= woff[t + 1]) ++t;
+            const int p = item - woff[t];
+            const int iu = win[t][0] + p % win[t][1], iv = win[t][2] + p / win[t][1];
+            const int k = k0 + t;
             const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
             if (yr == 0.0f) continue;
-            double s[3], w[3];
-            view_ray(g, k, iu, iv, s, w);
             RaySetup rs;
-            if (!ray_setup<N>(gb, s, w, rs)) continue;
+            if (!view_setup<N>(g, gb, k, iu, iv, rs)) continue;
             // brick bounds in the ray's mirrored (d, a, b) coordinates
             int blo[3], bhi[3], L[3], Loff = 0;
 #pragma unroll
@@ -328,7 +388,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
                 L[q] = rs.sg[q] * lstride[e];
                 Loff -= b0[e] * lstride[e];
             }
-            const int jlo = max(rs.j0, blo[0]), jhi = min(rs.j1, bhi[0]);
+            int jlo = max(rs.j0, blo[0]), jhi = min(rs.j1, bhi[0]);
+            clip_to_brick(rs, N + 1, blo, bhi, jlo, jhi);
             const float yv = yr * rs.inv_wd;
 #pragma unroll 1
             for (int j = jlo; j <= jhi; ++j) {
@@ -379,16 +440,21 @@ static spl_status forward_quad(const spl_geometry *g, const float *c, float *y, 
 }
 
 template <int N>
-static spl_status adjoint_quad(const spl_geometry *g, const float *y, float *c, cudaStream_t st)
+static spl_status adjoint_quad(const spl_geometry *g, const float *y, float *c, cudaStream_t st, int form)
 {
     const DevGeom &dg = g->dev;
     const QuadRule qr = quad_rule(N);
     const long long nc = (long long)dg.n[0] * dg.n[1] * dg.n[2];
-    if (dg.kind == SPL_RAYS) {
+    if (dg.kind == SPL_RAYS || form == SPL_ADJ_SCATTER) {
         spl_status s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
         if (s != SPL_OK || dg.n_rays == 0) return s;
-        const long long blocks = (dg.n_rays + 127) / 128;
-        k_adjoint_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, y, c, qr);
+        if (dg.kind == SPL_RAYS) {
+            const long long blocks = (dg.n_rays + 127) / 128;
+            k_adjoint_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, y, c, qr);
+        } else {
+            dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
+            k_adjoint_views_scatter<N><<<grid, 128, 0, st>>>(dg, y, c, qr);
+        }
         return launch_status("adjoint launch");
     }
     static bool attr_set[4] = {false, false, false, false};
@@ -464,7 +530,9 @@ extern "C" spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *b
     if (s != SPL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (b->mode == SPL_FP_MLP) return spl::adjoint_mlp(g, b, y_dev, c_dev, st);
-    SPL_DISPATCH(b->degree, adjoint_quad, g, y_dev, c_dev, st)
+    if (b->adjoint != SPL_ADJ_GATHER && b->adjoint != SPL_ADJ_SCATTER)
+        return fail(SPL_ERR_ARG, "unknown adjoint form %d", b->adjoint);
+    SPL_DISPATCH(b->degree, adjoint_quad, g, y_dev, c_dev, st, b->adjoint)
 }
 
 extern "C" spl_status spl_count_pairs(const spl_geometry *g, int degree, unsigned long long *count_dev, void *stream)

@@ -52,6 +52,54 @@ struct QuadRule {
     int cap;             // loop bound of one slab sweep (kSlabIterCap)
 };
 
+// Direction-dependent part of the set-up (Definition 2.1 and the mirrored
+// frame).  Parallel views share one per view (computed once on the host),
+// other rays compute their own; the same function serves both so a ray gets
+// the same values wherever it is set up.
+struct DirSetup {
+    int ax[3];          // axis index of (d, a, b): dominant axis, then the others ascending
+    int sg[3];          // mirror sign of (d, a, b)
+    double r[2];        // |w_a|/|w_d|, |w_b|/|w_d| in [0, 1]
+    double invr[2];     // 1 / r (0 when r == 0)
+    float ra, rb, inv_ra, inv_rb, inv_wd;
+    float rah, ral, rbh, rbl;  // r as double-float pairs
+};
+
+__host__ __device__ inline void dir_setup(const double (&w)[3], DirSetup &ds)
+{
+    double wp[3];
+    int sg[3];
+    for (int e = 0; e < 3; ++e) {
+        sg[e] = (w[e] < 0.0) ? -1 : 1;
+        wp[e] = w[e] < 0.0 ? -w[e] : w[e];
+    }
+    int d = 0;
+    if (wp[1] > wp[d]) d = 1;
+    if (wp[2] > wp[d]) d = 2;
+    const int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+    ds.ax[0] = d;
+    ds.ax[1] = a;
+    ds.ax[2] = b;
+    ds.sg[0] = sg[d];
+    ds.sg[1] = sg[a];
+    ds.sg[2] = sg[b];
+    const double iwd = 1.0 / wp[d];
+    const double ra = wp[a] * iwd, rb = wp[b] * iwd;
+    ds.r[0] = ra;
+    ds.r[1] = rb;
+    ds.invr[0] = ra > 0.0 ? 1.0 / ra : 0.0;
+    ds.invr[1] = rb > 0.0 ? 1.0 / rb : 0.0;
+    ds.rah = (float)ra;
+    ds.ral = (float)(ra - (double)ds.rah);
+    ds.rbh = (float)rb;
+    ds.rbl = (float)(rb - (double)ds.rbh);
+    ds.ra = ds.rah;
+    ds.rb = ds.rbh;
+    ds.inv_ra = ra > 0.0 ? (float)ds.invr[0] : INFINITY;
+    ds.inv_rb = rb > 0.0 ? (float)ds.invr[1] : INFINITY;
+    ds.inv_wd = (float)iwd;
+}
+
 // Per-view pose in FP64 (one entry per view of a view geometry).
 struct ViewPose {
     double src[3];       // parallel: unit ray direction; cone: source position
@@ -59,6 +107,7 @@ struct ViewPose {
     double du[3], dv[3]; // detector axes (include the pixel pitch)
     double nrm[3];       // unit normal of the detector plane
     double ud[3], vd[3]; // dual axes: a = <P - dc, ud>, b = <P - dc, vd> for P on the plane
+    DirSetup dir;        // parallel views: direction set-up shared by all rays of the view
 };
 
 struct DevGeom {
@@ -190,47 +239,33 @@ struct RaySetup {
     float rah, ral, rbh, rbl;
 };
 
-// Ray in world coordinates -> slab-march set-up.  Returns false when the
-// ray meets no basis support of the grid.  Pure FP64, shared by every kernel
-// so that all of them enumerate the same pairs with the same values.
+// Position-dependent part: slab range of the ray and its transverse
+// coordinates on the reference slab.  Returns false when the ray meets no
+// basis support of the grid.  FP64, a few dozen operations.
 template <int N>
-__device__ __forceinline__ bool ray_setup(const GridBox &gb, const double (&s)[3], const double (&w)[3], RaySetup &rs)
+__device__ __forceinline__ bool pos_setup(const GridBox &gb, const DirSetup &ds, const double (&s)[3], RaySetup &rs)
 {
     constexpr double W = 0.5 * (N + 1);
-    double sp[3], wp[3];
-    int sg[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        sg[e] = (w[e] < 0.0) ? -1 : 1;
-        sp[e] = sg[e] * (s[e] - gb.org[e]);
-        wp[e] = fabs(w[e]);
-    }
-    int d = 0;
-    if (wp[1] > wp[d]) d = 1;
-    if (wp[2] > wp[d]) d = 2;
-    const int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
-    const int axs[3] = {d, a, b};
+    double sp[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const int e = axs[q];
+        const int e = ds.ax[q];
         rs.ax[q] = e;
-        rs.sg[q] = sg[e];
-        rs.lo[q] = sg[e] > 0 ? 0 : -(gb.n[e] - 1);
-        rs.hi[q] = sg[e] > 0 ? gb.n[e] - 1 : 0;
-        rs.S[q] = sg[e] * gb.stride[e];
+        rs.sg[q] = ds.sg[q];
+        rs.lo[q] = ds.sg[q] > 0 ? 0 : -(gb.n[e] - 1);
+        rs.hi[q] = ds.sg[q] > 0 ? gb.n[e] - 1 : 0;
+        rs.S[q] = ds.sg[q] * gb.stride[e];
+        sp[q] = ds.sg[q] * (s[e] - gb.org[e]);
     }
-    const double ra = wp[a] / wp[d], rb = wp[b] / wp[d];
     double jmin = rs.lo[0], jmax = rs.hi[0];
-    const double r2[2] = {ra, rb};
 #pragma unroll
     for (int q = 1; q < 3; ++q) {
-        const int e = axs[q];
-        const double r = r2[q - 1];
+        const double r = ds.r[q - 1];
         if (r > 0.0) {
             const double m = W * (1.0 + r);
-            jmin = fmax(jmin, sp[d] + (rs.lo[q] - m - sp[e]) / r);
-            jmax = fmin(jmax, sp[d] + (rs.hi[q] + m - sp[e]) / r);
-        } else if (!(sp[e] >= rs.lo[q] - W && sp[e] < rs.hi[q] + W)) {
+            jmin = fmax(jmin, fma(rs.lo[q] - m - sp[q], ds.invr[q - 1], sp[0]));
+            jmax = fmin(jmax, fma(rs.hi[q] + m - sp[q], ds.invr[q - 1], sp[0]));
+        } else if (!(sp[q] >= rs.lo[q] - W && sp[q] < rs.hi[q] + W)) {
             // constant transverse coordinate outside every support; the lower
             // end is inclusive for the half-open box of degree 0
             return false;
@@ -243,22 +278,33 @@ __device__ __forceinline__ bool ray_setup(const GridBox &gb, const double (&s)[3
     if (jl > jh) return false;
     rs.j0 = (int)jl;
     rs.j1 = (int)jh;
-    const double A = sp[a] + (rs.j0 - sp[d]) * ra;
-    const double B = sp[b] + (rs.j0 - sp[d]) * rb;
+    const double A = fma(rs.j0 - sp[0], ds.r[0], sp[1]);
+    const double B = fma(rs.j0 - sp[0], ds.r[1], sp[2]);
     rs.Ah = (float)A;
     rs.Al = (float)(A - (double)rs.Ah);
     rs.Bh = (float)B;
     rs.Bl = (float)(B - (double)rs.Bh);
-    rs.rah = (float)ra;
-    rs.ral = (float)(ra - (double)rs.rah);
-    rs.rbh = (float)rb;
-    rs.rbl = (float)(rb - (double)rs.rbh);
-    rs.ra = rs.rah;
-    rs.rb = rs.rbh;
-    rs.inv_ra = ra > 0.0 ? (float)(1.0 / ra) : INFINITY;
-    rs.inv_rb = rb > 0.0 ? (float)(1.0 / rb) : INFINITY;
-    rs.inv_wd = (float)(1.0 / wp[d]);
+    rs.rah = ds.rah;
+    rs.ral = ds.ral;
+    rs.rbh = ds.rbh;
+    rs.rbl = ds.rbl;
+    rs.ra = ds.ra;
+    rs.rb = ds.rb;
+    rs.inv_ra = ds.inv_ra;
+    rs.inv_rb = ds.inv_rb;
+    rs.inv_wd = ds.inv_wd;
     return true;
+}
+
+// Ray in world coordinates -> slab-march set-up (both parts).  Shared by
+// every kernel so that all of them enumerate the same pairs with the same
+// footprint values.
+template <int N>
+__device__ __forceinline__ bool ray_setup(const GridBox &gb, const double (&s)[3], const double (&w)[3], RaySetup &rs)
+{
+    DirSetup ds;
+    dir_setup(w, ds);
+    return pos_setup<N>(gb, ds, s, rs);
 }
 
 // A + k r as integer + fraction in [0, 1], with A and r double-floats:
@@ -407,6 +453,24 @@ __device__ __forceinline__ void view_ray(const DevGeom &g, int k, int iu, int iv
             w[e] = dd[e] / nrm;
         }
     }
+}
+
+// Set up pixel (iu, iv) of view k.  Parallel views take the per-view
+// direction set-up and only compute the pixel position; cone rays set up
+// their own direction.
+template <int N>
+__device__ __forceinline__ bool view_setup(const DevGeom &g, const GridBox &gb, int k, int iu, int iv, RaySetup &rs)
+{
+    double s[3], w[3];
+    if (g.kind == 1) {
+        const ViewPose &P = g.views[k];
+        const double a = iu - 0.5 * (g.nu - 1), b = iv - 0.5 * (g.nv - 1);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) s[e] = fma(b, P.dv[e], fma(a, P.du[e], P.dc[e]));
+        return pos_setup<N>(gb, P.dir, s, rs);
+    }
+    view_ray(g, k, iu, iv, s, w);
+    return ray_setup<N>(gb, s, w, rs);
 }
 
 __device__ __forceinline__ void explicit_ray(const DevGeom &g, long long r, double (&s)[3], double (&w)[3])

@@ -165,6 +165,30 @@ def test_adjoint_explicit_rays(env, orc, degree):
     assert rel_l2(c, cref) <= TOL, rel_l2(c, cref)
 
 
+@pytest.mark.parametrize("kind", ["parallel", "cone"])
+@pytest.mark.parametrize("degree", [1, 3])
+def test_adjoint_scatter_form(env, orc, kind, degree):
+    """The ray-driven scatter form of A^T gives the same result as the
+    gather form and the oracle."""
+    torch, spl = env
+    rng = np.random.default_rng(1550 + degree)
+    origin = I.centred_origin(DIMS)
+    geo = parallel_geometry(rng) if kind == "parallel" else cone_geometry()
+    y = rng.normal(size=geo.n_rays).astype(np.float32)
+    g = spl.Geometry(DIMS, origin, geo)
+    yt = torch.tensor(y, device="cuda")
+    cs = torch.full(g.coeff_shape, float("nan"), dtype=torch.float32, device="cuda")
+    cgat = torch.empty_like(cs)
+    spl.adjoint(g, yt, cs, spl.basis(degree, adjoint=spl.SPL_ADJ_SCATTER))
+    spl.adjoint(g, yt, cgat, spl.basis(degree, adjoint=spl.SPL_ADJ_GATHER))
+    g.status()
+    cref = orc.adjoint(degree, DIMS, origin, y.astype(np.float64), oracle_geom(orc, geo))
+    a = cs.cpu().numpy().astype(np.float64)
+    b = cgat.cpu().numpy().astype(np.float64)
+    assert rel_l2(a, cref) <= TOL and rel_l2(b, cref) <= TOL
+    assert rel_l2(a, b) <= 1e-6
+
+
 @pytest.mark.parametrize("kind", ["parallel", "cone", "rays"])
 def test_dot_product_adjointness(env, kind):
     """<A c, y> = <c, A^T y> for the GPU operators (FP32 arithmetic, FP64
