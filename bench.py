@@ -56,8 +56,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=3)
-    ap.add_argument("--adjoint", default="gather", choices=["gather", "scatter"],
-                    help="form of A^T: brick gather (deterministic) or ray-driven scatter (float atomics)")
+    ap.add_argument("--adjoint", default="scatter", choices=["gather", "scatter"],
+                    help="form of A^T: ray-driven scatter (float atomics, the library default) or brick gather")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU-baseline sample")
     return ap.parse_args()

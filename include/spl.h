@@ -57,10 +57,14 @@ typedef enum {
 enum { SPL_RAYS = 0, SPL_PARALLEL = 1, SPL_CONE = 2 };
 /* footprint evaluators: exact quadrature, or the learned f_theta (Sec. 2.2) */
 enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1 };
-/* adjoint forms for view geometries: brick gather (no global atomics,
- * deterministic) or ray-driven scatter (float atomics, order-dependent
- * rounding); both visit the same pairs with the same footprint values */
-enum { SPL_ADJ_GATHER = 0, SPL_ADJ_SCATTER = 1 };
+/* adjoint forms for view geometries: SPL_ADJ_AUTO picks the faster one on
+ * this GPU (the scatter form); SPL_ADJ_GATHER walks coefficient bricks and
+ * accumulates in shared memory (no global atomics); SPL_ADJ_SCATTER walks
+ * rays like spl_forward and adds with float atomics to global memory.  Both
+ * visit the same pairs with the same footprint values; both add in an
+ * order that varies between runs (float atomics in shared or global
+ * memory), so results agree to rounding, not bit for bit. */
+enum { SPL_ADJ_AUTO = 0, SPL_ADJ_GATHER = 1, SPL_ADJ_SCATTER = 2 };
 
 typedef struct spl_geometry spl_geometry; /* opaque, library-owned */
 typedef struct spl_mlp spl_mlp;           /* opaque, library-owned */
@@ -106,7 +110,7 @@ typedef struct {
     int mode;
     const spl_mlp *mlp;
     int kahan;
-    int adjoint;  /* SPL_ADJ_GATHER (0) or SPL_ADJ_SCATTER (1); view geometries only */
+    int adjoint;  /* SPL_ADJ_AUTO (0), SPL_ADJ_GATHER or SPL_ADJ_SCATTER; view geometries only */
 } spl_basis_desc;
 
 /* ---------------------------------------------------------------- geometry */
@@ -147,9 +151,10 @@ spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *basis, const
 /* Adjoint (back-projection) c = A^T y: the transpose of the matrix of Eq. 6,
  * matched exactly to spl_forward (Sec. 2.3): it visits the same
  * (ray, basis) pairs and evaluates bit-identical footprint values.  View
- * geometries use a gather form (one thread block per coefficient brick,
- * looping over views and the detector window of the brick; no global
- * atomics); explicit rays use a ray-driven scatter with float atomics.
+ * geometries use the form chosen by basis->adjoint (SPL_ADJ_*): a
+ * ray-driven scatter with float atomics (the default) or a gather over
+ * coefficient bricks that loops over views and the detector window of the
+ * brick (no global atomics); explicit rays always scatter.
  *   y_dev: n_rays float32 (read only);  c_dev: [nz][ny][nx] float32,
  *   overwritten.  Errors as spl_forward. */
 spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *basis, const float *y_dev, float *c_dev,

@@ -8,15 +8,19 @@
 // hits).  The slab partial sums are added along the ray with Kahan
 // compensation.
 //
-// Adjoint (view geometries): gather form, one block per 16^3 coefficient
-// brick.  For every view the block projects the brick's support box onto the
-// detector, walks the rays of that pixel window through the brick's slabs
-// with the same set-up and slab sweep as the forward (identical pairs and
-// footprint values), and accumulates y_r * P into shared memory; after each
-// view the per-view partials are folded into FP64 totals.  No global
-// atomics; each coefficient is written once.
-// Adjoint (explicit rays): no view structure to gather over, so a
-// ray-driven scatter with float atomics into a zeroed output.
+// Adjoint, view geometries, two forms that visit the same pairs with the
+// same footprint values:
+//  * scatter (default): the forward's thread mapping; each flushed
+//    contribution y_r * P is added to c with a float atomic (a
+//    fire-and-forget reduction in L2), which overlaps with the FP32 work --
+//    on GB300 A^T then costs about as much as A;
+//  * gather: one block per 16^3 coefficient brick; for every batch of 8
+//    views the block projects the brick's support box onto the detectors,
+//    walks the rays of those pixel windows through the brick's slabs with
+//    the same set-up and slab sweep, accumulates y_r * P in shared memory
+//    and folds the batch into FP64 totals; no global atomics, each
+//    coefficient written once.
+// Adjoint, explicit rays: no view structure to gather over: scatter.
 #include <stdio.h>
 
 #include "spl_host.h"
@@ -445,7 +449,7 @@ static spl_status adjoint_quad(const spl_geometry *g, const float *y, float *c, 
     const DevGeom &dg = g->dev;
     const QuadRule qr = quad_rule(N);
     const long long nc = (long long)dg.n[0] * dg.n[1] * dg.n[2];
-    if (dg.kind == SPL_RAYS || form == SPL_ADJ_SCATTER) {
+    if (dg.kind == SPL_RAYS || form != SPL_ADJ_GATHER) {
         spl_status s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
         if (s != SPL_OK || dg.n_rays == 0) return s;
         if (dg.kind == SPL_RAYS) {
@@ -530,7 +534,7 @@ extern "C" spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *b
     if (s != SPL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (b->mode == SPL_FP_MLP) return spl::adjoint_mlp(g, b, y_dev, c_dev, st);
-    if (b->adjoint != SPL_ADJ_GATHER && b->adjoint != SPL_ADJ_SCATTER)
+    if (b->adjoint != SPL_ADJ_AUTO && b->adjoint != SPL_ADJ_GATHER && b->adjoint != SPL_ADJ_SCATTER)
         return fail(SPL_ERR_ARG, "unknown adjoint form %d", b->adjoint);
     SPL_DISPATCH(b->degree, adjoint_quad, g, y_dev, c_dev, st, b->adjoint)
 }

@@ -335,7 +335,6 @@ __device__ __forceinline__ void integrate_piece(float x0, float x1, int id, floa
                                                 const QuadRule &qr, float (&acc)[N + 1][N + 1])
 {
     constexpr int M = GL<N>::M;
-    constexpr float W = 0.5f * (N + 1);
     const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
     float pc[N + 1], sgn, Kd;
     piece_coeffs<N>(id, pc, sgn, Kd);

@@ -17,7 +17,7 @@ from . import build as _build
 SPL_OK = 0
 SPL_RAYS, SPL_PARALLEL, SPL_CONE = 0, 1, 2
 SPL_FP_QUAD, SPL_FP_MLP = 0, 1
-SPL_ADJ_GATHER, SPL_ADJ_SCATTER = 0, 1
+SPL_ADJ_AUTO, SPL_ADJ_GATHER, SPL_ADJ_SCATTER = 0, 1, 2
 MLP_PARAMS = 8769
 STATUS_NAMES = {0: "SPL_OK", 1: "SPL_ERR_ARG", 2: "SPL_ERR_NONFINITE", 3: "SPL_ERR_CUDA", 4: "SPL_ERR_STEPCAP",
                 5: "SPL_ERR_OOM", 6: "SPL_ERR_STATE", 7: "SPL_ERR_UNSUPPORTED"}
@@ -196,7 +196,7 @@ class Geometry:
         check(lib().spl_geometry_status(self._h, _stream(stream)))
 
 
-def basis(degree: int, mode: int = SPL_FP_QUAD, mlp=None, kahan: bool = True, adjoint: int = SPL_ADJ_GATHER) -> BasisDesc:
+def basis(degree: int, mode: int = SPL_FP_QUAD, mlp=None, kahan: bool = True, adjoint: int = SPL_ADJ_AUTO) -> BasisDesc:
     b = BasisDesc()
     b.degree, b.mode, b.kahan, b.adjoint = int(degree), int(mode), 1 if kahan else 0, int(adjoint)
     b.mlp = mlp.handle if mlp is not None else None

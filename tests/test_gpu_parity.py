@@ -56,12 +56,12 @@ def gpu_forward(env, dims, origin, geo, c, degree, kahan=True):
     return y.cpu().numpy().astype(np.float64)
 
 
-def gpu_adjoint(env, dims, origin, geo, y, degree):
+def gpu_adjoint(env, dims, origin, geo, y, degree, form=0):
     torch, spl = env
     g = spl.Geometry(dims, origin, geo)
     yt = torch.tensor(np.asarray(y, dtype=np.float32), device="cuda")
     c = torch.full(g.coeff_shape, float("nan"), dtype=torch.float32, device="cuda")
-    spl.adjoint(g, yt, c, spl.basis(degree))
+    spl.adjoint(g, yt, c, spl.basis(degree, adjoint=form))
     g.status()
     return c.cpu().numpy().astype(np.float64)
 
@@ -131,13 +131,14 @@ def test_forward_explicit_rays(env, orc, degree):
     assert y[-1] == 0.0 and y[-2] == 0.0  # rays that miss the grid
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("degree", [0, 1, 2, 3])
-def test_adjoint_parallel(env, orc, degree):
+def test_adjoint_parallel(env, orc, degree, form):
     rng = np.random.default_rng(1300 + degree)
     origin = I.centred_origin(DIMS)
     geo = parallel_geometry(rng)
     y = rng.normal(size=geo.n_rays).astype(np.float32).astype(np.float64)
-    c = gpu_adjoint(env, DIMS, origin, geo, y, degree)
+    c = gpu_adjoint(env, DIMS, origin, geo, y, degree, form)
     cref = orc.adjoint(degree, DIMS, origin, y, oracle_geom(orc, geo))
     assert np.all(np.isfinite(c))
     assert rel_l2(c, cref) <= TOL, rel_l2(c, cref)

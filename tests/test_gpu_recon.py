@@ -53,7 +53,8 @@ def test_autograd_backward_is_adjoint(env, orc):
     loss = 0.5 * ((y - y_obs) ** 2).sum()
     loss.backward()
     direct = proj.adjoint((y - y_obs).detach())
-    assert torch.equal(c.grad, direct)
+    # same kernel; float atomics add in a run-dependent order
+    assert torch.allclose(c.grad, direct, rtol=1e-5, atol=1e-5 * float(direct.abs().max()))
     # oracle gradient A^T (A c - y)
     og = oracle_geom(orc, geo)
     c64 = c.detach().cpu().numpy().astype(np.float64)
@@ -66,7 +67,7 @@ def test_autograd_backward_is_adjoint(env, orc):
     cb = recon.backproject(yv, proj)
     w = torch.tensor(rng.normal(size=DIMS[::-1]).astype(np.float32), device="cuda")
     (cb * w).sum().backward()
-    assert torch.equal(yv.grad, proj.forward(w))
+    assert torch.equal(yv.grad, proj.forward(w))  # the forward is deterministic
 
 
 def test_loss_gradient_finite_difference(env):
