@@ -185,6 +185,17 @@ spl_status spl_features(int degree, long long count, const float *omega_dev, con
 
 /* ---------------------------------------------------------------- learned footprint (Sec. 2.2, Algorithm 1) */
 
+/* Training samples of Algorithm 1 from caller-drawn random numbers (the
+ * caller owns the generator): normals_dev [count][3] standard normal,
+ * uniforms_dev [count][2] in [0, 1).  Writes unit directions
+ * w = n/|n| (uniform on the sphere) to omega_dev [count][3] and offsets p,
+ * uniform in the disc of radius sqrt(3) W = sqrt(3)(n+1)/2 of H_w, to
+ * p_dev [count][3] (the disc contains the whole footprint support). */
+spl_status spl_footprint_samples(int degree, long long count, const float *normals_dev, const float *uniforms_dev,
+                                 float *omega_dev, float *p_dev, void *stream);
+
+
+
 /* The network is fixed: 5 -> 64 -> 64 -> 64 -> 1, SiLU after the three
  * hidden layers.  Parameters (float32 master copy) are laid out per layer as
  * W [out][in] row-major followed by b [out]; SPL_MLP_PARAMS values in all.

@@ -101,6 +101,8 @@ def _load():
             lib.orc_mlp_forward.argtypes = [C.c_int, _ip, _dp, C.c_longlong, _dp, _dp, C.c_int]
             lib.orc_mlp_loss_grad.restype = C.c_double
             lib.orc_mlp_loss_grad.argtypes = [C.c_int, _ip, _dp, C.c_longlong, _dp, _dp, _dp]
+            lib.orc_mlp_loss_grad_mode.restype = C.c_double
+            lib.orc_mlp_loss_grad_mode.argtypes = [C.c_int, _ip, _dp, C.c_longlong, _dp, _dp, _dp, C.c_int]
             lib.orc_features.argtypes = [C.c_int, _dp, _dp, _dp]
             lib.orc_forward_mlp.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_int, _ip, _dp, C.c_int, _dp]
             lib.orc_num_threads.restype = C.c_int
@@ -347,14 +349,17 @@ def mlp_forward(sizes, params, X, mode: int = 0):
     return out
 
 
-def mlp_loss_grad(sizes, params, X, Y):
-    """(L, dL/dparams) for L = mean (f_theta(x) - y)^2 (Algorithm 1's loss)."""
+def mlp_loss_grad(sizes, params, X, Y, mode: int = 0):
+    """(L, dL/dparams) for L = mean (f_theta(x) - y)^2 (Algorithm 1's loss);
+    mode 1 differentiates the BF16-contract forward (roundings passed
+    straight through)."""
     s, sp = _i(sizes)
     p, pp = _d(params)
     x, xp = _d(np.asarray(X).reshape(-1, sizes[0]))
     yy, yp = _d(np.asarray(Y).reshape(-1))
     g = np.zeros(p.shape[0])
-    loss = _load().orc_mlp_loss_grad(len(sizes) - 1, sp, pp, x.shape[0], xp, yp, g.ctypes.data_as(_dp))
+    loss = _load().orc_mlp_loss_grad_mode(len(sizes) - 1, sp, pp, x.shape[0], xp, yp, g.ctypes.data_as(_dp),
+                                          int(mode))
     return float(loss), g
 
 

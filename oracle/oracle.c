@@ -844,10 +844,21 @@ void orc_mlp_forward(int nl, const int *sizes, const double *prm, long long B, c
 }
 
 /* Gradient of L = (1/B) sum_b (f(x_b) - y_b)^2 with respect to all
- * parameters (same layout as prm), FP64 forward (mode 0) and backward.
- * Returns L. */
+ * parameters (same layout as prm), backward in FP64.  mode 0: FP64 forward.
+ * mode 1: the BF16-contract forward (act_mode 1); the backward then uses the
+ * rounded weights and the rounded activations that entered each layer, and
+ * passes gradients straight through the roundings.  Returns L. */
+double orc_mlp_loss_grad_mode(int nl, const int *sizes, const double *prm, long long B, const double *X,
+                              const double *Y, double *grad, int mode);
+
 double orc_mlp_loss_grad(int nl, const int *sizes, const double *prm, long long B, const double *X,
                          const double *Y, double *grad)
+{
+    return orc_mlp_loss_grad_mode(nl, sizes, prm, B, X, Y, grad, 0);
+}
+
+double orc_mlp_loss_grad_mode(int nl, const int *sizes, const double *prm, long long B, const double *X,
+                              const double *Y, double *grad, int mode)
 {
     long long np = orc_mlp_param_count(nl, sizes);
     memset(grad, 0, sizeof(double) * np);
@@ -866,7 +877,7 @@ double orc_mlp_loss_grad(int nl, const int *sizes, const double *prm, long long 
     for (long long b = 0; b < B; ++b) {
         const double *x = X + b * sizes[0];
         double f;
-        mlp_forward_one(nl, sizes, prm, x, 0, zs, hs, &f);
+        mlp_forward_one(nl, sizes, prm, x, mode, zs, hs, &f);
         double r = f - Y[b];
         loss += r * r;
         /* dL/dz of the output layer */
@@ -876,15 +887,22 @@ double orc_mlp_loss_grad(int nl, const int *sizes, const double *prm, long long 
             const double *Wl = prm + poff[li];
             double *gW = grad + poff[li], *gb = gW + (long long)no * ni;
             const double *hin = (li == 0) ? x : hs + aoff[li - 1];
+            const int tensor = (li > 0 && li < nl - 1);
             for (int o = 0; o < no; ++o) {
                 gb[o] += g[o];
-                for (int i = 0; i < ni; ++i) gW[(long long)o * ni + i] += g[o] * hin[i];
+                for (int i = 0; i < ni; ++i) {
+                    const double hv = (mode != 0 && tensor) ? act_round(hin[i], mode) : hin[i];
+                    gW[(long long)o * ni + i] += g[o] * hv;
+                }
             }
             if (li == 0) break;
             /* back through W then through SiLU of the previous layer */
             for (int i = 0; i < ni; ++i) {
                 double acc = 0.0;
-                for (int o = 0; o < no; ++o) acc += Wl[(long long)o * ni + i] * g[o];
+                for (int o = 0; o < no; ++o) {
+                    const double wv = mode != 0 ? bf16_round(Wl[(long long)o * ni + i]) : Wl[(long long)o * ni + i];
+                    acc += wv * g[o];
+                }
                 double z = zs[aoff[li - 1] + i];
                 double sg = 1.0 / (1.0 + exp(-z));
                 gn[i] = acc * sg * (1.0 + z * (1.0 - sg));

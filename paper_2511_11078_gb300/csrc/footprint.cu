@@ -13,6 +13,7 @@ namespace spl {
 struct PointSink {
     float v;
     __device__ __forceinline__ void piece() {}
+    __device__ __forceinline__ void slab(int, float, int, float) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a0 <= 0 && a1 >= 0 && b0 <= 0 && b1 >= 0;
@@ -86,6 +87,51 @@ __global__ void k_features(int degree, long long count, const float *__restrict_
     for (int e = 0; e < 5; ++e) feat[5 * i + e] = (float)f[e];
 }
 
+// Algorithm 1's training distribution from caller-drawn random numbers:
+// w = n / |n| (n standard normal: uniform on the sphere), p uniform in the
+// disc of radius sqrt(3) W of H_w: p = r (cos a u + sin a v) with
+// r = sqrt(3) W sqrt(u1), a = 2 pi u2 and (u, v) an orthonormal pair
+// perpendicular to w.
+__global__ void k_samples(int degree, long long count, const float *__restrict__ normals,
+                          const float *__restrict__ uniforms, float *__restrict__ omega, float *__restrict__ p)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double w[3];
+    double nrm = 0.0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        w[e] = normals[3 * i + e];
+        nrm += w[e] * w[e];
+    }
+    nrm = sqrt(nrm);
+    if (!(nrm > 0.0)) {
+        w[0] = 0.0;
+        w[1] = 0.0;
+        w[2] = 1.0;
+        nrm = 1.0;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) w[e] /= nrm;
+    }
+    // u = normalize(ref x w) with ref = e3 unless w is close to e3
+    const double ref[3] = {fabs(w[2]) < 0.9 ? 0.0 : 1.0, 0.0, fabs(w[2]) < 0.9 ? 1.0 : 0.0};
+    double u[3] = {ref[1] * w[2] - ref[2] * w[1], ref[2] * w[0] - ref[0] * w[2], ref[0] * w[1] - ref[1] * w[0]};
+    const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) u[e] /= un;
+    const double v[3] = {w[1] * u[2] - w[2] * u[1], w[2] * u[0] - w[0] * u[2], w[0] * u[1] - w[1] * u[0]};
+    const double W = 0.5 * (degree + 1);
+    const double r = sqrt(3.0) * W * sqrt((double)uniforms[2 * i]);
+    const double a = 6.283185307179586 * (double)uniforms[2 * i + 1];
+    const double ca = cos(a), sa = sin(a);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        omega[3 * i + e] = (float)w[e];
+        p[3 * i + e] = (float)(r * (ca * u[e] + sa * v[e]));
+    }
+}
+
 }  // namespace spl
 
 using namespace spl;
@@ -131,4 +177,18 @@ extern "C" spl_status spl_features(int degree, long long count, const float *ome
     const long long blocks = (count + 127) / 128;
     k_features<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(degree, count, omega_dev, p_dev, feat_dev);
     return cuda_check(cudaGetLastError(), "features launch");
+}
+
+extern "C" spl_status spl_footprint_samples(int degree, long long count, const float *normals_dev,
+                                            const float *uniforms_dev, float *omega_dev, float *p_dev, void *stream)
+{
+    clear_error();
+    if (degree < 0 || degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", degree);
+    if (count < 0) return fail(SPL_ERR_ARG, "bad count");
+    if (count == 0) return SPL_OK;
+    if (!normals_dev || !uniforms_dev || !omega_dev || !p_dev) return fail(SPL_ERR_ARG, "NULL array");
+    const long long blocks = (count + 127) / 128;
+    k_samples<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(degree, count, normals_dev, uniforms_dev, omega_dev,
+                                                                  p_dev);
+    return cuda_check(cudaGetLastError(), "samples launch");
 }

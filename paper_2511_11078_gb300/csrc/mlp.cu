@@ -1,46 +1,502 @@
-// mlp.cu -- learned footprint f_theta (Sec. 2.2, Algorithm 1).
+// mlp.cu -- the learned footprint f_theta (Sec. 2.2) and its training
+// (Algorithm 1): parameters, BF16 evaluation copy, batched evaluation on the
+// tensor cores, the MLP footprint of spl_footprint, gradients of the L2
+// loss and Adam.
+//
+// Training step (all kernels here, one stream, no host sync):
+//   k_train_forward  -- the inference tile (BF16 MMAs) on the batch, saving
+//                       pre-activations and the activations that entered
+//                       each layer;
+//   k_train_backward -- one thread per row: dL/dz of every layer (FP32, the
+//                       BF16 roundings passed straight through);
+//   k_train_wgrad    -- per batch chunk, dL/dW = sum_b dz_b x h_b^T and
+//                       dL/db (FP32), into fixed partial slots;
+//   k_train_reduce   -- adds the chunk partials in index order (deterministic)
+//                       and the loss;
+//   k_adam           -- Adam on the FP32 master copy, then k_prep refreshes
+//                       the BF16 evaluation copy.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
 #include "spl_mlp.cuh"
+
+namespace spl {
+
+constexpr int kEvalThreads = 128;  // 4 warps, one 16-row tile per warp at a time
+constexpr int kChunkRows = 256;    // rows per weight-gradient partial
+constexpr int kWgThreads = 256;
+
+}  // namespace spl
 
 struct spl_mlp {
     int degree;
+    int max_batch;
+    int device;
+    int step;
+    float *master;    // [kParams] FP32 master parameters
+    float *adam_m;    // [kParams]
+    float *adam_v;    // [kParams]
+    float *grad;      // [kParams]
+    uint32_t *w23;    // evaluation copy, BF16 hidden layers
+    float *f32;       // evaluation copy, FP32 first/last layers and biases
+    float *act;       // [6][max_batch][64] z1 h1 z2 h2 z3 h3
+    float *out;       // [max_batch] outputs
+    float *dz;        // [3][max_batch][64] dz1 dz2 dz3
+    float *dz4;       // [max_batch]
+    float *part;      // [chunks][kParams + 1] weight-gradient (and loss) partials
+    double *loss_part;  // [max_batch / 128 + 1] per-block loss partials
+    void *block;      // single device allocation holding all of the above
 };
 
 namespace spl {
-spl_status forward_mlp(const spl_geometry *, const spl_basis_desc *, const float *, float *, cudaStream_t)
-{
-    return fail(SPL_ERR_UNSUPPORTED, "MLP footprint not built yet");
-}
-spl_status adjoint_mlp(const spl_geometry *, const spl_basis_desc *, const float *, float *, cudaStream_t)
-{
-    return fail(SPL_ERR_UNSUPPORTED, "MLP footprint not built yet");
-}
-spl_status footprint_mlp(const spl_basis_desc *, long long, const float *, const float *, float *, cudaStream_t)
-{
-    return fail(SPL_ERR_UNSUPPORTED, "MLP footprint not built yet");
-}
-}  // namespace spl
 
-extern "C" int spl_mlp_degree(const spl_mlp *m) { return m ? m->degree : -1; }
+MlpDev mlp_dev(const spl_mlp *m)
+{
+    MlpDev d;
+    d.w23 = m->w23;
+    d.f32 = m->f32;
+    return d;
+}
+
+// ---------------------------------------------------------------- evaluation copy
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__global__ void k_prep(const float *__restrict__ P, uint32_t *__restrict__ w23, float *__restrict__ f32)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // hidden layers: rows of W2 / W3 as BF16 pairs, padded stride
+    if (i < 2 * kHid * kRowWords) {
+        const int layer = i / (kHid * kRowWords), rem = i % (kHid * kRowWords);
+        const int row = rem / kRowWords, w = rem % kRowWords;
+        const float *W = P + (layer == 0 ? kOffW2 : kOffW3);
+        uint32_t v = 0;
+        if (w < kHid / 2) v = pack_bf16(W[row * kHid + 2 * w], W[row * kHid + 2 * w + 1]);
+        w23[i] = v;
+    }
+    if (i < kF32Size) {
+        float v;
+        if (i < kF32B1) v = bf16r(P[kOffW1 + i]);
+        else if (i < kF32B2) v = P[kOffB1 + (i - kF32B1)];
+        else if (i < kF32B3) v = P[kOffB2 + (i - kF32B2)];
+        else if (i < kF32W4) v = P[kOffB3 + (i - kF32B3)];
+        else if (i < kF32B4) v = bf16r(P[kOffW4 + (i - kF32W4)]);
+        else v = P[kOffB4];
+        f32[i] = v;
+    }
+}
+
+static spl_status prep(spl_mlp *m, cudaStream_t st)
+{
+    const int n = 2 * kHid * kRowWords;
+    k_prep<<<(n + 255) / 256, 256, 0, st>>>(m->master, m->w23, m->f32);
+    return cuda_check(cudaGetLastError(), "mlp prep launch");
+}
+
+// ---------------------------------------------------------------- batched evaluation
+// FROM_WP: rows given as (omega, p) -> canonical features and the exact
+// support mask of the basis at the origin; otherwise rows are features.
+template <bool FROM_WP>
+__global__ void __launch_bounds__(kEvalThreads) k_mlp_rows(MlpDev w, int degree, long long count,
+                                                           const float *__restrict__ a, const float *__restrict__ b,
+                                                           float *__restrict__ out)
+{
+    __shared__ MlpSmem S;
+    mlp_load_smem(w, S);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long warps = (long long)gridDim.x * (kEvalThreads / 32);
+    const long long wid = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
+    const long long tiles = (count + 15) / 16;
+    for (long long tile = wid; tile < tiles; tile += warps) {
+        float x[2][5];
+        float mask[2] = {1.0f, 1.0f};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long r = tile * 16 + g + 8 * h;
+            if (r < count) {
+                if (FROM_WP) {
+                    double wv[3], pv[3], f[5];
+                    double nrm = 0.0;
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        wv[e] = a[3 * r + e];
+                        pv[e] = b[3 * r + e];
+                        nrm += wv[e] * wv[e];
+                    }
+                    nrm = sqrt(nrm);
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) wv[e] /= nrm;
+                    canonical_features(degree, wv, pv, f);
+#pragma unroll
+                    for (int e = 0; e < 5; ++e) x[h][e] = (float)f[e];
+                    // exact support: the line p + t w meets the open cube
+                    // [-W, W]^3 in a segment of positive length
+                    const double W = 0.5 * (degree + 1);
+                    double lo = -1e300, hi = 1e300;
+                    bool in = true;
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        if (wv[e] == 0.0) {
+                            in = in && (pv[e] >= -W && pv[e] < W) && (degree == 0 || pv[e] > -W);
+                        } else {
+                            const double t1 = (-W - pv[e]) / wv[e], t2 = (W - pv[e]) / wv[e];
+                            lo = fmax(lo, fmin(t1, t2));
+                            hi = fmin(hi, fmax(t1, t2));
+                        }
+                    }
+                    mask[h] = (in && hi > lo) ? 1.0f : 0.0f;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 5; ++e) x[h][e] = a[5 * r + e];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 5; ++e) x[h][e] = 0.0f;
+                mask[h] = 0.0f;
+            }
+        }
+        float o0, o1;
+        mlp_tile16<false>(S, x[0], x[1], o0, o1);
+        if (t == 0) {
+            const long long r0 = tile * 16 + g, r1 = r0 + 8;
+            if (r0 < count) out[r0] = o0 * mask[0];
+            if (r1 < count) out[r1] = o1 * mask[1];
+        }
+    }
+}
+
+static unsigned eval_blocks(long long count)
+{
+    const long long tiles = (count + 15) / 16;
+    const long long blocks = (tiles + 3) / 4;
+    return (unsigned)(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16);
+}
+
+spl_status footprint_mlp(const spl_basis_desc *b, long long count, const float *w, const float *p, float *out,
+                         cudaStream_t st)
+{
+    k_mlp_rows<true><<<eval_blocks(count), kEvalThreads, 0, st>>>(mlp_dev(b->mlp), b->degree, count, w, p, out);
+    return cuda_check(cudaGetLastError(), "mlp footprint launch");
+}
+
+// ---------------------------------------------------------------- training
+__global__ void __launch_bounds__(kEvalThreads) k_train_forward(MlpDev w, int B, const float *__restrict__ X,
+                                                                float *act, float *out, int max_batch)
+{
+    __shared__ MlpSmem S;
+    mlp_load_smem(w, S);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int warps = gridDim.x * (kEvalThreads / 32);
+    const int wid = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
+    const int tiles = (B + 15) / 16;
+    const size_t L = (size_t)max_batch * 64;
+    for (int tile = wid; tile < tiles; tile += warps) {
+        float x[2][5];
+        MlpSave sv{act, act + L, act + 2 * L, act + 3 * L, act + 4 * L, act + 5 * L, -1, -1};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = tile * 16 + g + 8 * h;
+#pragma unroll
+            for (int e = 0; e < 5; ++e) x[h][e] = r < B ? X[5 * r + e] : 0.0f;
+        }
+        // every lane of a quad saves its own columns of the quad's two rows
+        sv.row_g = tile * 16 + g < B ? tile * 16 + g : -1;
+        sv.row_g8 = tile * 16 + g + 8 < B ? tile * 16 + g + 8 : -1;
+        float o0, o1;
+        mlp_tile16<true>(S, x[0], x[1], o0, o1, &sv);
+        if (t == 0) {
+            if (sv.row_g >= 0) out[sv.row_g] = o0;
+            if (sv.row_g8 >= 0) out[sv.row_g8] = o1;
+        }
+    }
+}
+
+__device__ __forceinline__ float silu_grad(float z)
+{
+    const float s = 1.0f / (1.0f + expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// dL/dz of every layer for L = (1/B) sum (f(x_b) - y_b)^2; one thread per row.
+// Weights as used in the forward (BF16-rounded) come from the FP32 master
+// rounded on the fly; roundings of activations pass straight through.
+__global__ void __launch_bounds__(128) k_train_backward(const float *__restrict__ P, int B,
+                                                        const float *__restrict__ Y, const float *__restrict__ act,
+                                                        const float *__restrict__ out, float *dz, float *dz4,
+                                                        double *loss_part, int max_batch)
+{
+    __shared__ float W2[kHid * kHid], W3[kHid * kHid], W4[kHid];
+    __shared__ double red[4];
+    for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
+        W2[i] = bf16r(P[kOffW2 + i]);
+        W3[i] = bf16r(P[kOffW3 + i]);
+    }
+    if (threadIdx.x < kHid) W4[threadIdx.x] = bf16r(P[kOffW4 + threadIdx.x]);
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t L = (size_t)max_batch * 64;
+    double l2 = 0.0;
+    if (r < B) {
+        const float res = out[r] - Y[r];
+        l2 = (double)res * res;
+        const float d4 = 2.0f * res / (float)B;
+        dz4[r] = d4;
+        const float *z1 = act + r * 64, *z2 = act + 2 * L + r * 64, *z3 = act + 4 * L + r * 64;
+        float *g1 = dz + r * 64, *g2 = dz + L + r * 64, *g3 = dz + 2 * L + r * 64;
+        for (int c = 0; c < kHid; ++c) g3[c] = W4[c] * d4 * silu_grad(z3[c]);
+        for (int i = 0; i < kHid; ++i) {
+            float acc = 0.0f;
+            for (int c = 0; c < kHid; ++c) acc = fmaf(W3[c * kHid + i], g3[c], acc);
+            g2[i] = acc * silu_grad(z2[i]);
+        }
+        for (int i = 0; i < kHid; ++i) {
+            float acc = 0.0f;
+            for (int c = 0; c < kHid; ++c) acc = fmaf(W2[c * kHid + i], g2[c], acc);
+            g1[i] = acc * silu_grad(z1[i]);
+        }
+    }
+    // per-block loss partial (fixed order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l2 += __shfl_down_sync(0xffffffffu, l2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
+    __syncthreads();
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+// Weight gradients of one batch chunk: block (chunk, layer); each thread
+// owns a fixed set of (out, in) entries and sums the chunk's rows in order.
+__global__ void __launch_bounds__(kWgThreads) k_train_wgrad(int B, const float *__restrict__ X,
+                                                            const float *__restrict__ act,
+                                                            const float *__restrict__ dz,
+                                                            const float *__restrict__ dz4, float *part, int max_batch)
+{
+    const int chunk = blockIdx.x, layer = blockIdx.y;
+    const size_t L = (size_t)max_batch * 64;
+    const int r0 = chunk * kChunkRows, r1 = min(B, r0 + kChunkRows);
+    float *dst = part + (size_t)chunk * (kParams + 1);
+    // geometry of the layer: in-dim, out-dim, inputs, output grads, offsets
+    int nin, nout, offW, offB, hstride;
+    const float *H, *G;
+    int gstride;
+    if (layer == 0) { nin = kIn; nout = kHid; H = X; hstride = kIn; G = dz; gstride = 64; offW = kOffW1; offB = kOffB1; }
+    else if (layer == 1) { nin = kHid; nout = kHid; H = act + L; hstride = 64; G = dz + L; gstride = 64; offW = kOffW2; offB = kOffB2; }
+    else if (layer == 2) { nin = kHid; nout = kHid; H = act + 3 * L; hstride = 64; G = dz + 2 * L; gstride = 64; offW = kOffW3; offB = kOffB3; }
+    else { nin = kHid; nout = 1; H = act + 5 * L; hstride = 64; G = dz4; gstride = 1; offW = kOffW4; offB = kOffB4; }
+    const int nw = nin * nout;
+    for (int e = threadIdx.x; e < nw + nout; e += blockDim.x) {
+        float acc = 0.0f;
+        if (e < nw) {
+            const int o = e / nin, i = e % nin;
+            for (int r = r0; r < r1; ++r) acc = fmaf(G[(size_t)r * gstride + o], H[(size_t)r * hstride + i], acc);
+            dst[offW + e] = acc;
+        } else {
+            const int o = e - nw;
+            for (int r = r0; r < r1; ++r) acc += G[(size_t)r * gstride + o];
+            dst[offB + o] = acc;
+        }
+    }
+}
+
+__global__ void k_train_reduce(const float *__restrict__ part, int chunks, const double *__restrict__ loss_part,
+                               int nloss, int B, float *grad, float *loss_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kParams) {
+        float acc = 0.0f;
+        for (int c = 0; c < chunks; ++c) acc += part[(size_t)c * (kParams + 1) + i];
+        grad[i] = acc;
+    }
+    if (i == 0 && loss_out) {
+        double l = 0.0;
+        for (int k = 0; k < nloss; ++k) l += loss_part[k];
+        loss_out[0] = (float)(l / (double)B);
+    }
+}
+
+__global__ void k_adam(float *P, float *m, float *v, const float *__restrict__ g, float lr, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kParams) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+static spl_status grad_impl(spl_mlp *m, int B, const float *X, const float *Y, float *grad, float *loss,
+                            cudaStream_t st)
+{
+    const MlpDev w = mlp_dev(m);
+    const int tiles = (B + 15) / 16;
+    const int fblocks = (tiles + 3) / 4;
+    k_train_forward<<<fblocks, kEvalThreads, 0, st>>>(w, B, X, m->act, m->out, m->max_batch);
+    const int bblocks = (B + 127) / 128;
+    k_train_backward<<<bblocks, 128, 0, st>>>(m->master, B, Y, m->act, m->out, m->dz, m->dz4, m->loss_part,
+                                              m->max_batch);
+    const int chunks = (B + kChunkRows - 1) / kChunkRows;
+    k_train_wgrad<<<dim3(chunks, 4), kWgThreads, 0, st>>>(B, X, m->act, m->dz, m->dz4, m->part, m->max_batch);
+    k_train_reduce<<<(kParams + 255) / 256, 256, 0, st>>>(m->part, chunks, m->loss_part, bblocks, B, grad, loss);
+    return cuda_check(cudaGetLastError(), "mlp gradient launch");
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): seeded initial parameters.
+static uint64_t splitmix64(uint64_t &x)
+{
+    uint64_t z = (x += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace spl
 
 using namespace spl;
 
-extern "C" spl_status spl_mlp_create(int, int, unsigned long long, spl_mlp **out)
+extern "C" int spl_mlp_degree(const spl_mlp *m) { return m ? m->degree : -1; }
+
+extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long long seed, spl_mlp **out)
 {
-    if (out) *out = nullptr;
-    return fail(SPL_ERR_UNSUPPORTED, "MLP footprint not built yet");
+    clear_error();
+    if (!out) return fail(SPL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (degree < 0 || degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", degree);
+    if (max_batch < 16 || max_batch > (1 << 22)) return fail(SPL_ERR_ARG, "max_batch %d not in 16..2^22", max_batch);
+    spl_mlp *m = (spl_mlp *)calloc(1, sizeof(spl_mlp));
+    if (!m) return fail(SPL_ERR_OOM, "host allocation failed");
+    m->degree = degree;
+    m->max_batch = max_batch;
+    cudaGetDevice(&m->device);
+    const int chunks = (max_batch + kChunkRows - 1) / kChunkRows;
+    const int nloss = (max_batch + 127) / 128;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_master = take(kParams * 4), o_m = take(kParams * 4), o_v = take(kParams * 4),
+                 o_grad = take(kParams * 4), o_w23 = take(2 * kHid * kRowWords * 4), o_f32 = take(kF32Size * 4),
+                 o_act = take((size_t)6 * max_batch * 64 * 4), o_out = take((size_t)max_batch * 4),
+                 o_dz = take((size_t)3 * max_batch * 64 * 4), o_dz4 = take((size_t)max_batch * 4),
+                 o_part = take((size_t)chunks * (kParams + 1) * 4), o_loss = take((size_t)nloss * 8);
+    void *blk = nullptr;
+    cudaError_t ce = cudaMalloc(&blk, off);
+    if (ce != cudaSuccess) {
+        free(m);
+        cudaGetLastError();
+        return fail(SPL_ERR_OOM, "cudaMalloc(%zu) failed: %s", off, cudaGetErrorString(ce));
+    }
+    char *base = (char *)blk;
+    m->block = blk;
+    m->master = (float *)(base + o_master);
+    m->adam_m = (float *)(base + o_m);
+    m->adam_v = (float *)(base + o_v);
+    m->grad = (float *)(base + o_grad);
+    m->w23 = (uint32_t *)(base + o_w23);
+    m->f32 = (float *)(base + o_f32);
+    m->act = (float *)(base + o_act);
+    m->out = (float *)(base + o_out);
+    m->dz = (float *)(base + o_dz);
+    m->dz4 = (float *)(base + o_dz4);
+    m->part = (float *)(base + o_part);
+    m->loss_part = (double *)(base + o_loss);
+    // seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for weights and biases
+    float *h = (float *)malloc(kParams * sizeof(float));
+    if (!h) { cudaFree(blk); free(m); return fail(SPL_ERR_OOM, "host allocation failed"); }
+    uint64_t st = seed;
+    const int fan_in[4] = {kIn, kHid, kHid, kHid};
+    const int offs[5] = {0, kOffW2, kOffW3, kOffW4, kParams};
+    for (int layer = 0; layer < 4; ++layer) {
+        const float bound = 1.0f / sqrtf((float)fan_in[layer]);
+        for (int i = offs[layer]; i < offs[layer + 1]; ++i) {
+            const double u = (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+            h[i] = (float)((2.0 * u - 1.0) * bound);
+        }
+    }
+    spl_status s = spl_mlp_set_params(m, h);
+    free(h);
+    if (s != SPL_OK) {
+        cudaFree(blk);
+        free(m);
+        return s;
+    }
+    *out = m;
+    return SPL_OK;
 }
-extern "C" void spl_mlp_destroy(spl_mlp *) {}
-extern "C" spl_status spl_mlp_set_params(spl_mlp *, const float *) { return fail(SPL_ERR_UNSUPPORTED, "n/a"); }
-extern "C" spl_status spl_mlp_get_params(const spl_mlp *, float *) { return fail(SPL_ERR_UNSUPPORTED, "n/a"); }
-extern "C" spl_status spl_mlp_eval(const spl_mlp *, long long, const float *, float *, void *)
+
+extern "C" void spl_mlp_destroy(spl_mlp *m)
 {
-    return fail(SPL_ERR_UNSUPPORTED, "n/a");
+    if (!m) return;
+    if (m->block) cudaFree(m->block);
+    free(m);
 }
-extern "C" spl_status spl_mlp_grad(spl_mlp *, int, const float *, const float *, float *, float *, void *)
+
+extern "C" spl_status spl_mlp_set_params(spl_mlp *m, const float *host_params)
 {
-    return fail(SPL_ERR_UNSUPPORTED, "n/a");
+    clear_error();
+    if (!m || !host_params) return fail(SPL_ERR_ARG, "NULL argument");
+    for (int i = 0; i < kParams; ++i)
+        if (!isfinite(host_params[i])) return fail(SPL_ERR_NONFINITE, "parameter %d is not finite", i);
+    spl_status s = cuda_check(cudaMemcpy(m->master, host_params, kParams * 4, cudaMemcpyHostToDevice), "params upload");
+    if (s != SPL_OK) return s;
+    s = cuda_check(cudaMemset(m->adam_m, 0, kParams * 4), "adam reset");
+    if (s != SPL_OK) return s;
+    s = cuda_check(cudaMemset(m->adam_v, 0, kParams * 4), "adam reset");
+    if (s != SPL_OK) return s;
+    m->step = 0;
+    s = prep(m, 0);
+    if (s != SPL_OK) return s;
+    return cuda_check(cudaDeviceSynchronize(), "params prep");
 }
-extern "C" spl_status spl_mlp_train_step(spl_mlp *, int, const float *, const float *, float, float *, void *)
+
+extern "C" spl_status spl_mlp_get_params(const spl_mlp *m, float *host_params)
 {
-    return fail(SPL_ERR_UNSUPPORTED, "n/a");
+    clear_error();
+    if (!m || !host_params) return fail(SPL_ERR_ARG, "NULL argument");
+    return cuda_check(cudaMemcpy(host_params, m->master, kParams * 4, cudaMemcpyDeviceToHost), "params download");
+}
+
+extern "C" spl_status spl_mlp_eval(const spl_mlp *m, long long count, const float *feat_dev, float *out_dev,
+                                   void *stream)
+{
+    clear_error();
+    if (!m) return fail(SPL_ERR_ARG, "mlp is NULL");
+    if (count < 0) return fail(SPL_ERR_ARG, "bad count");
+    if (count == 0) return SPL_OK;
+    if (!feat_dev || !out_dev) return fail(SPL_ERR_ARG, "NULL array");
+    k_mlp_rows<false><<<eval_blocks(count), kEvalThreads, 0, (cudaStream_t)stream>>>(mlp_dev(m), m->degree, count,
+                                                                                      feat_dev, nullptr, out_dev);
+    return cuda_check(cudaGetLastError(), "mlp eval launch");
+}
+
+extern "C" spl_status spl_mlp_grad(spl_mlp *m, int batch, const float *feat_dev, const float *target_dev,
+                                   float *grad_dev, float *loss_dev, void *stream)
+{
+    clear_error();
+    if (!m || !feat_dev || !target_dev || !grad_dev) return fail(SPL_ERR_ARG, "NULL argument");
+    if (batch < 1 || batch > m->max_batch) return fail(SPL_ERR_ARG, "batch %d not in 1..%d", batch, m->max_batch);
+    return grad_impl(m, batch, feat_dev, target_dev, grad_dev, loss_dev, (cudaStream_t)stream);
+}
+
+extern "C" spl_status spl_mlp_train_step(spl_mlp *m, int batch, const float *feat_dev, const float *target_dev,
+                                         float lr, float *loss_dev, void *stream)
+{
+    clear_error();
+    if (!m || !feat_dev || !target_dev) return fail(SPL_ERR_ARG, "NULL argument");
+    if (batch < 1 || batch > m->max_batch) return fail(SPL_ERR_ARG, "batch %d not in 1..%d", batch, m->max_batch);
+    if (!(lr >= 0.0f) || !isfinite(lr)) return fail(SPL_ERR_ARG, "bad learning rate");
+    cudaStream_t st = (cudaStream_t)stream;
+    spl_status s = grad_impl(m, batch, feat_dev, target_dev, m->grad, loss_dev, st);
+    if (s != SPL_OK) return s;
+    m->step += 1;
+    const float c1 = 1.0f - powf(0.9f, (float)m->step), c2 = 1.0f - powf(0.999f, (float)m->step);
+    k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(m->master, m->adam_m, m->adam_v, m->grad, lr, c1, c2);
+    s = cuda_check(cudaGetLastError(), "adam launch");
+    if (s != SPL_OK) return s;
+    return prep(m, st);
 }

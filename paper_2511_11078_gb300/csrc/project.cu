@@ -35,6 +35,7 @@ struct FwdSink {
     int loa, hia, lob, hib;
     float acc;
     __device__ __forceinline__ void piece() {}
+    __device__ __forceinline__ void slab(int, float, int, float) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
@@ -50,6 +51,7 @@ struct CountSink {
     unsigned int n;       // bases with a nonzero footprint
     unsigned int pieces;  // integrated pieces (m Gauss nodes each)
     __device__ __forceinline__ void piece() { ++pieces; }
+    __device__ __forceinline__ void slab(int, float, int, float) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
@@ -66,6 +68,7 @@ struct AtomicSink {
     int loa, hia, lob, hib;
     float yv;
     __device__ __forceinline__ void piece() {}
+    __device__ __forceinline__ void slab(int, float, int, float) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
@@ -84,6 +87,7 @@ struct BrickSink {
     int loa, hia, lob, hib;
     float yv;
     __device__ __forceinline__ void piece() {}
+    __device__ __forceinline__ void slab(int, float, int, float) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;

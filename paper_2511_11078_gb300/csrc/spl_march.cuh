@@ -359,8 +359,12 @@ __device__ __forceinline__ void integrate_piece(float x0, float x1, int id, floa
 // crosses in this slab is handed to sink.flush(j, la, lb, F) exactly once,
 // with F = |w_d| * Pphi(w, s - l).  sink.relevant(...) tells whether any
 // basis of the current window matters (skips the nodes of pieces that
-// cannot reach the sink).  Returns false if the loop bound was reached.
-template <int N, class Sink>
+// cannot reach the sink); sink.slab(IA, fa, IB, fb) receives the ray's
+// transverse coordinates on the slab plane (A_j = IA + fa, B_j = IB + fb).
+// QUAD = false enumerates the pairs only: F = 1 for a basis whose support
+// the ray crosses with positive length, 0 otherwise (no quadrature).
+// Returns false if the loop bound was reached.
+template <int N, class Sink, bool QUAD = true>
 __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const QuadRule &qr, Sink &sink)
 {
     constexpr float W = 0.5f * (N + 1);
@@ -368,6 +372,7 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
     float fa, fb;
     df_coord(rs.Ah, rs.Al, rs.rah, rs.ral, j - rs.j0, IA, fa);
     df_coord(rs.Bh, rs.Bl, rs.rbh, rs.rbl, j - rs.j0, IB, fb);
+    sink.slab(IA, fa, IB, fb);
     const float Ca = fa + W, Cb = fb + W;
     int qa = (int)floorf(fmaf(-W, rs.ra, Ca));
     int qb = (int)floorf(fmaf(-W, rs.rb, Cb));
@@ -388,7 +393,14 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
         const float x1 = fmaxf(x1r, x0);
         const int la0 = IA + qa - N, lb0 = IB + qb - N;
         if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
-            integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
+            if constexpr (QUAD) {
+                integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
+            } else {
+#pragma unroll
+                for (int i = 0; i <= N; ++i)
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) acc[i][k] = 1.0f;
+            }
             sink.piece();
         }
         x0 = x1;

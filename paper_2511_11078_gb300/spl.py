@@ -62,6 +62,7 @@ _SIGS = {
     "spl_count_pairs": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "spl_footprint": (C.c_int, [C.POINTER(BasisDesc), C.c_longlong, _vp, _vp, _vp, _vp]),
     "spl_features": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp, _vp, _vp]),
+    "spl_footprint_samples": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
     "spl_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_ulonglong, C.POINTER(_vp)]),
     "spl_mlp_destroy": (None, [_vp]),
     "spl_mlp_degree": (C.c_int, [_vp]),
@@ -237,6 +238,59 @@ def footprint(bas: BasisDesc, omega, p, out, stream=None):
 
 def features(degree: int, omega, p, feat, stream=None):
     check(lib().spl_features(int(degree), omega.shape[0], _ptr(omega), _ptr(p), _ptr(feat), _stream(stream)))
+
+
+def footprint_samples(degree: int, normals, uniforms, omega, p, stream=None):
+    check(lib().spl_footprint_samples(int(degree), normals.shape[0], _ptr(normals), _ptr(uniforms), _ptr(omega),
+                                      _ptr(p), _stream(stream)))
+
+
+class Mlp:
+    """The learned footprint f_theta (spl_mlp): 5 -> 64 -> 64 -> 64 -> 1 SiLU."""
+
+    def __init__(self, degree: int, max_batch: int = 8192, seed: int = 0):
+        h = _vp()
+        check(lib().spl_mlp_create(int(degree), int(max_batch), C.c_ulonglong(int(seed)), C.byref(h)))
+        self._h = h
+        self.degree = int(degree)
+        self.max_batch = int(max_batch)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().spl_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        check(lib().spl_mlp_get_params(self._h, out.ctypes.data_as(_fp)))
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_PARAMS:
+            raise ValueError("need %d parameters" % MLP_PARAMS)
+        check(lib().spl_mlp_set_params(self._h, p.ctypes.data_as(_fp)))
+
+    def eval(self, feat, out, stream=None):
+        check(lib().spl_mlp_eval(self._h, feat.shape[0], _ptr(feat), _ptr(out), _stream(stream)))
+
+    def grad(self, feat, target, grad, loss=None, stream=None):
+        check(lib().spl_mlp_grad(self._h, feat.shape[0], _ptr(feat), _ptr(target), _ptr(grad), _ptr(loss),
+                                 _stream(stream)))
+
+    def train_step(self, feat, target, lr: float, loss=None, stream=None):
+        check(lib().spl_mlp_train_step(self._h, feat.shape[0], _ptr(feat), _ptr(target), C.c_float(lr), _ptr(loss),
+                                       _stream(stream)))
 
 
 def dot_workspace(device=None):
