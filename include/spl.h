@@ -179,7 +179,8 @@ spl_status spl_footprint(const spl_basis_desc *basis, long long count, const flo
  * G that maps w into the chamber 0 <= w1 <= w2 <= w3 (phi is invariant under
  * it), the frame u = normalize(e1 x Gw), v = u x Gw (Algorithm 2 fixes only
  * u perpendicular to w and v = u x w), and
- * (Gw1, Gw2, Gw3, <Gp,u>/(sqrt(3) W), <Gp,v>/(sqrt(3) W)), W = (n+1)/2. */
+ * (Gw1, Gw2, Gw3, <Gp,u> sqrt(3)/W, <Gp,v> sqrt(3)/W), W = (n+1)/2 (the
+ * sampling disc of radius sqrt(3) W maps to radius 3). */
 spl_status spl_features(int degree, long long count, const float *omega_dev, const float *p_dev, float *feat_dev,
                         void *stream);
 

@@ -920,7 +920,8 @@ double orc_mlp_loss_grad_mode(int nl, const int *sizes, const double *prm, long 
 /* the chamber 0 <= w1 <= w2 <= w3 (flip negative components, then sort      */
 /* ascending, stable).  Frame: u = normalize(e1 x w), v = u x w (Algorithm 2  */
 /* only fixes u perpendicular to w and v = u x w).  Features:                 */
-/* (w1, w2, w3, <Gp,u>/(sqrt(3) W), <Gp,v>/(sqrt(3) W)).                       */
+/* (w1, w2, w3, <Gp,u> sqrt(3)/W, <Gp,v> sqrt(3)/W): the sampling disc of     */
+/* radius sqrt(3) W maps to radius 3.                                         */
 /* ------------------------------------------------------------------------- */
 void orc_features(int n, const double *w_in, const double *p_in, double *feat)
 {
@@ -941,7 +942,7 @@ void orc_features(int n, const double *w_in, const double *p_in, double *feat)
     double nr = sqrt(w[1] * w[1] + w[2] * w[2]);
     double u[3] = {0.0, -w[2] / nr, w[1] / nr};
     double v[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
-    double sc = 1.0 / (sqrt(3.0) * W);
+    double sc = sqrt(3.0) / W;
     feat[0] = w[0]; feat[1] = w[1]; feat[2] = w[2];
     feat[3] = (p[0] * u[0] + p[1] * u[1] + p[2] * u[2]) * sc;
     feat[4] = (p[0] * v[0] + p[1] * v[1] + p[2] * v[2]) * sc;

@@ -22,7 +22,9 @@ constexpr int kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kHid;
 // MLP input features of (w, p): signed permutation G mapping w into the
 // chamber 0 <= w1 <= w2 <= w3 (phi is invariant under it, so
 // Pphi(Gw, Gp) = Pphi(w, p)), frame u = normalize(e1 x Gw), v = u x Gw, and
-// (Gw1, Gw2, Gw3, <Gp,u>/(sqrt3 W), <Gp,v>/(sqrt3 W)).  FP64.
+// (Gw1, Gw2, Gw3, <Gp,u> sqrt3/W, <Gp,v> sqrt3/W): the sampling disc of
+// radius sqrt3 W maps to radius 3, wide enough in feature space for the
+// footprint bump to be learned quickly.  FP64.
 __host__ __device__ inline void canonical_features(int degree, const double (&w_in)[3], const double (&p_in)[3],
                                                    double (&f)[5])
 {
@@ -46,7 +48,7 @@ __host__ __device__ inline void canonical_features(int degree, const double (&w_
     const double nr = sqrt(w[1] * w[1] + w[2] * w[2]);
     const double u[3] = {0.0, -w[2] / nr, w[1] / nr};
     const double v[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
-    const double sc = 1.0 / (sqrt(3.0) * W);
+    const double sc = sqrt(3.0) / W;
     f[0] = w[0];
     f[1] = w[1];
     f[2] = w[2];
@@ -286,7 +288,7 @@ __device__ __forceinline__ void mlp_ray_setup(int degree, const double (&w)[3], 
     const double nr = sqrt(w1 * w1 + w2 * w2);
     const double u[3] = {0.0, -w2 / nr, w1 / nr};
     const double v[3] = {u[1] * w2 - u[2] * w1, u[2] * w0 - u[0] * w2, u[0] * w1 - u[1] * w0};
-    const double sc = 1.0 / (sqrt(3.0) * W);
+    const double sc = sqrt(3.0) / W;
     int pos[3];
     for (int k = 0; k < 3; ++k) pos[ord[k]] = k;
     mr.wc[0] = (float)w0;

@@ -458,7 +458,7 @@ def test_features_invariance_and_frame(orc):
             np.testing.assert_allclose(np.sort(np.abs(w)), f[:3], atol=1e-15)
             # (u, v) components carry the projection of p on H_w
             pp = p - (p @ w) * w
-            assert abs((f[3] ** 2 + f[4] ** 2) * (3.0 * W * W) - pp @ pp) < 1e-12
+            assert abs((f[3] ** 2 + f[4] ** 2) * (W * W / 3.0) - pp @ pp) < 1e-12
             # invariant along w and under signed permutations
             np.testing.assert_allclose(orc.features(n, w, p + 3.3 * w), f, atol=1e-13)
             perm = rng.permutation(3)
