@@ -41,9 +41,14 @@ METRIC = "A/A^T G-contributions/s (exact quadrature footprint, one CGLS iteratio
 UNIT = "Gcontrib/s"
 WORKLOAD = "tilt-128^3-cubic-parallel-244x192^2"
 
-# FP32 arithmetic per Gauss node and per flushed contribution of the cubic
-# slab sweep ("roofline"): 86 FLOP / node, 2 FLOP / flush.
-FLOP_PER_NODE = {0: 12, 1: 26, 2: 52, 3: 86}
+# FP32 arithmetic per Gauss node of the slab sweep (node position, d-factor,
+# two sets of n+1 B-spline weights, node weight, scalings, (n+1)^2 outer
+# product) and per flushed contribution (one FMA).
+FLOP_PER_NODE = {0: 9, 1: 24, 2: 53, 3: 90}
+# flat rays (a zero direction component): n+1 nodes per piece, no b-weights
+# and an (n+1)-vector update per node; one extra multiply per flush
+FLOP_PER_FLAT_NODE = {0: 8, 1: 15, 2: 27, 3: 41}
+MLP_FLOP_PER_PAIR = 2 * (5 * 64 + 2 * 64 * 64 + 64)
 FLOP_PER_PAIR = 2
 NODES_PER_PIECE = {0: 1, 1: 2, 2: 4, 3: 5}
 SMS, FP32_LANES = 152, 128
@@ -59,6 +64,8 @@ def parse():
     ap.add_argument("--adjoint", default="scatter", choices=["gather", "scatter"],
                     help="form of A^T: ray-driven scatter (float atomics, the library default) or brick gather")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mlp-steps", type=int, default=10000,
+                    help="Adam steps of the learned footprint trained before the MLP measurement (0: skip it)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU-baseline sample")
     return ap.parse_args()
 
@@ -220,6 +227,55 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+# learned footprint: train f_theta (Algorithm 1), then time A and A^T with it
+# --------------------------------------------------------------------------
+def mlp_measure(args, wl, geom, c_true, y, pairs, proj, dev):
+    import torch
+
+    from paper_2511_11078_gb300 import learn, spl
+
+    n = args.degree
+    t0 = time.perf_counter()
+    data = learn.FootprintSet(n, 1 << 22, seed=31, device=dev)
+    val = learn.FootprintSet(n, 1 << 16, seed=32, device=dev)
+    mlp = spl.Mlp(n, max_batch=8192, seed=5)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    learn.train(mlp, data, steps=args.mlp_steps, batch=8192, lr0=3e-3, lr_min=1e-6)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    acc = learn.evaluate(mlp, val)
+    b = spl.basis(n, spl.SPL_FP_MLP, mlp)
+    yq = torch.empty_like(y)
+    ym = torch.empty_like(y)
+    cm = torch.empty_like(c_true)
+    cq = torch.empty_like(c_true)
+    proj.forward(c_true, out=yq)
+    spl.forward(geom, c_true, ym, b)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    spl.forward(geom, c_true, ym, b)
+    ev[1].record(stream)
+    spl.adjoint(geom, y, cm, b)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    geom.status()
+    a_ms, at_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    proj.adjoint(y, out=cq)
+    torch.cuda.synchronize()
+    return {"footprint": "f_theta 5-64-64-64-1 SiLU, BF16 weights/activations, FP32 accumulation (mma.sync)",
+            "A_ms": a_ms, "AT_ms": at_ms, "A_gcontrib_s": pairs / a_ms / 1e6, "AT_gcontrib_s": pairs / at_ms / 1e6,
+            "s_per_recon_iter_est": (a_ms + at_ms) / 1e3,
+            "tensor_tflops_A": pairs * MLP_FLOP_PER_PAIR / a_ms / 1e9,
+            "train_steps": args.mlp_steps, "train_batch": 8192, "train_samples": 1 << 22,
+            "train_s": t2 - t1, "dataset_s": t1 - t0,
+            "footprint_max_abs_over_peak": acc["max_abs_rel_peak"], "footprint_rms": acc["rms"],
+            "A_rel_l2_vs_exact": float((ym - yq).norm() / yq.norm()),
+            "AT_rel_l2_vs_exact": float((cm - cq).norm() / cq.norm())}
+
+
+# --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
 def run_ours(args):
@@ -252,7 +308,7 @@ def run_ours(args):
     gen.manual_seed(I.SEED_BASE + 2)
     sigma = 0.01 * float(y_clean.max())
     y = y_clean + sigma * torch.randn(y_clean.shape, generator=gen, device=dev)
-    pairs, pieces = spl.count_work(geom, n)
+    pairs, pieces, flat_pieces = spl.count_work(geom, n)
     geom.status()
 
     cg = CGLS(proj, y)
@@ -348,7 +404,8 @@ def run_ours(args):
     peaks = measured_peaks()
     max_mhz = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
     fp32_peak_tflops = SMS * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
-    flops_fwd = pieces * NODES_PER_PIECE[n] * FLOP_PER_NODE[n] + pairs * FLOP_PER_PAIR
+    flops_fwd = (pieces * NODES_PER_PIECE[n] * FLOP_PER_NODE[n] + flat_pieces * (n + 1) * FLOP_PER_FLAT_NODE[n]
+                 + pairs * FLOP_PER_PAIR)
     dominant = "k_forward_views" if fwd >= adj else (
         "k_adjoint_bricks" if args.adjoint == "gather" else "k_adjoint_views_scatter")
     dom_ms = max(fwd, adj)
@@ -365,7 +422,7 @@ def run_ours(args):
                        "adjoint": args.adjoint,
                        "coeffs": list(wl.dims), "views": wl.geometry.n_views, "detector": [wl.geometry.nu,
                                                                                           wl.geometry.nv],
-                       "contributions_per_A": pairs, "pieces_per_A": pieces,
+                       "contributions_per_A": pairs, "pieces_per_A": pieces, "flat_pieces_per_A": flat_pieces,
                        "l2": "256 MB buffer written between timed steps (outside the step events)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "s_per_recon_iter": ms / 1e3,
@@ -377,6 +434,9 @@ def run_ours(args):
             "clocks": clocks,
             "roofline": roofline,
             "wall_s_timed_region": t_wall}
+
+    if args.mlp_steps > 0:
+        line["mlp"] = mlp_measure(args, wl, geom, c_true, y, pairs, proj, dev)
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         wl.coeffs = wl.coeffs.astype(np.float64)

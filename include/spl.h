@@ -160,10 +160,12 @@ spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *basis, const
 spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *basis, const float *y_dev, float *c_dev,
                        void *stream);
 
-/* Work of one forward projection, added to count_dev (uint64 [2], device):
+/* Work of one forward projection, added to count_dev (uint64 [3], device):
  * count_dev[0] += number of (ray, basis) pairs with a nonzero footprint (the
- * contributions of Eq. 4); count_dev[1] += number of integrated pieces (each
- * one Gauss-Legendre rule of ceil((3n+1)/2) nodes). */
+ * contributions of Eq. 4); count_dev[1] += integrated pieces of rays with
+ * three nonzero direction components (one Gauss-Legendre rule of
+ * ceil((3n+1)/2) nodes each); count_dev[2] += pieces of rays with a zero
+ * component (n+1 nodes each: the third factor is constant along the ray). */
 spl_status spl_count_pairs(const spl_geometry *g, int degree, unsigned long long *count_dev, void *stream);
 
 /* Footprint Pphi(w, p) (Eq. 4's contribution) of the basis at the origin for

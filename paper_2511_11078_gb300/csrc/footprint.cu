@@ -43,7 +43,7 @@ __device__ __forceinline__ float footprint_exact(const double (&w)[3], const dou
     if (!ray_setup<N>(unit_box(), p, w, rs)) return 0.0f;
     PointSink sk{0.0f};
 #pragma unroll 1
-    for (int j = rs.j0; j <= rs.j1; ++j) slab_sweep<N>(rs, j, qr, sk);
+    for (int j = rs.j0; j <= rs.j1; ++j) sweep<N>(rs, j, qr, sk);
     return sk.v * rs.inv_wd;
 }
 

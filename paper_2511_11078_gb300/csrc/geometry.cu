@@ -73,6 +73,12 @@ static void init_rules()
             g_rules[n].x[q] = q < m ? (float)x[q] : 0.0f;
             g_rules[n].w[q] = q < m ? (float)w[q] : 0.0f;
         }
+        // n+1 nodes: exact for the degree-2n products of flat rays
+        legendre_rule(n + 1, x, w);
+        for (int q = 0; q < kMaxNodes; ++q) {
+            g_rules[n].x1[q] = q <= n ? (float)x[q] : 0.0f;
+            g_rules[n].w1[q] = q <= n ? (float)w[q] : 0.0f;
+        }
     }
 }
 

@@ -115,7 +115,7 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
 #pragma unroll 1
     for (int j = rs.j0; j <= rs.j1; ++j) {
         FwdSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0.0f};
-        ok &= slab_sweep<N>(rs, j, qr, sk);
+        ok &= sweep<N>(rs, j, qr, sk);
         const float v = sk.acc * rs.inv_wd;
         if (kahan) kahan_add(sum, comp, v);
         else sum += v;
@@ -155,15 +155,16 @@ __global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__
 // ---------------------------------------------------------------- pair count
 template <int N>
 __device__ __forceinline__ void march_count(const RaySetup &rs, const QuadRule &qr, int *err, unsigned int &pairs,
-                                            unsigned int &pieces)
+                                            unsigned int &pieces, unsigned int &flat_pieces)
 {
     CountSink sk{rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0u, 0u};
     bool ok = true;
 #pragma unroll 1
-    for (int j = rs.j0; j <= rs.j1; ++j) ok &= slab_sweep<N>(rs, j, qr, sk);
+    for (int j = rs.j0; j <= rs.j1; ++j) ok &= sweep<N>(rs, j, qr, sk);
     if (!ok) atomicOr(err, 1);
     pairs = sk.n;
-    pieces = sk.pieces;
+    pieces = rs.rb == 0.0f ? 0u : sk.pieces;
+    flat_pieces = rs.rb == 0.0f ? sk.pieces : 0u;
 }
 
 __device__ __forceinline__ void add_count(unsigned long long *count, unsigned int v)
@@ -180,26 +181,29 @@ __global__ void __launch_bounds__(128) k_count_views(DevGeom g, unsigned long lo
     int iu, iv;
     tile_pixel(iu, iv);
     const int k = blockIdx.z;
-    unsigned int v = 0, pc = 0;
+    unsigned int v = 0, pc = 0, pf = 0;
     RaySetup rs;
-    if (iu < g.nu && iv < g.nv && view_setup<N>(g, grid_of(g), k, iu, iv, rs)) march_count<N>(rs, qr, g.err, v, pc);
+    if (iu < g.nu && iv < g.nv && view_setup<N>(g, grid_of(g), k, iu, iv, rs))
+        march_count<N>(rs, qr, g.err, v, pc, pf);
     add_count(count, v);
     add_count(count + 1, pc);
+    add_count(count + 2, pf);
 }
 
 template <int N>
 __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long long *count, QuadRule qr)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned int v = 0, pc = 0;
+    unsigned int v = 0, pc = 0, pf = 0;
     if (r < g.n_rays) {
         double s[3], w[3];
         explicit_ray(g, r, s, w);
         RaySetup rs;
-        if (ray_setup<N>(grid_of(g), s, w, rs)) march_count<N>(rs, qr, g.err, v, pc);
+        if (ray_setup<N>(grid_of(g), s, w, rs)) march_count<N>(rs, qr, g.err, v, pc, pf);
     }
     add_count(count, v);
     add_count(count + 1, pc);
+    add_count(count + 2, pf);
 }
 
 // ---------------------------------------------------------------- adjoint: ray-driven scatter
@@ -211,7 +215,7 @@ __device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float 
 #pragma unroll 1
     for (int j = rs.j0; j <= rs.j1; ++j) {
         AtomicSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], yr * rs.inv_wd};
-        ok &= slab_sweep<N>(rs, j, qr, sk);
+        ok &= sweep<N>(rs, j, qr, sk);
     }
     if (!ok) atomicOr(err, 1);
 }
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
 #pragma unroll 1
             for (int j = jlo; j <= jhi; ++j) {
                 BrickSink sk{part, L[0], L[1], L[2], Loff, blo[1], bhi[1], blo[2], bhi[2], yv};
-                ok &= slab_sweep<N>(rs, j, qr, sk);
+                ok &= sweep<N>(rs, j, qr, sk);
             }
         }
         __syncthreads();

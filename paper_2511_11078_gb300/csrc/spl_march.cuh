@@ -47,9 +47,11 @@ constexpr int kMaxNodes = 8;
 constexpr int kSlabIterCap = 40;
 
 struct QuadRule {
-    float x[kMaxNodes];  // Gauss-Legendre nodes on [-1, 1]
-    float w[kMaxNodes];  // weights
-    int cap;             // loop bound of one slab sweep (kSlabIterCap)
+    float x[kMaxNodes];   // Gauss-Legendre nodes on [-1, 1], m = ceil((3n+1)/2) of them
+    float w[kMaxNodes];   // weights
+    float x1[kMaxNodes];  // the (n+1)-node rule: exact for degree 2n (flat rays, see slab_sweep)
+    float w1[kMaxNodes];
+    int cap;              // loop bound of one slab sweep (kSlabIterCap)
 };
 
 // Direction-dependent part of the set-up (Definition 2.1 and the mirrored
@@ -57,7 +59,7 @@ struct QuadRule {
 // other rays compute their own; the same function serves both so a ray gets
 // the same values wherever it is set up.
 struct DirSetup {
-    int ax[3];          // axis index of (d, a, b): dominant axis, then the others ascending
+    int ax[3];          // axis index of (d, a, b): dominant axis, then the others by decreasing |w|
     int sg[3];          // mirror sign of (d, a, b)
     double r[2];        // |w_a|/|w_d|, |w_b|/|w_d| in [0, 1]
     double invr[2];     // 1 / r (0 when r == 0)
@@ -76,7 +78,14 @@ __host__ __device__ inline void dir_setup(const double (&w)[3], DirSetup &ds)
     int d = 0;
     if (wp[1] > wp[d]) d = 1;
     if (wp[2] > wp[d]) d = 2;
-    const int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+    // transverse axes: a has the larger component (ties: lower index), so a
+    // ray with one zero component always has r_b = 0
+    int a = (d == 0) ? 1 : 0, b = (d == 2) ? 1 : 2;
+    if (wp[b] > wp[a]) {
+        const int tmp = a;
+        a = b;
+        b = tmp;
+    }
     ds.ax[0] = d;
     ds.ax[1] = a;
     ds.ax[2] = b;
@@ -355,6 +364,28 @@ __device__ __forceinline__ void integrate_piece(float x0, float x1, int id, floa
     }
 }
 
+// Flat ray (r_b = 0): the b-factor is constant along the ray, so only the
+// 1-D integrals G_i = int beta(xi) beta(A + r_a xi - l_a(i)) dxi (degree 2N,
+// N+1 nodes) are accumulated; F_ik = G_i * wb_k at the flush.
+template <int N>
+__device__ __forceinline__ void integrate_piece_flat(float x0, float x1, int id, float Ka, float ra,
+                                                     const QuadRule &qr, float (&G)[N + 1])
+{
+    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
+    float pc[N + 1], sgn, Kd;
+    piece_coeffs<N>(id, pc, sgn, Kd);
+#pragma unroll
+    for (int q = 0; q <= N; ++q) {
+        const float xi = fmaf(half, qr.x1[q], mid);
+        const float bd = horner<N>(pc, fmaf(sgn, xi, Kd));
+        float wa[N + 1];
+        bweights<N>(fmaf(ra, xi, Ka), wa);
+        const float cw = (half * qr.w1[q]) * bd;
+#pragma unroll
+        for (int i = 0; i <= N; ++i) G[i] = fmaf(cw, wa[i], G[i]);
+    }
+}
+
 // Sweep slab j of a ray: every basis l' = (j, la, lb) whose support the ray
 // crosses in this slab is handed to sink.flush(j, la, lb, F) exactly once,
 // with F = |w_d| * Pphi(w, s - l).  sink.relevant(...) tells whether any
@@ -364,7 +395,7 @@ __device__ __forceinline__ void integrate_piece(float x0, float x1, int id, floa
 // QUAD = false enumerates the pairs only: F = 1 for a basis whose support
 // the ray crosses with positive length, 0 otherwise (no quadrature).
 // Returns false if the loop bound was reached.
-template <int N, class Sink, bool QUAD = true>
+template <int N, class Sink, bool QUAD = true, bool FLAT = false>
 __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const QuadRule &qr, Sink &sink)
 {
     constexpr float W = 0.5f * (N + 1);
@@ -383,6 +414,9 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
     for (int i = 0; i <= N; ++i)
 #pragma unroll
         for (int k = 0; k <= N; ++k) acc[i][k] = 0.0f;
+    // flat ray: constant b-weights, G_i kept in acc[i][0]
+    float wb[N + 1];
+    if constexpr (FLAT) bweights<N>(Cb - (float)qb, wb);
     float x0 = -W;
     int id = 0;
 #pragma unroll 1
@@ -393,7 +427,14 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
         const float x1 = fmaxf(x1r, x0);
         const int la0 = IA + qa - N, lb0 = IB + qb - N;
         if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
-            if constexpr (QUAD) {
+            if constexpr (QUAD && FLAT) {
+                float G[N + 1];
+#pragma unroll
+                for (int i = 0; i <= N; ++i) G[i] = acc[i][0];
+                integrate_piece_flat<N>(x0, x1, id, Ca - (float)qa, rs.ra, qr, G);
+#pragma unroll
+                for (int i = 0; i <= N; ++i) acc[i][0] = G[i];
+            } else if constexpr (QUAD) {
                 integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
             } else {
 #pragma unroll
@@ -409,12 +450,13 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
 #pragma unroll
                 for (int i = 0; i <= N; ++i)
 #pragma unroll
-                    for (int k = 0; k <= N; ++k) sink.flush(j, la0 + i, lb0 + k, acc[i][k]);
+                    for (int k = 0; k <= N; ++k)
+                        sink.flush(j, la0 + i, lb0 + k, (QUAD && FLAT) ? acc[i][0] * wb[k] : acc[i][k]);
                 return true;
             }
         } else if (ev == 1) {
 #pragma unroll
-            for (int k = 0; k <= N; ++k) sink.flush(j, la0, lb0 + k, acc[0][k]);
+            for (int k = 0; k <= N; ++k) sink.flush(j, la0, lb0 + k, (QUAD && FLAT) ? acc[0][0] * wb[k] : acc[0][k]);
 #pragma unroll
             for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -437,6 +479,17 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
         }
     }
     return false;
+}
+
+// Quadrature sweep of slab j with the rule the ray needs: the flat rule when
+// the ray has a zero transverse component (r_b = 0), the full one otherwise.
+// Every kernel goes through here, so a ray gets the same footprint values in
+// the forward, the adjoint and the pair count.
+template <int N, class Sink>
+__device__ __forceinline__ bool sweep(const RaySetup &rs, int j, const QuadRule &qr, Sink &sink)
+{
+    if (rs.rb == 0.0f) return slab_sweep<N, Sink, true, true>(rs, j, qr, sink);
+    return slab_sweep<N, Sink, true, false>(rs, j, qr, sink);
 }
 
 // ------------------------------------------------------------------ rays of a geometry

@@ -217,14 +217,15 @@ def adjoint(geom: Geometry, y, c, bas: BasisDesc, stream=None):
 
 
 def count_work(geom: Geometry, degree: int, stream=None):
-    """(pairs, pieces) of one forward projection: contributions with a
-    nonzero footprint, and integrated pieces (Gauss rules)."""
+    """(pairs, pieces, flat_pieces) of one forward projection: contributions
+    with a nonzero footprint, integrated pieces with the full Gauss rule and
+    with the (n+1)-node rule of rays with a zero direction component."""
     import torch
 
-    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
     check(lib().spl_count_pairs(geom.handle, int(degree), _ptr(cnt), _stream(stream)))
     v = cnt.cpu().tolist()
-    return int(v[0]), int(v[1])
+    return int(v[0]), int(v[1]), int(v[2])
 
 
 def count_pairs(geom: Geometry, degree: int, stream=None) -> int:
