@@ -13,7 +13,7 @@ namespace spl {
 struct PointSink {
     float v;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float) {}
+    __device__ __forceinline__ void slab(int, float, int, float, int) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a0 <= 0 && a1 >= 0 && b0 <= 0 && b1 >= 0;

@@ -45,7 +45,7 @@ struct MlpQueueSink {
     int lane;
     bool adj;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int ia, float fa_, int ib, float fb_)
+    __device__ __forceinline__ void slab(int ia, float fa_, int ib, float fb_, int)
     {
         IA = ia;
         fa = fa_;

@@ -33,32 +33,40 @@ struct FwdSink {
     const float *__restrict__ c;
     int S0, S1, S2;
     int loa, hia, lob, hib;
+    bool in = false;  // every window of the current slab lies inside the bounds
     float acc;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float) {}
+    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
+    {
+        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
+    }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
     }
     __device__ __forceinline__ void flush(int j, int la, int lb, float v)
     {
-        if (la >= loa && la <= hia && lb >= lob && lb <= hib) acc = fmaf(__ldg(c + (j * S0 + la * S1 + lb * S2)), v, acc);
+        if (in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) acc = fmaf(__ldg(c + (j * S0 + la * S1 + lb * S2)), v, acc);
     }
 };
 
 struct CountSink {
     int loa, hia, lob, hib;
+    bool in = false;  // every window of the current slab lies inside the bounds
     unsigned int n;       // bases with a nonzero footprint
     unsigned int pieces;  // integrated pieces (m Gauss nodes each)
     __device__ __forceinline__ void piece() { ++pieces; }
-    __device__ __forceinline__ void slab(int, float, int, float) {}
+    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
+    {
+        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
+    }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
     }
     __device__ __forceinline__ void flush(int, int la, int lb, float v)
     {
-        n += (la >= loa && la <= hia && lb >= lob && lb <= hib && v > 0.0f) ? 1u : 0u;
+        n += ((in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) && v > 0.0f) ? 1u : 0u;
     }
 };
 
@@ -66,16 +74,20 @@ struct AtomicSink {
     float *__restrict__ c;
     int S0, S1, S2;
     int loa, hia, lob, hib;
+    bool in = false;  // every window of the current slab lies inside the bounds
     float yv;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float) {}
+    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
+    {
+        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
+    }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
     }
     __device__ __forceinline__ void flush(int j, int la, int lb, float v)
     {
-        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(c + (j * S0 + la * S1 + lb * S2), yv * v);
+        if (in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) atomicAdd(c + (j * S0 + la * S1 + lb * S2), yv * v);
     }
 };
 
@@ -85,16 +97,20 @@ struct BrickSink {
     float *part;
     int L0, L1, L2, Loff;
     int loa, hia, lob, hib;
+    bool in = false;  // every window of the current slab lies inside the bounds
     float yv;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float) {}
+    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
+    {
+        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
+    }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
     }
     __device__ __forceinline__ void flush(int j, int la, int lb, float v)
     {
-        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(part + (j * L0 + la * L1 + lb * L2 + Loff), yv * v);
+        if (in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) atomicAdd(part + (j * L0 + la * L1 + lb * L2 + Loff), yv * v);
     }
 };
 

@@ -390,8 +390,10 @@ __device__ __forceinline__ void integrate_piece_flat(float x0, float x1, int id,
 // crosses in this slab is handed to sink.flush(j, la, lb, F) exactly once,
 // with F = |w_d| * Pphi(w, s - l).  sink.relevant(...) tells whether any
 // basis of the current window matters (skips the nodes of pieces that
-// cannot reach the sink); sink.slab(IA, fa, IB, fb) receives the ray's
-// transverse coordinates on the slab plane (A_j = IA + fa, B_j = IB + fb).
+// cannot reach the sink); sink.slab(IA, fa, IB, fb, N) receives the ray's
+// transverse coordinates on the slab plane (A_j = IA + fa, B_j = IB + fb);
+// every window of the slab lies in la in [IA - N, IA + 2N + 4] (same for b),
+// which lets a sink skip its per-flush bounds checks on interior slabs.
 // QUAD = false enumerates the pairs only: F = 1 for a basis whose support
 // the ray crosses with positive length, 0 otherwise (no quadrature).
 // Returns false if the loop bound was reached.
@@ -403,10 +405,15 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
     float fa, fb;
     df_coord(rs.Ah, rs.Al, rs.rah, rs.ral, j - rs.j0, IA, fa);
     df_coord(rs.Bh, rs.Bl, rs.rbh, rs.rbl, j - rs.j0, IB, fb);
-    sink.slab(IA, fa, IB, fb);
+    sink.slab(IA, fa, IB, fb, N);
     const float Ca = fa + W, Cb = fb + W;
     int qa = (int)floorf(fmaf(-W, rs.ra, Ca));
     int qb = (int)floorf(fmaf(-W, rs.rb, Cb));
+    // r <= 1 moves a transverse coordinate by at most N+1 over the slab, so a
+    // window shifts at most N+3 times per axis (one extra for a start that
+    // rounds down); more is treated as a loop bound, which keeps every window
+    // inside [IA - N, IA + 2N + 4] (the range sinks rely on)
+    const int qa_lim = qa + N + 3, qb_lim = qb + N + 3;
     float na = rs.ra > 0.0f ? ((float)(qa + 1) - Ca) * rs.inv_ra : INFINITY;
     float nb = rs.rb > 0.0f ? ((float)(qb + 1) - Cb) * rs.inv_rb : INFINITY;
     float acc[N + 1][N + 1];
@@ -418,67 +425,75 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
     float wb[N + 1];
     if constexpr (FLAT) bweights<N>(Cb - (float)qb, wb);
     float x0 = -W;
-    int id = 0;
+    int it = 0;
+    // The slab's d-factor has N+1 polynomial pieces xi in [id - W, id + 1 - W);
+    // the loop over them is unrolled so each piece's polynomial is a
+    // compile-time constant; inside a d-piece the a- and b-knot crossings
+    // split it further (at most kSlabIterCap pieces in all).
+#pragma unroll
+    for (int id = 0; id <= N; ++id) {
+        const float xend = (float)(id + 1) - W;
 #pragma unroll 1
-    for (int it = 0; it < qr.cap; ++it) {
-        const float nd = (float)(id + 1) - W;
-        const float x1r = fminf(nd, fminf(na, nb));
-        const int ev = (x1r == nd) ? 0 : ((x1r == na) ? 1 : 2);
-        const float x1 = fmaxf(x1r, x0);
-        const int la0 = IA + qa - N, lb0 = IB + qb - N;
-        if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
-            if constexpr (QUAD && FLAT) {
-                float G[N + 1];
+        for (;;) {
+            if (++it > qr.cap) return false;
+            const float x1r = fminf(xend, fminf(na, nb));
+            const float x1 = fmaxf(x1r, x0);
+            const int la0 = IA + qa - N, lb0 = IB + qb - N;
+            if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
+                if constexpr (QUAD && FLAT) {
+                    float G[N + 1];
 #pragma unroll
-                for (int i = 0; i <= N; ++i) G[i] = acc[i][0];
-                integrate_piece_flat<N>(x0, x1, id, Ca - (float)qa, rs.ra, qr, G);
+                    for (int i = 0; i <= N; ++i) G[i] = acc[i][0];
+                    integrate_piece_flat<N>(x0, x1, id, Ca - (float)qa, rs.ra, qr, G);
 #pragma unroll
-                for (int i = 0; i <= N; ++i) acc[i][0] = G[i];
-            } else if constexpr (QUAD) {
-                integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
+                    for (int i = 0; i <= N; ++i) acc[i][0] = G[i];
+                } else if constexpr (QUAD) {
+                    integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
+                } else {
+#pragma unroll
+                    for (int i = 0; i <= N; ++i)
+#pragma unroll
+                        for (int k = 0; k <= N; ++k) acc[i][k] = 1.0f;
+                }
+                sink.piece();
+            }
+            x0 = x1;
+            if (x1r == xend) break;  // end of the d-piece (first among equal events)
+            if (x1r == na) {
+                // the lowest a-row leaves the ray's reach: flush it, shift
+#pragma unroll
+                for (int k = 0; k <= N; ++k)
+                    sink.flush(j, la0, lb0 + k, (QUAD && FLAT) ? acc[0][0] * wb[k] : acc[0][k]);
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) acc[i][k] = acc[i + 1][k];
+#pragma unroll
+                for (int k = 0; k <= N; ++k) acc[N][k] = 0.0f;
+                if (++qa > qa_lim) return false;
+                na = ((float)(qa + 1) - Ca) * rs.inv_ra;
             } else {
+                // the lowest b-column leaves
 #pragma unroll
-                for (int i = 0; i <= N; ++i)
+                for (int i = 0; i <= N; ++i) sink.flush(j, la0 + i, lb0, acc[i][0]);
 #pragma unroll
-                    for (int k = 0; k <= N; ++k) acc[i][k] = 1.0f;
+                for (int i = 0; i <= N; ++i) {
+#pragma unroll
+                    for (int k = 0; k < N; ++k) acc[i][k] = acc[i][k + 1];
+                    acc[i][N] = 0.0f;
+                }
+                if (++qb > qb_lim) return false;
+                nb = ((float)(qb + 1) - Cb) * rs.inv_rb;
             }
-            sink.piece();
-        }
-        x0 = x1;
-        if (ev == 0) {
-            if (++id > N) {
-#pragma unroll
-                for (int i = 0; i <= N; ++i)
-#pragma unroll
-                    for (int k = 0; k <= N; ++k)
-                        sink.flush(j, la0 + i, lb0 + k, (QUAD && FLAT) ? acc[i][0] * wb[k] : acc[i][k]);
-                return true;
-            }
-        } else if (ev == 1) {
-#pragma unroll
-            for (int k = 0; k <= N; ++k) sink.flush(j, la0, lb0 + k, (QUAD && FLAT) ? acc[0][0] * wb[k] : acc[0][k]);
-#pragma unroll
-            for (int i = 0; i < N; ++i)
-#pragma unroll
-                for (int k = 0; k <= N; ++k) acc[i][k] = acc[i + 1][k];
-#pragma unroll
-            for (int k = 0; k <= N; ++k) acc[N][k] = 0.0f;
-            ++qa;
-            na = ((float)(qa + 1) - Ca) * rs.inv_ra;
-        } else {
-#pragma unroll
-            for (int i = 0; i <= N; ++i) sink.flush(j, la0 + i, lb0, acc[i][0]);
-#pragma unroll
-            for (int i = 0; i <= N; ++i) {
-#pragma unroll
-                for (int k = 0; k < N; ++k) acc[i][k] = acc[i][k + 1];
-                acc[i][N] = 0.0f;
-            }
-            ++qb;
-            nb = ((float)(qb + 1) - Cb) * rs.inv_rb;
         }
     }
-    return false;
+    const int la0 = IA + qa - N, lb0 = IB + qb - N;
+#pragma unroll
+    for (int i = 0; i <= N; ++i)
+#pragma unroll
+        for (int k = 0; k <= N; ++k)
+            sink.flush(j, la0 + i, lb0 + k, (QUAD && FLAT) ? acc[i][0] * wb[k] : acc[i][k]);
+    return true;
 }
 
 // Quadrature sweep of slab j with the rule the ray needs: the flat rule when
