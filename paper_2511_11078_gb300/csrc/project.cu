@@ -33,8 +33,8 @@ struct FwdSink {
     const float *__restrict__ c;
     int S0, S1, S2;
     int loa, hia, lob, hib;
-    bool in = false;  // every window of the current slab lies inside the bounds
     float acc;
+    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
     {
@@ -52,9 +52,9 @@ struct FwdSink {
 
 struct CountSink {
     int loa, hia, lob, hib;
-    bool in = false;  // every window of the current slab lies inside the bounds
     unsigned int n;       // bases with a nonzero footprint
     unsigned int pieces;  // integrated pieces (m Gauss nodes each)
+    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() { ++pieces; }
     __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
     {
@@ -74,8 +74,8 @@ struct AtomicSink {
     float *__restrict__ c;
     int S0, S1, S2;
     int loa, hia, lob, hib;
-    bool in = false;  // every window of the current slab lies inside the bounds
     float yv;
+    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
     {
@@ -97,8 +97,8 @@ struct BrickSink {
     float *part;
     int L0, L1, L2, Loff;
     int loa, hia, lob, hib;
-    bool in = false;  // every window of the current slab lies inside the bounds
     float yv;
+    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
     {
