@@ -34,19 +34,15 @@ struct FwdSink {
     int S0, S1, S2;
     int loa, hia, lob, hib;
     float acc;
-    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
-    {
-        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
-    }
+    __device__ __forceinline__ void slab(int, float, int, float, int) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
     }
     __device__ __forceinline__ void flush(int j, int la, int lb, float v)
     {
-        if (in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) acc = fmaf(__ldg(c + (j * S0 + la * S1 + lb * S2)), v, acc);
+        if (la >= loa && la <= hia && lb >= lob && lb <= hib) acc = fmaf(__ldg(c + (j * S0 + la * S1 + lb * S2)), v, acc);
     }
 };
 
@@ -54,19 +50,15 @@ struct CountSink {
     int loa, hia, lob, hib;
     unsigned int n;       // bases with a nonzero footprint
     unsigned int pieces;  // integrated pieces (m Gauss nodes each)
-    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() { ++pieces; }
-    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
-    {
-        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
-    }
+    __device__ __forceinline__ void slab(int, float, int, float, int) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
     }
     __device__ __forceinline__ void flush(int, int la, int lb, float v)
     {
-        n += ((in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) && v > 0.0f) ? 1u : 0u;
+        n += (la >= loa && la <= hia && lb >= lob && lb <= hib && v > 0.0f) ? 1u : 0u;
     }
 };
 
@@ -75,19 +67,15 @@ struct AtomicSink {
     int S0, S1, S2;
     int loa, hia, lob, hib;
     float yv;
-    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
-    {
-        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
-    }
+    __device__ __forceinline__ void slab(int, float, int, float, int) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
     }
     __device__ __forceinline__ void flush(int j, int la, int lb, float v)
     {
-        if (in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) atomicAdd(c + (j * S0 + la * S1 + lb * S2), yv * v);
+        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(c + (j * S0 + la * S1 + lb * S2), yv * v);
     }
 };
 
@@ -98,19 +86,15 @@ struct BrickSink {
     int L0, L1, L2, Loff;
     int loa, hia, lob, hib;
     float yv;
-    bool in = false;  // every window of the current slab lies inside the bounds
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int ia, float, int ib, float, int n)
-    {
-        in = ia - n >= loa && ia + 2 * n + 4 <= hia && ib - n >= lob && ib + 2 * n + 4 <= hib;
-    }
+    __device__ __forceinline__ void slab(int, float, int, float, int) {}
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
-        return in || (a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib);
+        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
     }
     __device__ __forceinline__ void flush(int j, int la, int lb, float v)
     {
-        if (in || (la >= loa && la <= hia && lb >= lob && lb <= hib)) atomicAdd(part + (j * L0 + la * L1 + lb * L2 + Loff), yv * v);
+        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(part + (j * L0 + la * L1 + lb * L2 + Loff), yv * v);
     }
 };
 

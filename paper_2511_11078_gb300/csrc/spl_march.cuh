@@ -425,75 +425,69 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
     float wb[N + 1];
     if constexpr (FLAT) bweights<N>(Cb - (float)qb, wb);
     float x0 = -W;
-    int it = 0;
-    // The slab's d-factor has N+1 polynomial pieces xi in [id - W, id + 1 - W);
-    // the loop over them is unrolled so each piece's polynomial is a
-    // compile-time constant; inside a d-piece the a- and b-knot crossings
-    // split it further (at most kSlabIterCap pieces in all).
-#pragma unroll
-    for (int id = 0; id <= N; ++id) {
-        const float xend = (float)(id + 1) - W;
+    int id = 0;  // d-piece: xi in [id - W, id + 1 - W)
 #pragma unroll 1
-        for (;;) {
-            if (++it > qr.cap) return false;
-            const float x1r = fminf(xend, fminf(na, nb));
-            const float x1 = fmaxf(x1r, x0);
-            const int la0 = IA + qa - N, lb0 = IB + qb - N;
-            if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
-                if constexpr (QUAD && FLAT) {
-                    float G[N + 1];
+    for (int it = 0; it < qr.cap; ++it) {
+        const float nd = (float)(id + 1) - W;
+        const float x1r = fminf(nd, fminf(na, nb));
+        const int ev = (x1r == nd) ? 0 : ((x1r == na) ? 1 : 2);
+        const float x1 = fmaxf(x1r, x0);
+        const int la0 = IA + qa - N, lb0 = IB + qb - N;
+        if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
+            if constexpr (QUAD && FLAT) {
+                float G[N + 1];
 #pragma unroll
-                    for (int i = 0; i <= N; ++i) G[i] = acc[i][0];
-                    integrate_piece_flat<N>(x0, x1, id, Ca - (float)qa, rs.ra, qr, G);
+                for (int i = 0; i <= N; ++i) G[i] = acc[i][0];
+                integrate_piece_flat<N>(x0, x1, id, Ca - (float)qa, rs.ra, qr, G);
 #pragma unroll
-                    for (int i = 0; i <= N; ++i) acc[i][0] = G[i];
-                } else if constexpr (QUAD) {
-                    integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
-                } else {
-#pragma unroll
-                    for (int i = 0; i <= N; ++i)
-#pragma unroll
-                        for (int k = 0; k <= N; ++k) acc[i][k] = 1.0f;
-                }
-                sink.piece();
-            }
-            x0 = x1;
-            if (x1r == xend) break;  // end of the d-piece (first among equal events)
-            if (x1r == na) {
-                // the lowest a-row leaves the ray's reach: flush it, shift
-#pragma unroll
-                for (int k = 0; k <= N; ++k)
-                    sink.flush(j, la0, lb0 + k, (QUAD && FLAT) ? acc[0][0] * wb[k] : acc[0][k]);
-#pragma unroll
-                for (int i = 0; i < N; ++i)
-#pragma unroll
-                    for (int k = 0; k <= N; ++k) acc[i][k] = acc[i + 1][k];
-#pragma unroll
-                for (int k = 0; k <= N; ++k) acc[N][k] = 0.0f;
-                if (++qa > qa_lim) return false;
-                na = ((float)(qa + 1) - Ca) * rs.inv_ra;
+                for (int i = 0; i <= N; ++i) acc[i][0] = G[i];
+            } else if constexpr (QUAD) {
+                integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
             } else {
-                // the lowest b-column leaves
 #pragma unroll
-                for (int i = 0; i <= N; ++i) sink.flush(j, la0 + i, lb0, acc[i][0]);
+                for (int i = 0; i <= N; ++i)
 #pragma unroll
-                for (int i = 0; i <= N; ++i) {
-#pragma unroll
-                    for (int k = 0; k < N; ++k) acc[i][k] = acc[i][k + 1];
-                    acc[i][N] = 0.0f;
-                }
-                if (++qb > qb_lim) return false;
-                nb = ((float)(qb + 1) - Cb) * rs.inv_rb;
+                    for (int k = 0; k <= N; ++k) acc[i][k] = 1.0f;
             }
+            sink.piece();
+        }
+        x0 = x1;
+        if (ev == 0) {
+            if (++id > N) {
+#pragma unroll
+                for (int i = 0; i <= N; ++i)
+#pragma unroll
+                    for (int k = 0; k <= N; ++k)
+                        sink.flush(j, la0 + i, lb0 + k, (QUAD && FLAT) ? acc[i][0] * wb[k] : acc[i][k]);
+                return true;
+            }
+        } else if (ev == 1) {
+            // the lowest a-row leaves the ray's reach: flush it, shift
+#pragma unroll
+            for (int k = 0; k <= N; ++k) sink.flush(j, la0, lb0 + k, (QUAD && FLAT) ? acc[0][0] * wb[k] : acc[0][k]);
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+#pragma unroll
+                for (int k = 0; k <= N; ++k) acc[i][k] = acc[i + 1][k];
+#pragma unroll
+            for (int k = 0; k <= N; ++k) acc[N][k] = 0.0f;
+            if (++qa > qa_lim) return false;
+            na = ((float)(qa + 1) - Ca) * rs.inv_ra;
+        } else {
+            // the lowest b-column leaves
+#pragma unroll
+            for (int i = 0; i <= N; ++i) sink.flush(j, la0 + i, lb0, acc[i][0]);
+#pragma unroll
+            for (int i = 0; i <= N; ++i) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) acc[i][k] = acc[i][k + 1];
+                acc[i][N] = 0.0f;
+            }
+            if (++qb > qb_lim) return false;
+            nb = ((float)(qb + 1) - Cb) * rs.inv_rb;
         }
     }
-    const int la0 = IA + qa - N, lb0 = IB + qb - N;
-#pragma unroll
-    for (int i = 0; i <= N; ++i)
-#pragma unroll
-        for (int k = 0; k <= N; ++k)
-            sink.flush(j, la0 + i, lb0 + k, (QUAD && FLAT) ? acc[i][0] * wb[k] : acc[i][k]);
-    return true;
+    return false;
 }
 
 // Quadrature sweep of slab j with the rule the ray needs: the flat rule when
