@@ -111,10 +111,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_mlp_rows(MlpDev w, int degree,
     for (long long tile = wid; tile < tiles; tile += warps) {
         float x[2][5];
         float mask[2] = {1.0f, 1.0f};
+        // FROM_WP: lane t = 0 of a quad prepares row g, lane t = 1 row g + 8
+        // (FP64 work once per row), then the quad shares them by shuffles
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const long long r = tile * 16 + g + 8 * h;
-            if (r < count) {
+            if (FROM_WP && t != h) {
+#pragma unroll
+                for (int e = 0; e < 5; ++e) x[h][e] = 0.0f;
+                mask[h] = 0.0f;
+            } else if (r < count) {
                 if (FROM_WP) {
                     double wv[3], pv[3], f[5];
                     double nrm = 0.0;
@@ -155,6 +161,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_mlp_rows(MlpDev w, int degree,
                 for (int e = 0; e < 5; ++e) x[h][e] = 0.0f;
                 mask[h] = 0.0f;
             }
+        }
+        if (FROM_WP) {
+            const int src0 = lane & ~3, src1 = src0 + 1;
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                x[0][e] = __shfl_sync(0xffffffffu, x[0][e], src0);
+                x[1][e] = __shfl_sync(0xffffffffu, x[1][e], src1);
+            }
+            mask[0] = __shfl_sync(0xffffffffu, mask[0], src0);
+            mask[1] = __shfl_sync(0xffffffffu, mask[1], src1);
         }
         float o0, o1;
         mlp_tile16<false>(S, x[0], x[1], o0, o1);
@@ -219,16 +235,49 @@ __device__ __forceinline__ float silu_grad(float z)
     return s * (1.0f + z * (1.0f - s));
 }
 
-// dL/dz of every layer for L = (1/B) sum (f(x_b) - y_b)^2; one thread per row.
-// Weights as used in the forward (BF16-rounded) come from the FP32 master
-// rounded on the fly; roundings of activations pass straight through.
-__global__ void __launch_bounds__(128) k_train_backward(const float *__restrict__ P, int B,
-                                                        const float *__restrict__ Y, const float *__restrict__ act,
-                                                        const float *__restrict__ out, float *dz, float *dz4,
-                                                        double *loss_part, int max_batch)
+// dL/dz of every layer for L = (1/B) sum (f(x_b) - y_b)^2; one thread per
+// row, the layer's gradient vector in registers, weights read as float4
+// from shared memory (four independent FMA chains).  Weights as used in the
+// forward (BF16-rounded) come from the FP32 master rounded on the fly;
+// roundings of activations pass straight through.
+constexpr int kBwdThreads = 64;
+
+__device__ __forceinline__ void back_layer(const float *__restrict__ Wt, const float (&gin)[kHid],
+                                           const float *__restrict__ z, float *__restrict__ gout_g, float (&gout)[kHid])
 {
-    __shared__ float W2[kHid * kHid], W3[kHid * kHid], W4[kHid];
-    __shared__ double red[4];
+    // gout[i] = silu'(z[i]) * sum_c W[c][i] gin[c]; Wt is W transposed, row i
+#pragma unroll
+    for (int i0 = 0; i0 < kHid; i0 += 4) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < kHid; ++c) {
+            const float4 w = *reinterpret_cast<const float4 *>(Wt + c * kHid + i0);
+            acc.x = fmaf(w.x, gin[c], acc.x);
+            acc.y = fmaf(w.y, gin[c], acc.y);
+            acc.z = fmaf(w.z, gin[c], acc.z);
+            acc.w = fmaf(w.w, gin[c], acc.w);
+        }
+        const float4 zz = *reinterpret_cast<const float4 *>(z + i0);
+        gout[i0] = acc.x * silu_grad(zz.x);
+        gout[i0 + 1] = acc.y * silu_grad(zz.y);
+        gout[i0 + 2] = acc.z * silu_grad(zz.z);
+        gout[i0 + 3] = acc.w * silu_grad(zz.w);
+        *reinterpret_cast<float4 *>(gout_g + i0) = make_float4(gout[i0], gout[i0 + 1], gout[i0 + 2], gout[i0 + 3]);
+    }
+}
+
+__global__ void __launch_bounds__(kBwdThreads) k_train_backward(const float *__restrict__ P, int B,
+                                                                const float *__restrict__ Y,
+                                                                const float *__restrict__ act,
+                                                                const float *__restrict__ out, float *dz, float *dz4,
+                                                                double *loss_part, int max_batch)
+{
+    // W2, W3 stored as [c][i] = W[c][i] (row c = output unit): reading
+    // W[c][i0..i0+3] for fixed c is a float4
+    __shared__ __align__(16) float W2[kHid * kHid];
+    __shared__ __align__(16) float W3[kHid * kHid];
+    __shared__ float W4[kHid];
+    __shared__ double red[kBwdThreads / 32];
     for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
         W2[i] = bf16r(P[kOffW2 + i]);
         W3[i] = bf16r(P[kOffW3 + i]);
@@ -243,59 +292,90 @@ __global__ void __launch_bounds__(128) k_train_backward(const float *__restrict_
         l2 = (double)res * res;
         const float d4 = 2.0f * res / (float)B;
         dz4[r] = d4;
-        const float *z1 = act + r * 64, *z2 = act + 2 * L + r * 64, *z3 = act + 4 * L + r * 64;
-        float *g1 = dz + r * 64, *g2 = dz + L + r * 64, *g3 = dz + 2 * L + r * 64;
-        for (int c = 0; c < kHid; ++c) g3[c] = W4[c] * d4 * silu_grad(z3[c]);
-        for (int i = 0; i < kHid; ++i) {
-            float acc = 0.0f;
-            for (int c = 0; c < kHid; ++c) acc = fmaf(W3[c * kHid + i], g3[c], acc);
-            g2[i] = acc * silu_grad(z2[i]);
+        const float *z3 = act + 4 * L + (size_t)r * 64;
+        float g3[kHid], g2[kHid], g1[kHid];
+#pragma unroll
+        for (int c = 0; c < kHid; c += 4) {
+            const float4 zz = *reinterpret_cast<const float4 *>(z3 + c);
+            g3[c] = W4[c] * d4 * silu_grad(zz.x);
+            g3[c + 1] = W4[c + 1] * d4 * silu_grad(zz.y);
+            g3[c + 2] = W4[c + 2] * d4 * silu_grad(zz.z);
+            g3[c + 3] = W4[c + 3] * d4 * silu_grad(zz.w);
+            *reinterpret_cast<float4 *>(dz + 2 * L + (size_t)r * 64 + c) = make_float4(g3[c], g3[c + 1], g3[c + 2], g3[c + 3]);
         }
-        for (int i = 0; i < kHid; ++i) {
-            float acc = 0.0f;
-            for (int c = 0; c < kHid; ++c) acc = fmaf(W2[c * kHid + i], g2[c], acc);
-            g1[i] = acc * silu_grad(z1[i]);
-        }
+        back_layer(W3, g3, act + 2 * L + (size_t)r * 64, dz + L + (size_t)r * 64, g2);
+        back_layer(W2, g2, act + (size_t)r * 64, dz + (size_t)r * 64, g1);
     }
     // per-block loss partial (fixed order)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l2 += __shfl_down_sync(0xffffffffu, l2, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
     __syncthreads();
-    if (threadIdx.x == 0) loss_part[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kBwdThreads / 32; ++w) t += red[w];
+        loss_part[blockIdx.x] = t;
+    }
 }
 
-// Weight gradients of one batch chunk: block (chunk, layer); each thread
-// owns a fixed set of (out, in) entries and sums the chunk's rows in order.
+// Weight gradients of one batch chunk: block (chunk, layer).  Rows are
+// staged through shared memory 32 at a time; for the 64x64 layers each
+// thread owns one output unit o and 16 consecutive inputs, and sums the
+// chunk's rows in order (deterministic).
+constexpr int kStageRows = 32;
+
 __global__ void __launch_bounds__(kWgThreads) k_train_wgrad(int B, const float *__restrict__ X,
                                                             const float *__restrict__ act,
                                                             const float *__restrict__ dz,
                                                             const float *__restrict__ dz4, float *part, int max_batch)
 {
+    __shared__ __align__(16) float Gs[kStageRows][kHid];
+    __shared__ __align__(16) float Hs[kStageRows][kHid];
     const int chunk = blockIdx.x, layer = blockIdx.y;
     const size_t L = (size_t)max_batch * 64;
     const int r0 = chunk * kChunkRows, r1 = min(B, r0 + kChunkRows);
     float *dst = part + (size_t)chunk * (kParams + 1);
-    // geometry of the layer: in-dim, out-dim, inputs, output grads, offsets
-    int nin, nout, offW, offB, hstride;
+    int nin, nout, offW, offB, hstride, gstride;
     const float *H, *G;
-    int gstride;
     if (layer == 0) { nin = kIn; nout = kHid; H = X; hstride = kIn; G = dz; gstride = 64; offW = kOffW1; offB = kOffB1; }
     else if (layer == 1) { nin = kHid; nout = kHid; H = act + L; hstride = 64; G = dz + L; gstride = 64; offW = kOffW2; offB = kOffB2; }
     else if (layer == 2) { nin = kHid; nout = kHid; H = act + 3 * L; hstride = 64; G = dz + 2 * L; gstride = 64; offW = kOffW3; offB = kOffB3; }
     else { nin = kHid; nout = 1; H = act + 5 * L; hstride = 64; G = dz4; gstride = 1; offW = kOffW4; offB = kOffB4; }
-    const int nw = nin * nout;
-    for (int e = threadIdx.x; e < nw + nout; e += blockDim.x) {
-        float acc = 0.0f;
-        if (e < nw) {
-            const int o = e / nin, i = e % nin;
-            for (int r = r0; r < r1; ++r) acc = fmaf(G[(size_t)r * gstride + o], H[(size_t)r * hstride + i], acc);
-            dst[offW + e] = acc;
-        } else {
-            const int o = e - nw;
-            for (int r = r0; r < r1; ++r) acc += G[(size_t)r * gstride + o];
-            dst[offB + o] = acc;
+    // thread -> (o, 16 inputs starting at i0); the thread with i0 = 0 also
+    // sums the bias gradient of o
+    const int nslots = nout * ((nin + 15) / 16);
+    const int slot = threadIdx.x;
+    const bool has_w = slot < nslots;
+    const int o = has_w ? slot / ((nin + 15) / 16) : 0;
+    const int i0 = has_w ? (slot % ((nin + 15) / 16)) * 16 : 0;
+    const bool has_b = has_w && i0 == 0;
+    float acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+    float accb = 0.0f;
+    for (int rs = r0; rs < r1; rs += kStageRows) {
+        const int nr = min(kStageRows, r1 - rs);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kStageRows * kHid; e += blockDim.x) {
+            const int rr = e / kHid, cc = e % kHid;
+            Gs[rr][cc] = (rr < nr && cc < nout) ? G[(size_t)(rs + rr) * gstride + cc] : 0.0f;
+            Hs[rr][cc] = (rr < nr && cc < nin) ? H[(size_t)(rs + rr) * hstride + cc] : 0.0f;
         }
+        __syncthreads();
+        if (has_w) {
+            for (int rr = 0; rr < nr; ++rr) {
+                const float gv = Gs[rr][o];
+                accb += gv;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] = fmaf(gv, Hs[rr][i0 + q], acc[q]);
+            }
+        }
+    }
+    if (has_w) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (i0 + q < nin) dst[offW + o * nin + i0 + q] = acc[q];
+        if (has_b) dst[offB + o] = accb;
     }
 }
 
@@ -335,9 +415,9 @@ static spl_status grad_impl(spl_mlp *m, int B, const float *X, const float *Y, f
     const int tiles = (B + 15) / 16;
     const int fblocks = (tiles + 3) / 4;
     k_train_forward<<<fblocks, kEvalThreads, 0, st>>>(w, B, X, m->act, m->out, m->max_batch);
-    const int bblocks = (B + 127) / 128;
-    k_train_backward<<<bblocks, 128, 0, st>>>(m->master, B, Y, m->act, m->out, m->dz, m->dz4, m->loss_part,
-                                              m->max_batch);
+    const int bblocks = (B + kBwdThreads - 1) / kBwdThreads;
+    k_train_backward<<<bblocks, kBwdThreads, 0, st>>>(m->master, B, Y, m->act, m->out, m->dz, m->dz4, m->loss_part,
+                                                      m->max_batch);
     const int chunks = (B + kChunkRows - 1) / kChunkRows;
     k_train_wgrad<<<dim3(chunks, 4), kWgThreads, 0, st>>>(B, X, m->act, m->dz, m->dz4, m->part, m->max_batch);
     k_train_reduce<<<(kParams + 255) / 256, 256, 0, st>>>(m->part, chunks, m->loss_part, bblocks, B, grad, loss);
@@ -372,7 +452,7 @@ extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long lo
     m->max_batch = max_batch;
     cudaGetDevice(&m->device);
     const int chunks = (max_batch + kChunkRows - 1) / kChunkRows;
-    const int nloss = (max_batch + 127) / 128;
+    const int nloss = (max_batch + kBwdThreads - 1) / kBwdThreads;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
