@@ -122,33 +122,30 @@ __global__ void __launch_bounds__(kEvalThreads) k_mlp_rows(MlpDev w, int degree,
                 mask[h] = 0.0f;
             } else if (r < count) {
                 if (FROM_WP) {
-                    double wv[3], pv[3], f[5];
-                    double nrm = 0.0;
+                    float wv[3], pv[3];
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
                         wv[e] = a[3 * r + e];
                         pv[e] = b[3 * r + e];
-                        nrm += wv[e] * wv[e];
                     }
-                    nrm = sqrt(nrm);
+                    const float inrm = rsqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
 #pragma unroll
-                    for (int e = 0; e < 3; ++e) wv[e] /= nrm;
-                    canonical_features(degree, wv, pv, f);
-#pragma unroll
-                    for (int e = 0; e < 5; ++e) x[h][e] = (float)f[e];
+                    for (int e = 0; e < 3; ++e) wv[e] *= inrm;
+                    canonical_features_f32(degree, wv, pv, x[h]);
                     // exact support: the line p + t w meets the open cube
                     // [-W, W]^3 in a segment of positive length
-                    const double W = 0.5 * (degree + 1);
-                    double lo = -1e300, hi = 1e300;
+                    const float W = 0.5f * (degree + 1);
+                    float lo = -INFINITY, hi = INFINITY;
                     bool in = true;
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        if (wv[e] == 0.0) {
+                        if (wv[e] == 0.0f) {
                             in = in && (pv[e] >= -W && pv[e] < W) && (degree == 0 || pv[e] > -W);
                         } else {
-                            const double t1 = (-W - pv[e]) / wv[e], t2 = (W - pv[e]) / wv[e];
-                            lo = fmax(lo, fmin(t1, t2));
-                            hi = fmin(hi, fmax(t1, t2));
+                            const float iw = 1.0f / wv[e];
+                            const float t1 = (-W - pv[e]) * iw, t2 = (W - pv[e]) * iw;
+                            lo = fmaxf(lo, fminf(t1, t2));
+                            hi = fminf(hi, fmaxf(t1, t2));
                         }
                     }
                     mask[h] = (in && hi > lo) ? 1.0f : 0.0f;

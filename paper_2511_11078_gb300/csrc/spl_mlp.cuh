@@ -56,6 +56,41 @@ __host__ __device__ inline void canonical_features(int degree, const double (&w_
     f[4] = (p[0] * v[0] + p[1] * v[1] + p[2] * v[2]) * sc;
 }
 
+// The same features in FP32 (the library's FP64 units are scarce on GB300;
+// the features are FP32 values either way).  Same flip, stable sort and frame.
+__device__ __forceinline__ void canonical_features_f32(int degree, const float (&w_in)[3], const float (&p_in)[3],
+                                                       float (&f)[5])
+{
+    const float W = 0.5f * (degree + 1);
+    float w[3], p[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const bool neg = w_in[e] < 0.0f;
+        w[e] = neg ? -w_in[e] : w_in[e];
+        p[e] = neg ? -p_in[e] : p_in[e];
+    }
+#pragma unroll
+    for (int i = 1; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j > 0; --j) {
+            const bool sw = w[j - 1] > w[j];
+            const float a = w[j - 1], b = w[j], pa = p[j - 1], pb = p[j];
+            w[j - 1] = sw ? b : a;
+            w[j] = sw ? a : b;
+            p[j - 1] = sw ? pb : pa;
+            p[j] = sw ? pa : pb;
+        }
+    const float inr = rsqrtf(w[1] * w[1] + w[2] * w[2]);
+    const float u1 = -w[2] * inr, u2 = w[1] * inr;  // u = (0, u1, u2)
+    const float v0 = u1 * w[2] - u2 * w[1], v1 = u2 * w[0], v2 = -u1 * w[0];
+    const float sc = 1.7320508075688772f / W;
+    f[0] = w[0];
+    f[1] = w[1];
+    f[2] = w[2];
+    f[3] = (p[1] * u1 + p[2] * u2) * sc;
+    f[4] = (p[0] * v0 + p[1] * v1 + p[2] * v2) * sc;
+}
+
 // ---------------------------------------------------------------- device weights
 // Evaluation copy of the parameters: the two 64x64 layers as BF16 with a
 // padded row stride (72 BF16 = 36 words: the B-fragment loads of a warp hit

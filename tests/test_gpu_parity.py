@@ -379,3 +379,41 @@ def test_full_size_adjoint_sampled(env, orc, tilt128):
     ref, _ = orc.adjoint_at(3, wl.dims, wl.origin, y.astype(np.float64), oracle_geom(orc, wl.geometry), k)
     got = c.cpu().numpy().reshape(-1)[k].astype(np.float64)
     assert rel_l2(got, ref) <= TOL, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("which", ["cone256", "helical512"])
+def test_full_size_cone_and_helical_sampled(env, orc, which):
+    """The 256^3 circular cone-beam and 512^3 helical workloads at full
+    volume and detector size, on a subset of their views: sampled rays of A
+    and sampled coefficients of A^T against the oracle."""
+    torch, spl = env
+    if which == "cone256":
+        wl = I.workload_cone()
+        views = [0, 45, 90, 200]
+    else:
+        wl = I.workload_helical()
+        views = [0, 181, 360, 719]
+    geo = wl.geometry.subset_views(views)
+    g = spl.Geometry(wl.dims, wl.origin, geo)
+    c = torch.tensor(wl.coeffs, device="cuda")
+    y = torch.empty(g.n_rays, dtype=torch.float32, device="cuda")
+    spl.forward(g, c, y, spl.basis(3))
+    g.status()
+    rng = np.random.default_rng(2600)
+    rays = np.sort(rng.choice(g.n_rays, 40, replace=False))
+    og = oracle_geom(orc, geo)
+    yref, pairs = orc.forward_subset(3, wl.dims, wl.origin, wl.coeffs.astype(np.float64), og, rays)
+    got = y.cpu().numpy()[rays].astype(np.float64)
+    assert pairs.sum() > 0
+    assert rel_l2(got, yref) <= TOL, rel_l2(got, yref)
+    yv = rng.uniform(0, 1, size=g.n_rays).astype(np.float32)
+    cb = torch.empty(g.coeff_shape, dtype=torch.float32, device="cuda")
+    spl.adjoint(g, torch.tensor(yv, device="cuda"), cb, spl.basis(3))
+    g.status()
+    n = int(np.prod(wl.dims))
+    ctr = ((np.array(wl.dims[::-1]) // 2) * np.array([wl.dims[0] * wl.dims[1], wl.dims[0], 1])).sum()
+    k = np.unique(np.concatenate([rng.choice(n, 12, replace=False), [ctr, ctr + 7, ctr + 3 * wl.dims[0]]]))
+    ref, npair = orc.adjoint_at(3, wl.dims, wl.origin, yv.astype(np.float64), og, k)
+    gotc = cb.cpu().numpy().reshape(-1)[k].astype(np.float64)
+    assert npair.sum() > 0
+    assert rel_l2(gotc, ref) <= TOL, rel_l2(gotc, ref)
