@@ -265,7 +265,7 @@ def bandlimited_noise(rng: np.random.Generator, dims, sigma: float, amplitude: f
     fy = np.fft.fftfreq(ny)[None, :, None]
     fx = np.fft.rfftfreq(nx)[None, None, :]
     H = np.exp(-2.0 * (np.pi * sigma) ** 2 * (fx * fx + fy * fy + fz * fz)).astype(np.float32)
-    out = np.fft.irfftn(F * H, s=(nz, ny, nx)).astype(np.float32)
+    out = np.fft.irfftn(F * H, s=(nz, ny, nx), axes=(0, 1, 2)).astype(np.float32)
     out *= amplitude / max(float(out.std()), 1e-30)
     return out
 

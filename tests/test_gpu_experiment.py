@@ -18,5 +18,6 @@ def test_spline_beats_voxel_reconstruction():
     spl.lib()
     r = E.run(dims=(90, 90, 25), n_views=100, det=(90, 25), iters=50, degrees=(2, 0))
     print(r)
+    # (the data residual is no criterion: the voxel model can fit the noisy
+    # data more closely while reconstructing the function worse)
     assert r["degree_2"]["psnr_db"] > r["degree_0"]["psnr_db"] + 1.0
-    assert r["degree_2"]["residual"] < r["degree_0"]["residual"]
