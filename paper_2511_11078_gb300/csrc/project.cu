@@ -125,7 +125,7 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
 }
 
 template <int N>
-__global__ void __launch_bounds__(128) k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y,
+__global__ void __launch_bounds__(128, 6) k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y,
                                                        QuadRule qr, int kahan)
 {
     int iu, iv;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
 
 // view geometries, scatter form: the forward's thread mapping, float atomics
 template <int N>
-__global__ void __launch_bounds__(128) k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y,
+__global__ void __launch_bounds__(128, 6) k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y,
                                                                float *__restrict__ c, QuadRule qr)
 {
     int iu, iv;
