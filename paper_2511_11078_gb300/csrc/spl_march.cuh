@@ -164,35 +164,31 @@ template <> struct BSpl<3> {
 
 template <int N> struct GL { static constexpr int M = (3 * N + 2) / 2 > 0 ? (3 * N + 2) / 2 : 1; };
 
-// The two outer weights vanish at an end of [0, 1]; they are evaluated in
-// factored form g^N/N! and (1-g)^N/N! so that they keep full relative
-// accuracy near the support edge (the expanded power form would cancel).
+// Weights of the N+1 bases whose support contains a point, with t = 1 - g.
+// The outer weights vanish at an end of [0, 1] and are evaluated in factored
+// form t^N/N!, g^N/N! (full relative accuracy near a support edge); the
+// inner ones use the mirror symmetry B_{N,i}(g) = B_{N,N-i}(1 - g):
+//   cubic:     w1 = 2/3 - g^2 (1 - g/2),  w2 = 2/3 - t^2 (1 - t/2)
+//   quadratic: w1 = 1/2 + g t
 template <int N>
 __device__ __forceinline__ void bweights(float g, float (&w)[N + 1])
 {
+    const float t = 1.0f - g;
     if constexpr (N == 0) {
         w[0] = 1.0f;
     } else if constexpr (N == 1) {
-        w[0] = 1.0f - g;
+        w[0] = t;
         w[1] = g;
+    } else if constexpr (N == 2) {
+        w[0] = 0.5f * t * t;
+        w[1] = fmaf(g, t, 0.5f);
+        w[2] = 0.5f * g * g;
     } else {
-        constexpr float inv_fact = (N == 2) ? 0.5f : 1.0f / 6.0f;
-        const float h = 1.0f - g;
-        float gp = g, hp = h;
-#pragma unroll
-        for (int k = 1; k < N; ++k) {
-            gp *= g;
-            hp *= h;
-        }
-        w[0] = hp * inv_fact;
-        w[N] = gp * inv_fact;
-#pragma unroll
-        for (int i = 1; i < N; ++i) {
-            float v = BSpl<N>::c(i, N);
-#pragma unroll
-            for (int k = N - 1; k >= 0; --k) v = fmaf(v, g, BSpl<N>::c(i, k));
-            w[i] = v;
-        }
+        const float g2 = g * g, t2 = t * t;
+        w[0] = t2 * t * (1.0f / 6.0f);
+        w[1] = fmaf(-g2, fmaf(-0.5f, g, 1.0f), 2.0f / 3.0f);
+        w[2] = fmaf(-t2, fmaf(-0.5f, t, 1.0f), 2.0f / 3.0f);
+        w[3] = g2 * g * (1.0f / 6.0f);
     }
 }
 
