@@ -52,6 +52,11 @@ MLP_FLOP_PER_PAIR = 2 * (5 * 64 + 2 * 64 * 64 + 64)
 FLOP_PER_PAIR = 2
 NODES_PER_PIECE = {0: 1, 1: 2, 2: 4, 3: 5}
 SMS, FP32_LANES = 152, 128
+# DRAM bytes (read + write) per launch from the ncu capture of each kernel
+# on this workload (profiles/k_*-tilt128-cubic.md); to be reset to None
+# whenever the kernel changes after the capture.
+NCU_TRAFFIC = {"k_forward_views": 9.229312e6 + 3.740416e6, "k_adjoint_views_scatter": 45.263616e6 + 1.529088e6,
+               "k_adjoint_bricks": None}
 
 
 def parse():
@@ -411,7 +416,7 @@ def run_ours(args):
     dom_ms = max(fwd, adj)
     achieved = flops_fwd / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get(dominant),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz max SM clock" % max_mhz,
                 "algorithmic_flop_per_launch": flops_fwd}
 
