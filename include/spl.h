@@ -65,6 +65,9 @@ enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1 };
  * order that varies between runs (float atomics in shared or global
  * memory), so results agree to rounding, not bit for bit. */
 enum { SPL_ADJ_AUTO = 0, SPL_ADJ_GATHER = 1, SPL_ADJ_SCATTER = 2 };
+/* slice-separable parallel views (see spl_prepare): SPL_SEP_AUTO uses the
+ * plane-matrix path for them, SPL_SEP_OFF walks them like any other view */
+enum { SPL_SEP_AUTO = 0, SPL_SEP_OFF = 1 };
 
 typedef struct spl_geometry spl_geometry; /* opaque, library-owned */
 typedef struct spl_mlp spl_mlp;           /* opaque, library-owned */
@@ -104,13 +107,17 @@ typedef struct {
  *           SPL_FP_MLP needs `mlp` built for the same degree.
  *   kahan:  nonzero = compensated (Kahan) FP32 sum of the slab partials along
  *           each ray; zero = plain FP32 sum.
- *   adjoint: form of spl_adjoint on view geometries (see SPL_ADJ_*). */
+ *   adjoint: form of spl_adjoint on view geometries (see SPL_ADJ_*).
+ *   separable: SPL_SEP_AUTO (0) or SPL_SEP_OFF: whether the slice-separable
+ *           views of a parallel geometry take the plane-matrix path
+ *           (exact quadrature only). */
 typedef struct {
     int degree;
     int mode;
     const spl_mlp *mlp;
     int kahan;
-    int adjoint;  /* SPL_ADJ_AUTO (0), SPL_ADJ_GATHER or SPL_ADJ_SCATTER; view geometries only */
+    int adjoint;   /* SPL_ADJ_AUTO (0), SPL_ADJ_GATHER or SPL_ADJ_SCATTER; view geometries only */
+    int separable; /* SPL_SEP_AUTO (0) or SPL_SEP_OFF */
 } spl_basis_desc;
 
 /* ---------------------------------------------------------------- geometry */
@@ -135,13 +142,45 @@ long long spl_geometry_coeffs(const spl_geometry *g);
  * since the last call, SPL_ERR_CUDA on a CUDA error, else SPL_OK. */
 spl_status spl_geometry_status(const spl_geometry *g, void *stream);
 
+/* Slice-separable views.  A parallel view is slice-separable along axis b
+ * when its direction has a zero b component and its detector rows run
+ * along b: det_u has no b component and det_v has only one.  The rays of
+ * such a view are flat, so a footprint factors exactly,
+ *   Pphi(w, s - l) = G(u; l_p, l_q) * beta^n(z_v - l_b),
+ * with G the footprint of the 2-D tensor B-spline in the plane of the other
+ * two axes (p, q) and z_v the b coordinate of detector row v.  All rows of a
+ * detector column then share one plane path, and
+ *   y(u, v) = sum_(l_p, l_q) G(u; l_p, l_q) * S(l_p, l_q; v),
+ *   S(l_p, l_q; v) = sum_(l_b) beta^n(z_v - l_b) c_l.
+ * The views of one separable group (the largest set that shares b, the b
+ * coordinate of the detector centre and the b step of det_v) take this
+ * path: the plane matrix G of the group (one row per view and detector
+ * column, one column per (l_p, l_q); its values come from the same flat cell
+ * march as every other ray) is built once per degree, with its transpose;
+ * a forward then resamples c along b into S and gathers the rows of G;
+ * an adjoint gathers the columns of G and resamples back along b, with no
+ * atomics.
+ * spl_prepare builds the plane matrices for basis->degree (one-time device
+ * allocation and kernels on `stream`, then a synchronisation).
+ * spl_forward / spl_adjoint call it on first use.  Geometries without
+ * separable views, basis->separable == SPL_SEP_OFF and the MLP footprint do
+ * not use it.  The plane buffers include the scratch of S and of its
+ * adjoint, so calls on one geometry must not overlap on the GPU.
+ * Returns SPL_OK also when the geometry has no separable views or the basis
+ * does not use the path.  Errors: SPL_ERR_ARG; SPL_ERR_OOM (the path stays
+ * off for this geometry and degree: spl_forward / spl_adjoint then walk
+ * those views like the others and succeed); SPL_ERR_CUDA. */
+spl_status spl_prepare(spl_geometry *g, const spl_basis_desc *basis, void *stream);
+
 /* ---------------------------------------------------------------- operators */
 
 /* Forward projection y = A c (Algorithm 2; Eq. 4 summed over all pairs).
- * One GPU thread per ray marches the slabs of the ray's dominant axis
- * (Definition 2.1); in each slab it visits the bases whose support the ray
- * crosses (Algorithm 3's neighbourhood, de-duplicated by construction) and
- * accumulates c_k * Pphi(w, s - X(k)).
+ * One GPU thread per ray marches the unit cells of the ray's dominant axis
+ * (Definition 2.1); an (n+1)^3 window holds the bases whose support contains
+ * the current point (Algorithm 3's neighbourhood, de-duplicated by
+ * construction), and each basis the ray crosses adds c_k * Pphi(w, s - X(k))
+ * once.  Slice-separable views of a parallel geometry go through the plane
+ * matrices instead (see spl_prepare), with the same footprint values.
  *   c_dev: [nz][ny][nx] float32 (read only);  y_dev: n_rays float32,
  *   overwritten.  Errors: SPL_ERR_ARG (null pointer, degree, mode, missing or
  *   mismatched MLP), SPL_ERR_CUDA (launch failure). */
@@ -154,7 +193,9 @@ spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *basis, const
  * geometries use the form chosen by basis->adjoint (SPL_ADJ_*): a
  * ray-driven scatter with float atomics (the default) or a gather over
  * coefficient bricks that loops over views and the detector window of the
- * brick (no global atomics); explicit rays always scatter.
+ * brick (no global atomics); explicit rays always scatter.  Slice-separable
+ * views of a parallel geometry are gathered through the transposed plane
+ * matrix (no atomics; see spl_prepare) and the other views added to them.
  *   y_dev: n_rays float32 (read only);  c_dev: [nz][ny][nx] float32,
  *   overwritten.  Errors as spl_forward. */
 spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *basis, const float *y_dev, float *c_dev,

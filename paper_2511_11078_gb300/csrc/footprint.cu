@@ -2,8 +2,8 @@
 // the MLP input features.
 //
 // Exact mode: the basis at the origin is a 1x1x1 grid; the ray {p + t w} is
-// set up and swept with the same slab engine as the projector, and the value
-// of the single basis is kept.  MLP mode: f_theta on the canonical features,
+// set up and walked with the same cell march as the projector, and the
+// value of the single basis is kept.  MLP mode: f_theta on the canonical features,
 // times the exact support indicator (the same pair test as the projector).
 #include "spl_host.h"
 #include "spl_mlp.cuh"
@@ -11,17 +11,18 @@
 namespace spl {
 
 struct PointSink {
+    static constexpr bool plane = false;
     float v;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float, int) {}
-    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
-        return a0 <= 0 && a1 >= 0 && b0 <= 0 && b1 >= 0;
+        return d0 <= 0 && d1 >= 0 && a0 <= 0 && a1 >= 0 && b0 <= 0 && b1 >= 0;
     }
-    __device__ __forceinline__ void flush(int, int la, int lb, float val)
+    __device__ __forceinline__ void flush(int ld, int la, int lb, float val)
     {
-        if (la == 0 && lb == 0) v = val;
+        if (ld == 0 && la == 0 && lb == 0) v = val;
     }
+    __device__ __forceinline__ void cell_end() {}
 };
 
 __device__ __forceinline__ GridBox unit_box()
@@ -42,8 +43,7 @@ __device__ __forceinline__ float footprint_exact(const double (&w)[3], const dou
     RaySetup rs;
     if (!ray_setup<N>(unit_box(), p, w, rs)) return 0.0f;
     PointSink sk{0.0f};
-#pragma unroll 1
-    for (int j = rs.j0; j <= rs.j1; ++j) sweep<N>(rs, j, qr, sk);
+    march<N>(rs, rs.c0, rs.c1, qr, sk);
     return sk.v * rs.inv_wd;
 }
 

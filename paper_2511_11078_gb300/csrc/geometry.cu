@@ -105,6 +105,8 @@ spl_status check_basis(const spl_basis_desc *b)
     if (b->degree < 0 || b->degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", b->degree);
     if (b->mode != SPL_FP_QUAD && b->mode != SPL_FP_MLP) return fail(SPL_ERR_ARG, "unknown footprint mode %d", b->mode);
     if (b->mode == SPL_FP_MLP && !b->mlp) return fail(SPL_ERR_ARG, "SPL_FP_MLP needs an MLP");
+    if (b->separable != SPL_SEP_AUTO && b->separable != SPL_SEP_OFF)
+        return fail(SPL_ERR_ARG, "unknown separable mode %d", b->separable);
     return SPL_OK;
 }
 
@@ -122,6 +124,58 @@ static void cross3(const double *a, const double *b, double *c)
 }
 
 static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Slice-separable view (see spl_prepare in spl.h): the direction's zero
+// component is the b axis of its direction set-up, det_u has no b
+// component and det_v only a b component.  Key of a group: b, and the b
+// index coordinate of detector row v, z0 + v dz.
+struct SepKey {
+    int b;
+    double z0, dz;
+};
+
+static bool sep_of(const ViewPose &P, const double *origin, int nv, SepKey &k)
+{
+    const int b = P.dir.ax[2];
+    if (P.dir.r[1] != 0.0 || P.du[b] != 0.0 || P.dv[b] == 0.0) return false;
+    for (int e = 0; e < 3; ++e)
+        if (e != b && P.dv[e] != 0.0) return false;
+    k.b = b;
+    k.dz = P.dv[b];
+    k.z0 = P.dc[b] - origin[b] - 0.5 * (nv - 1) * P.dv[b];
+    return true;
+}
+
+static bool sep_key_of(const ViewPose &P, const double *origin, int nv, const SepKey &key)
+{
+    SepKey k;
+    return sep_of(P, origin, nv, k) && k.b == key.b && k.z0 == key.z0 && k.dz == key.dz;
+}
+
+// the largest group among the first few distinct keys; returns its size
+static int separable_group(const ViewPose *views, int n_views, const double *origin, int nv, SepKey &best)
+{
+    constexpr int kKeys = 8;
+    SepKey keys[kKeys];
+    int cnt[kKeys] = {0}, nk = 0;
+    for (int v = 0; v < n_views; ++v) {
+        SepKey k;
+        if (!sep_of(views[v], origin, nv, k)) continue;
+        int i = 0;
+        while (i < nk && !(keys[i].b == k.b && keys[i].z0 == k.z0 && keys[i].dz == k.dz)) ++i;
+        if (i == nk) {
+            if (nk == kKeys) continue;
+            keys[nk++] = k;
+        }
+        ++cnt[i];
+    }
+    int bi = -1;
+    for (int i = 0; i < nk; ++i)
+        if (bi < 0 || cnt[i] > cnt[bi]) bi = i;
+    if (bi < 0) return 0;
+    best = keys[bi];
+    return cnt[bi];
+}
 
 extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geometry **out)
 {
@@ -148,6 +202,8 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
     for (int e = 0; e < 3; ++e) dg.org[e] = d.origin[e];
     size_t payload = 0;
     double *ray_host = nullptr;
+    int *view_order = nullptr;
+    size_t order_off = 0;
 
     if (d.kind == SPL_RAYS) {
         if (d.n_rays < 0 || (d.n_rays > 0 && (!d.ray_omega || !d.ray_s))) {
@@ -227,6 +283,39 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
             }
         }
         payload = (size_t)d.n_views * sizeof(ViewPose);
+        if (d.kind == SPL_PARALLEL) {
+            // view order: the slice-separable group, the other views whose
+            // rays have a zero transverse component (flat march), the rest;
+            // each class gets its own launch
+            view_order = (int *)malloc((d.n_views > 0 ? d.n_views : 1) * sizeof(int));
+            if (!view_order) { free(g->views_host); free(g); return fail(SPL_ERR_OOM, "host allocation failed"); }
+            SepKey key;
+            const int n_sep = separable_group(g->views_host, d.n_views, d.origin, d.nv, key);
+            int n = 0;
+            for (int k = 0; k < d.n_views; ++k)
+                if (n_sep > 0 && sep_key_of(g->views_host[k], d.origin, d.nv, key)) view_order[n++] = k;
+            for (int k = 0; k < d.n_views; ++k)
+                if (g->views_host[k].dir.rb == 0.0f && !(n_sep > 0 && sep_key_of(g->views_host[k], d.origin, d.nv, key)))
+                    view_order[n++] = k;
+            dg.n_flat = n;
+            for (int k = 0; k < d.n_views; ++k)
+                if (g->views_host[k].dir.rb != 0.0f) view_order[n++] = k;
+            dg.n_sep = n_sep;
+            if (n_sep > 0) {
+                PlaneGroup *pg = new PlaneGroup();
+                pg->b = key.b;
+                pg->p = key.b == 0 ? 1 : 0;
+                pg->q = key.b == 2 ? 1 : 2;
+                pg->n_views = n_sep;
+                pg->rows = (long long)n_sep * d.nu;
+                pg->ncol = (long long)dg.n[pg->p] * dg.n[pg->q];
+                pg->z0 = key.z0;
+                pg->dz = key.dz;
+                g->plane = pg;
+            }
+            order_off = (payload + 255) & ~(size_t)255;
+            payload = order_off + (size_t)d.n_views * sizeof(int);
+        }
     } else {
         free(g);
         return fail(SPL_ERR_ARG, "unknown geometry kind %d", d.kind);
@@ -238,6 +327,8 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
     cudaError_t ce = cudaMalloc(&blk, flag_off + 256);
     if (ce != cudaSuccess) {
         free(ray_host);
+        free(view_order);
+        plane_free(g->plane);
         free(g->views_host);
         free(g);
         cudaGetLastError();
@@ -245,11 +336,16 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
     }
     g->dev_block = blk;
     const void *src = d.kind == SPL_RAYS ? (const void *)ray_host : (const void *)g->views_host;
-    if (payload > 0) ce = cudaMemcpy(blk, src, payload, cudaMemcpyHostToDevice);
+    const size_t src_bytes = view_order ? (size_t)d.n_views * sizeof(ViewPose) : payload;
+    if (src_bytes > 0) ce = cudaMemcpy(blk, src, src_bytes, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && view_order && d.n_views > 0)
+        ce = cudaMemcpy((char *)blk + order_off, view_order, (size_t)d.n_views * sizeof(int), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset((char *)blk + flag_off, 0, 256);
     free(ray_host);
+    free(view_order);
     if (ce != cudaSuccess) {
         cudaFree(blk);
+        plane_free(g->plane);
         free(g->views_host);
         free(g);
         return cuda_check(ce, "geometry upload");
@@ -259,6 +355,7 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
         dg.ray_s = (const double *)blk + 3 * d.n_rays;
     } else {
         dg.views = (const ViewPose *)blk;
+        if (d.kind == SPL_PARALLEL) dg.view_order = (const int *)((const char *)blk + order_off);
     }
     dg.err = (int *)((char *)blk + flag_off);
     *out = g;
@@ -268,6 +365,7 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
 extern "C" void spl_destroy_geometry(spl_geometry *g)
 {
     if (!g) return;
+    plane_free(g->plane);
     if (g->dev_block) cudaFree(g->dev_block);
     free(g->views_host);
     free(g);

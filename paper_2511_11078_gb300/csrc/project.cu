@@ -5,8 +5,9 @@
 // Forward: one thread per ray; the 128 threads of a block cover a 16 x 8
 // detector tile of one view (a warp is an 8 x 4 sub-tile), so neighbouring
 // lanes walk neighbouring lines and gather neighbouring coefficients (L1
-// hits).  The slab partial sums are added along the ray with Kahan
-// compensation.
+// hits).  Each ray is walked with the cell march (one Gauss node set per
+// point of the ray, an (n+1)^3 register window); the per-cell partial sums
+// are added along the ray with Kahan compensation.
 //
 // Adjoint, view geometries, two forms that visit the same pairs with the
 // same footprint values:
@@ -16,8 +17,8 @@
 //    on GB300 A^T then costs about as much as A;
 //  * gather: one block per 16^3 coefficient brick; for every batch of 8
 //    views the block projects the brick's support box onto the detectors,
-//    walks the rays of those pixel windows through the brick's slabs with
-//    the same set-up and slab sweep, accumulates y_r * P in shared memory
+//    walks the rays of those pixel windows through the brick's cells with
+//    the same set-up and cell march, accumulates y_r * P in shared memory
 //    and folds the batch into FP64 totals; no global atomics, each
 //    coefficient written once.
 // Adjoint, explicit rays: no view structure to gather over: scatter.
@@ -29,73 +30,116 @@
 namespace spl {
 
 // ---------------------------------------------------------------- sinks
+// Region of bases a sink accepts, in the ray's mirrored (d, a, b)
+// coordinates: lo[q] .. lo[q] + ext[q].
+struct SinkBox {
+    int lo0, lo1, lo2;
+    unsigned ext0, ext1, ext2;
+    __device__ __forceinline__ bool holds(int d, int a, int b) const
+    {
+        return (unsigned)(d - lo0) <= ext0 && (unsigned)(a - lo1) <= ext1 && (unsigned)(b - lo2) <= ext2;
+    }
+    // whether the window [d0, d1] x [a0, a1] x [b0, b1] meets the region
+    __device__ __forceinline__ bool meets(int d0, int d1, int a0, int a1, int b0, int b1) const
+    {
+        return d1 >= lo0 && d0 <= lo0 + (int)ext0 && a1 >= lo1 && a0 <= lo1 + (int)ext1 && b1 >= lo2 &&
+               b0 <= lo2 + (int)ext2;
+    }
+};
+
+__device__ __forceinline__ SinkBox make_box(const int (&lo)[3], const int (&hi)[3])
+{
+    SinkBox b;
+    b.lo0 = lo[0];
+    b.lo1 = lo[1];
+    b.lo2 = lo[2];
+    b.ext0 = (unsigned)(hi[0] - lo[0]);
+    b.ext1 = (unsigned)(hi[1] - lo[1]);
+    b.ext2 = (unsigned)(hi[2] - lo[2]);
+    return b;
+}
+
+// forward: sum of c_l * F_l along the ray, Kahan-compensated per cell
 struct FwdSink {
+    static constexpr bool plane = false;
     const float *__restrict__ c;
     int S0, S1, S2;
-    int loa, hia, lob, hib;
-    float acc;
+    SinkBox bx;
+    float inv_wd;
+    bool kahan;
+    float acc, sum, comp;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float, int) {}
-    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return bx.meets(d0, d1, a0, a1, b0, b1);
     }
-    __device__ __forceinline__ void flush(int j, int la, int lb, float v)
+    __device__ __forceinline__ void flush(int ld, int la, int lb, float v)
     {
-        if (la >= loa && la <= hia && lb >= lob && lb <= hib) acc = fmaf(__ldg(c + (j * S0 + la * S1 + lb * S2)), v, acc);
+        if (bx.holds(ld, la, lb)) acc = fmaf(__ldg(c + (ld * S0 + la * S1 + lb * S2)), v, acc);
+    }
+    __device__ __forceinline__ void cell_end()
+    {
+        const float v = acc * inv_wd;
+        acc = 0.0f;
+        if (kahan) kahan_add(sum, comp, v);
+        else sum += v;
     }
 };
 
 struct CountSink {
-    int loa, hia, lob, hib;
+    static constexpr bool plane = false;
+    SinkBox bx;
     unsigned int n;       // bases with a nonzero footprint
-    unsigned int pieces;  // integrated pieces (m Gauss nodes each)
+    unsigned int pieces;  // integrated pieces (GL nodes each)
     __device__ __forceinline__ void piece() { ++pieces; }
-    __device__ __forceinline__ void slab(int, float, int, float, int) {}
-    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return bx.meets(d0, d1, a0, a1, b0, b1);
     }
-    __device__ __forceinline__ void flush(int, int la, int lb, float v)
+    __device__ __forceinline__ void flush(int ld, int la, int lb, float v)
     {
-        n += (la >= loa && la <= hia && lb >= lob && lb <= hib && v > 0.0f) ? 1u : 0u;
+        n += (bx.holds(ld, la, lb) && v > 0.0f) ? 1u : 0u;
     }
+    __device__ __forceinline__ void cell_end() {}
 };
 
+// adjoint, scatter: y_r / |w_d| * F_l added to c_l with a float atomic
 struct AtomicSink {
+    static constexpr bool plane = false;
     float *__restrict__ c;
     int S0, S1, S2;
-    int loa, hia, lob, hib;
+    SinkBox bx;
     float yv;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float, int) {}
-    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return bx.meets(d0, d1, a0, a1, b0, b1);
     }
-    __device__ __forceinline__ void flush(int j, int la, int lb, float v)
+    __device__ __forceinline__ void flush(int ld, int la, int lb, float v)
     {
-        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(c + (j * S0 + la * S1 + lb * S2), yv * v);
+        if (bx.holds(ld, la, lb)) atomicAdd(c + (ld * S0 + la * S1 + lb * S2), yv * v);
     }
+    __device__ __forceinline__ void cell_end() {}
 };
 
-// brick of the gather adjoint: bounds in mirrored (d, a, b) coordinates and
-// the mirrored strides of the shared-memory brick array
+// brick of the gather adjoint: the region is the brick, the target the
+// shared-memory brick array (mirrored strides L, offset Loff)
 struct BrickSink {
+    static constexpr bool plane = false;
     float *part;
     int L0, L1, L2, Loff;
-    int loa, hia, lob, hib;
+    SinkBox bx;
     float yv;
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int, float, int, float, int) {}
-    __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
+    __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
-        return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
+        return bx.meets(d0, d1, a0, a1, b0, b1);
     }
-    __device__ __forceinline__ void flush(int j, int la, int lb, float v)
+    __device__ __forceinline__ void flush(int ld, int la, int lb, float v)
     {
-        if (la >= loa && la <= hia && lb >= lob && lb <= hib) atomicAdd(part + (j * L0 + la * L1 + lb * L2 + Loff), yv * v);
+        if (bx.holds(ld, la, lb)) atomicAdd(part + (ld * L0 + la * L1 + lb * L2 + Loff), yv * v);
     }
+    __device__ __forceinline__ void cell_end() {}
 };
 
 // ---------------------------------------------------------------- forward
@@ -106,35 +150,61 @@ __device__ __forceinline__ void tile_pixel(int &iu, int &iv)
     iv = blockIdx.y * 8 + (wid >> 1) * 4 + (lane >> 3);
 }
 
-template <int N>
+// View classes of a view-kernel launch.  VM_MIXED: cone views, the march
+// form (flat or general) is chosen per ray.  VM_FLAT / VM_GENERAL: parallel
+// views of one class, taken from the geometry's view order; the form is
+// fixed at compile time, so each kernel carries the registers of one form
+// only (a parallel view's rays share their direction, hence their form).
+enum { VM_MIXED = 0, VM_FLAT = 1, VM_GENERAL = 2, VM_RAYS = 3 };
+
+template <int N, int VM, class Sink>
+__device__ __forceinline__ bool march_vm(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sk)
+{
+    if constexpr (VM == VM_FLAT) return cell_march<N, Sink, true>(rs, cf, cl, qr, sk);
+    else if constexpr (VM == VM_GENERAL) return cell_march<N, Sink, false>(rs, cf, cl, qr, sk);
+    else return march<N>(rs, cf, cl, qr, sk);
+}
+
+// view of this block: blockIdx.z (VM_MIXED) or view_order[v_off + blockIdx.z]
+template <int VM>
+__device__ __forceinline__ int view_of(const DevGeom &g, int v_off)
+{
+    if constexpr (VM == VM_MIXED) return blockIdx.z;
+    else return g.view_order[v_off + blockIdx.z];
+}
+
+// blocks per SM the register budget is sized for: the flat form needs an
+// (n+1)^2 window, the general one (n+1)^3
+template <int VM> struct ViewBlocks { static constexpr int value = VM == VM_FLAT ? 6 : 3; };
+
+template <int N, int VM>
 __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *__restrict__ c, const QuadRule &qr,
                                                bool kahan, int *err)
 {
-    float sum = 0.0f, comp = 0.0f;
-    bool ok = true;
-#pragma unroll 1
-    for (int j = rs.j0; j <= rs.j1; ++j) {
-        FwdSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0.0f};
-        ok &= sweep<N>(rs, j, qr, sk);
-        const float v = sk.acc * rs.inv_wd;
-        if (kahan) kahan_add(sum, comp, v);
-        else sum += v;
-    }
-    if (!ok) atomicOr(err, 1);
-    return sum;
+    FwdSink sk;
+    sk.c = c;
+    sk.S0 = rs.S[0];
+    sk.S1 = rs.S[1];
+    sk.S2 = rs.S[2];
+    sk.bx = make_box(rs.lo, rs.hi);
+    sk.inv_wd = rs.inv_wd;
+    sk.kahan = kahan;
+    sk.acc = sk.sum = sk.comp = 0.0f;
+    if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
+    return sk.sum;
 }
 
-template <int N>
-__global__ void __launch_bounds__(128, 6) k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y,
-                                                       QuadRule qr, int kahan)
+template <int N, int VM>
+__global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
+    k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y, QuadRule qr, int kahan, int v_off)
 {
     int iu, iv;
     tile_pixel(iu, iv);
-    const int k = blockIdx.z;
+    const int k = view_of<VM>(g, v_off);
     if (iu >= g.nu || iv >= g.nv) return;
     RaySetup rs;
     float v = 0.0f;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) v = march_forward<N>(rs, c, qr, kahan != 0, g.err);
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) v = march_forward<N, VM>(rs, c, qr, kahan != 0, g.err);
     y[((long long)k * g.nv + iv) * g.nu + iu] = v;
 }
 
@@ -148,7 +218,7 @@ __global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__
     explicit_ray(g, r, s, w);
     RaySetup rs;
     float v = 0.0f;
-    if (ray_setup<N>(grid_of(g), s, w, rs)) v = march_forward<N>(rs, c, qr, kahan != 0, g.err);
+    if (ray_setup<N>(grid_of(g), s, w, rs)) v = march_forward<N, VM_RAYS>(rs, c, qr, kahan != 0, g.err);
     y[r] = v;
 }
 
@@ -157,11 +227,11 @@ template <int N>
 __device__ __forceinline__ void march_count(const RaySetup &rs, const QuadRule &qr, int *err, unsigned int &pairs,
                                             unsigned int &pieces, unsigned int &flat_pieces)
 {
-    CountSink sk{rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], 0u, 0u};
-    bool ok = true;
-#pragma unroll 1
-    for (int j = rs.j0; j <= rs.j1; ++j) ok &= sweep<N>(rs, j, qr, sk);
-    if (!ok) atomicOr(err, 1);
+    CountSink sk;
+    sk.bx = make_box(rs.lo, rs.hi);
+    sk.n = 0u;
+    sk.pieces = 0u;
+    if (!march<N>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
     pairs = sk.n;
     pieces = rs.rb == 0.0f ? 0u : sk.pieces;
     flat_pieces = rs.rb == 0.0f ? sk.pieces : 0u;
@@ -207,17 +277,18 @@ __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long lon
 }
 
 // ---------------------------------------------------------------- adjoint: ray-driven scatter
-template <int N>
+template <int N, int VM>
 __device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float *__restrict__ c, const QuadRule &qr,
                                             int *err)
 {
-    bool ok = true;
-#pragma unroll 1
-    for (int j = rs.j0; j <= rs.j1; ++j) {
-        AtomicSink sk{c, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2], yr * rs.inv_wd};
-        ok &= sweep<N>(rs, j, qr, sk);
-    }
-    if (!ok) atomicOr(err, 1);
+    AtomicSink sk;
+    sk.c = c;
+    sk.S0 = rs.S[0];
+    sk.S1 = rs.S[1];
+    sk.S2 = rs.S[2];
+    sk.bx = make_box(rs.lo, rs.hi);
+    sk.yv = yr * rs.inv_wd;
+    if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
 }
 
 template <int N>
@@ -231,22 +302,22 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
     double s[3], w[3];
     explicit_ray(g, r, s, w);
     RaySetup rs;
-    if (ray_setup<N>(grid_of(g), s, w, rs)) scatter_ray<N>(rs, yr, c, qr, g.err);
+    if (ray_setup<N>(grid_of(g), s, w, rs)) scatter_ray<N, VM_RAYS>(rs, yr, c, qr, g.err);
 }
 
 // view geometries, scatter form: the forward's thread mapping, float atomics
-template <int N>
-__global__ void __launch_bounds__(128, 6) k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y,
-                                                               float *__restrict__ c, QuadRule qr)
+template <int N, int VM>
+__global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
+    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr, int v_off)
 {
     int iu, iv;
     tile_pixel(iu, iv);
-    const int k = blockIdx.z;
+    const int k = view_of<VM>(g, v_off);
     if (iu >= g.nu || iv >= g.nv) return;
     const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
     if (yr == 0.0f) return;
     RaySetup rs;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N>(rs, yr, c, qr, g.err);
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM>(rs, yr, c, qr, g.err);
 }
 
 // ---------------------------------------------------------------- adjoint: brick gather (view geometries)
@@ -300,32 +371,36 @@ __device__ __forceinline__ bool pixel_window(const DevGeom &g, int k, const doub
     return false;
 }
 
-// Clip the slab range [jlo, jhi] of a ray to the slabs whose window can
-// reach the brick's transverse bounds (conservative by one slab).
-__device__ __forceinline__ void clip_to_brick(const RaySetup &rs, int W2, const int (&blo)[3], const int (&bhi)[3],
-                                              int &jlo, int &jhi)
+// Clip the cell range [cf, cl] of a ray to the cells whose window can hold a
+// basis of the brick: over cell c the window's a-range is
+// [floor(v_a(c)) - N, floor(v_a(c+1))], v_a(c) = V + (c - c0) r_a (same for
+// b).  Conservative by two cells; starting before the first such cell is
+// what keeps the brick's values equal to the full march's.
+template <int N>
+__device__ __forceinline__ void clip_cells_to_brick(const RaySetup &rs, const int (&blo)[3], const int (&bhi)[3],
+                                                    int &cf, int &cl)
 {
-    const float A0 = rs.Ah + rs.Al, B0 = rs.Bh + rs.Bl;
-    const float base[2] = {A0, B0};
+    const float base[2] = {rs.Vah + rs.Val, rs.Vbh + rs.Vbl};
     const float r[2] = {rs.ra, rs.rb}, ir[2] = {rs.inv_ra, rs.inv_rb};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        // window of slab j covers (A(j) - m, A(j) + m), A(j) = base + (j - j0) r
-        const float m = 0.5f * W2 * (1.0f + r[q]);
         if (r[q] > 0.0f) {
-            const float jl = rs.j0 + (blo[q + 1] - m - base[q]) * ir[q];
-            const float jh = rs.j0 + (bhi[q + 1] + m - base[q]) * ir[q];
-            jlo = max(jlo, (int)fmaxf(floorf(jl) - 1.0f, -1e9f));
-            jhi = min(jhi, (int)fminf(ceilf(jh) + 1.0f, 1e9f));
-        } else if (!(base[q] + m > blo[q + 1] && base[q] - m < bhi[q + 1])) {
-            jhi = jlo - 1;
+            const float cfl = rs.c0 + (blo[q + 1] - base[q]) * ir[q];
+            const float chl = rs.c0 + (bhi[q + 1] + N + 1 - base[q]) * ir[q];
+            cf = max(cf, (int)fmaxf(floorf(cfl) - 2.0f, -1e9f));
+            cl = min(cl, (int)fminf(ceilf(chl) + 1.0f, 1e9f));
+        } else if (!(base[q] + 1.0f > blo[q + 1] && base[q] - (N + 1) < bhi[q + 1])) {
+            cl = cf - 1;
         }
     }
 }
 
+// vlist: the views to walk (NULL: all views 0 .. nview-1); add: c += the
+// brick totals instead of c = them
 template <int N>
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const float *__restrict__ y,
-                                                                float *__restrict__ c, QuadRule qr, int bx, int by)
+                                                                float *__restrict__ c, QuadRule qr, int bx, int by,
+                                                                const int *vlist, int nview, int add)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     double *tot = (double *)smem;                                // kBrickVol FP64 totals
@@ -353,11 +428,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
     const GridBox gb = grid_of(g);
     const int lstride[3] = {1, kBrick, kBrick * kBrick};
     bool ok = true;
-    for (int k0 = 0; k0 < g.n_views; k0 += kViewBatch) {
-        const int nb = min(kViewBatch, g.n_views - k0);
+    __shared__ int vk[kViewBatch];
+    for (int k0 = 0; k0 < nview; k0 += kViewBatch) {
+        const int nb = min(kViewBatch, nview - k0);
         if (threadIdx.x < nb) {
+            const int kv = vlist ? vlist[k0 + threadIdx.x] : k0 + threadIdx.x;
+            vk[threadIdx.x] = kv;
             int u0, u1, v0, v1;
-            if (pixel_window(g, k0 + threadIdx.x, lo, hi, u0, u1, v0, v1)) {
+            if (pixel_window(g, kv, lo, hi, u0, u1, v0, v1)) {
                 u0 = 0;
                 u1 = g.nu - 1;
                 v0 = 0;
@@ -384,7 +462,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
             while (item >= woff[t + 1]) ++t;
             const int p = item - woff[t];
             const int iu = win[t][0] + p % win[t][1], iv = win[t][2] + p / win[t][1];
-            const int k = k0 + t;
+            const int k = vk[t];
             const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
             if (yr == 0.0f) continue;
             RaySetup rs;
@@ -400,14 +478,19 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
                 L[q] = rs.sg[q] * lstride[e];
                 Loff -= b0[e] * lstride[e];
             }
-            int jlo = max(rs.j0, blo[0]), jhi = min(rs.j1, bhi[0]);
-            clip_to_brick(rs, N + 1, blo, bhi, jlo, jhi);
-            const float yv = yr * rs.inv_wd;
-#pragma unroll 1
-            for (int j = jlo; j <= jhi; ++j) {
-                BrickSink sk{part, L[0], L[1], L[2], Loff, blo[1], bhi[1], blo[2], bhi[2], yv};
-                ok &= sweep<N>(rs, j, qr, sk);
-            }
+            // a brick basis l_d is live in cells l_d .. l_d + N
+            int cf = max(rs.c0, blo[0]), cl = min(rs.c1, bhi[0] + N);
+            clip_cells_to_brick<N>(rs, blo, bhi, cf, cl);
+            if (cf > cl) continue;
+            BrickSink sk;
+            sk.part = part;
+            sk.L0 = L[0];
+            sk.L1 = L[1];
+            sk.L2 = L[2];
+            sk.Loff = Loff;
+            sk.bx = make_box(blo, bhi);
+            sk.yv = yr * rs.inv_wd;
+            ok &= march<N>(rs, cf, cl, qr, sk);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < kBrickVol; i += kAdjThreads) {
@@ -419,8 +502,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
     if (!ok) atomicOr(g.err, 1);
     for (int i = threadIdx.x; i < kBrickVol; i += kAdjThreads) {
         const int lx = i % kBrick, ly = (i / kBrick) % kBrick, lz = i / (kBrick * kBrick);
-        if (lx < bn[0] && ly < bn[1] && lz < bn[2])
-            c[((long long)(b0[2] + lz) * g.n[1] + (b0[1] + ly)) * g.n[0] + (b0[0] + lx)] = (float)tot[i];
+        if (lx < bn[0] && ly < bn[1] && lz < bn[2]) {
+            float &dst = c[((long long)(b0[2] + lz) * g.n[1] + (b0[1] + ly)) * g.n[0] + (b0[0] + lx)];
+            dst = add ? (float)((double)dst + tot[i]) : (float)tot[i];
+        }
     }
 }
 
@@ -435,51 +520,102 @@ static spl_status launch_status(const char *what)
     return cuda_check(cudaGetLastError(), what);
 }
 
+// Parallel geometries: the separable group through the plane matrices
+// (when used), the other flat views with the flat kernel, the rest with the
+// general one.  Returns the first view_order index the flat kernel takes.
+static int plane_views(const spl_geometry *g, const spl_basis_desc *b, cudaStream_t st, spl_status *err)
+{
+    *err = SPL_OK;
+    if (b->separable == SPL_SEP_OFF || b->mode != SPL_FP_QUAD || !g->plane) return 0;
+    spl_status e;
+    const bool ok = plane_ready(const_cast<spl_geometry *>(g), b->degree, st, &e);
+    if (!ok && e != SPL_OK && e != SPL_ERR_OOM) *err = e;  // out of memory: walk the views instead
+    clear_error();
+    return ok ? g->dev.n_sep : 0;
+}
+
 template <int N>
-static spl_status forward_quad(const spl_geometry *g, const float *c, float *y, cudaStream_t st, int kahan)
+static spl_status forward_quad(const spl_geometry *g, const spl_basis_desc *b, const float *c, float *y, cudaStream_t st)
 {
     const DevGeom &dg = g->dev;
     const QuadRule qr = quad_rule(N);
+    const int kahan = b->kahan;
     if (dg.n_rays == 0) return SPL_OK;
     if (dg.kind == SPL_RAYS) {
         const long long blocks = (dg.n_rays + 127) / 128;
         k_forward_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, c, y, qr, kahan);
+    } else if (dg.kind == SPL_PARALLEL) {
+        spl_status s;
+        const int v0 = plane_views(g, b, st, &s);
+        if (s != SPL_OK) return s;
+        if (v0 > 0) {
+            s = plane_forward(g, N, kahan, c, y, st);
+            if (s != SPL_OK) return s;
+        }
+        const int nf = dg.n_flat - v0, ng = dg.n_views - dg.n_flat;
+        const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
+        if (nf > 0) k_forward_views<N, VM_FLAT><<<dim3(gx, gy, nf), 128, 0, st>>>(dg, c, y, qr, kahan, v0);
+        if (ng > 0) k_forward_views<N, VM_GENERAL><<<dim3(gx, gy, ng), 128, 0, st>>>(dg, c, y, qr, kahan, dg.n_flat);
     } else {
         dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
-        k_forward_views<N><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan);
+        k_forward_views<N, VM_MIXED><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan, 0);
     }
     return launch_status("forward launch");
 }
 
 template <int N>
-static spl_status adjoint_quad(const spl_geometry *g, const float *y, float *c, cudaStream_t st, int form)
+static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, const float *y, float *c, cudaStream_t st)
 {
     const DevGeom &dg = g->dev;
     const QuadRule qr = quad_rule(N);
+    const int form = b->adjoint;
     const long long nc = (long long)dg.n[0] * dg.n[1] * dg.n[2];
-    if (dg.kind == SPL_RAYS || form != SPL_ADJ_GATHER) {
-        spl_status s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
-        if (s != SPL_OK || dg.n_rays == 0) return s;
-        if (dg.kind == SPL_RAYS) {
-            const long long blocks = (dg.n_rays + 127) / 128;
-            k_adjoint_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, y, c, qr);
+    spl_status s;
+    int v0 = 0;
+    if (dg.kind == SPL_PARALLEL) {
+        v0 = plane_views(g, b, st, &s);
+        if (s != SPL_OK) return s;
+    }
+    if (v0 > 0) {
+        // the plane path writes every coefficient; the other views add
+        s = plane_adjoint(g, N, y, c, st);
+        if (s != SPL_OK) return s;
+    } else if (dg.kind == SPL_RAYS || form != SPL_ADJ_GATHER) {
+        s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
+        if (s != SPL_OK) return s;
+    }
+    if (dg.n_rays == 0) return SPL_OK;
+    if (dg.kind == SPL_RAYS) {
+        const long long blocks = (dg.n_rays + 127) / 128;
+        k_adjoint_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, y, c, qr);
+        return launch_status("adjoint launch");
+    }
+    if (form != SPL_ADJ_GATHER) {
+        const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
+        if (dg.kind == SPL_PARALLEL) {
+            const int nf = dg.n_flat - v0, ng = dg.n_views - dg.n_flat;
+            if (nf > 0) k_adjoint_views_scatter<N, VM_FLAT><<<dim3(gx, gy, nf), 128, 0, st>>>(dg, y, c, qr, v0);
+            if (ng > 0) k_adjoint_views_scatter<N, VM_GENERAL><<<dim3(gx, gy, ng), 128, 0, st>>>(dg, y, c, qr, dg.n_flat);
         } else {
-            dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
-            k_adjoint_views_scatter<N><<<grid, 128, 0, st>>>(dg, y, c, qr);
+            k_adjoint_views_scatter<N, VM_MIXED><<<dim3(gx, gy, dg.n_views), 128, 0, st>>>(dg, y, c, qr, 0);
         }
         return launch_status("adjoint launch");
     }
     static bool attr_set[4] = {false, false, false, false};
     if (!attr_set[N]) {
-        spl_status s = cuda_check(cudaFuncSetAttribute(k_adjoint_bricks<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)kAdjSmem),
-                                  "adjoint smem attribute");
+        s = cuda_check(cudaFuncSetAttribute(k_adjoint_bricks<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kAdjSmem),
+                       "adjoint smem attribute");
         if (s != SPL_OK) return s;
         attr_set[N] = true;
     }
     const int bx = (dg.n[0] + kBrick - 1) / kBrick, by = (dg.n[1] + kBrick - 1) / kBrick,
               bz = (dg.n[2] + kBrick - 1) / kBrick;
-    k_adjoint_bricks<N><<<bx * by * bz, kAdjThreads, kAdjSmem, st>>>(dg, y, c, qr, bx, by);
+    // bricks over the views the plane path did not take (all of them
+    // without it); with the plane path they add to its result
+    const int *vlist = v0 > 0 ? dg.view_order + v0 : nullptr;
+    const int nview = dg.n_views - v0;
+    k_adjoint_bricks<N><<<bx * by * bz, kAdjThreads, kAdjSmem, st>>>(dg, y, c, qr, bx, by, vlist, nview, v0 > 0 ? 1 : 0);
     return launch_status("adjoint launch");
 }
 
@@ -532,7 +668,7 @@ extern "C" spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *b
     if (s != SPL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (b->mode == SPL_FP_MLP) return spl::forward_mlp(g, b, c_dev, y_dev, st);
-    SPL_DISPATCH(b->degree, forward_quad, g, c_dev, y_dev, st, b->kahan)
+    SPL_DISPATCH(b->degree, forward_quad, g, b, c_dev, y_dev, st)
 }
 
 extern "C" spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *b, const float *y_dev, float *c_dev,
@@ -544,7 +680,7 @@ extern "C" spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *b
     if (b->mode == SPL_FP_MLP) return spl::adjoint_mlp(g, b, y_dev, c_dev, st);
     if (b->adjoint != SPL_ADJ_AUTO && b->adjoint != SPL_ADJ_GATHER && b->adjoint != SPL_ADJ_SCATTER)
         return fail(SPL_ERR_ARG, "unknown adjoint form %d", b->adjoint);
-    SPL_DISPATCH(b->degree, adjoint_quad, g, y_dev, c_dev, st, b->adjoint)
+    SPL_DISPATCH(b->degree, adjoint_quad, g, b, y_dev, c_dev, st)
 }
 
 extern "C" spl_status spl_count_pairs(const spl_geometry *g, int degree, unsigned long long *count_dev, void *stream)

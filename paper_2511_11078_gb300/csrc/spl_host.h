@@ -7,15 +7,52 @@
 #include "spl.h"
 #include "spl_march.cuh"
 
+namespace spl {
+struct PlaneGroup;
+}
+
 struct spl_geometry {
     spl_geometry_desc desc;       // copy of the description (host pointers cleared)
     spl::DevGeom dev;             // kernel-side view (device pointers)
     spl::ViewPose *views_host;    // host copy of the view poses
     void *dev_block;              // single device allocation: poses/rays + error flag
     int device;
+    spl::PlaneGroup *plane;       // slice-separable view group (parallel geometries), or NULL
 };
 
 namespace spl {
+
+// Plane matrices of a slice-separable view group for one degree (device
+// buffers, one allocation).  Row r = (group view g, detector column u) =
+// g * nu + u; column = l_q * n_p + l_p (real in-plane indices, p < q).
+struct PlanePack {
+    int state;                 // 0 not built, 1 built, -1 unavailable (allocation failed)
+    void *block;               // allocation of the row/column pointers, weights and scratch
+    void *block2;              // allocation of the nnz-sized arrays
+    long long nnz;
+    long long *row_ptr;        // [rows + 1]
+    int *row_col;              // [nnz] columns of each row, in march order
+    float *row_val;            // [nnz] G values (1/|w_d| included)
+    long long *col_ptr;        // [ncol + 1]
+    int *col_row;              // [nnz] rows of each column
+    float *col_val;            // [nnz]
+    int *lb0;                  // [nv] first b-basis whose support holds detector row v
+    float *wz;                 // [nv][degree+1] beta^n(z_v - l_b), l_b = lb0[v] + i
+    int *vr;                   // [n_b][2] rows v whose b-window holds basis l_b (inclusive range)
+    float *S;                  // [ncol][nv] forward scratch: c resampled along b
+    float *T;                  // [ncol][nv] adjoint scratch
+    float *yt;                 // [rows][nv] adjoint scratch: y of the group, transposed
+};
+
+// Slice-separable view group of a parallel geometry (host object).
+struct PlaneGroup {
+    int b, p, q;               // separable axis and the in-plane axes (p < q)
+    int n_views;               // views in the group: dev.view_order[0 .. n_views)
+    long long rows;            // n_views * nu
+    long long ncol;            // n_p * n_q
+    double z0, dz;             // b index coordinate of detector row v: z0 + v * dz
+    PlanePack pack[4];         // per degree
+};
 
 // Record `msg` as the calling thread's last error and return `st`.
 spl_status fail(spl_status st, const char *fmt, ...);
@@ -35,5 +72,14 @@ int quad_nodes(int degree);
 
 // Validate a basis descriptor against a geometry (nullable).
 spl_status check_basis(const spl_basis_desc *b);
+
+// Plane-matrix path of slice-separable views (plane.cu).  plane_ready
+// builds the degree's pack on first use; false when the geometry has no
+// group or the pack is unavailable.
+bool plane_ready(spl_geometry *g, int degree, cudaStream_t st, spl_status *err);
+spl_status plane_forward(const spl_geometry *g, int degree, int kahan, const float *c, float *y, cudaStream_t st);
+// writes every coefficient (the other views' scatter adds after it)
+spl_status plane_adjoint(const spl_geometry *g, int degree, const float *y, float *c, cudaStream_t st);
+void plane_free(PlaneGroup *pg);
 
 }  // namespace spl

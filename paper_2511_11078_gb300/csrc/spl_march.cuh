@@ -126,6 +126,9 @@ struct DevGeom {
     int n_views, nu, nv;
     long long n_rays;
     const ViewPose *views;
+    const int *view_order;  // parallel views: the slice-separable group, the other flat views (r_b = 0), the rest
+    int n_sep;              // views of the slice-separable group (view_order[0 .. n_sep))
+    int n_flat;             // flat views, the group included (view_order[0 .. n_flat))
     const double *ray_w; // [n_rays][3] unit directions
     const double *ray_s; // [n_rays][3]
     int *err;            // device error flag (bit 0: a loop bound was reached)
@@ -238,15 +241,17 @@ struct RaySetup {
     float inv_ra, inv_rb;
     float inv_wd;    // 1 / |w_d|
     int j0, j1;      // mirrored slab range (inclusive), reference slab j0
+    int c0, c1;      // cell range of the cell march (inclusive), reference cell c0
     int lo[3], hi[3];  // mirrored grid bounds of (d, a, b)
     int S[3];        // signed linear strides of (d, a, b) in mirrored coordinates
     float Ah, Al, Bh, Bl;  // transverse coordinates at slab j0 (double-float)
+    float Vah, Val, Vbh, Vbl;  // shifted transverse coordinates v = u + W at v_d = c0 (double-float)
     float rah, ral, rbh, rbl;
 };
 
-// Position-dependent part: slab range of the ray and its transverse
-// coordinates on the reference slab.  Returns false when the ray meets no
-// basis support of the grid.  FP64, a few dozen operations.
+// Position-dependent part: slab and cell ranges of the ray and its
+// transverse coordinates on the reference slab and cell.  Returns false when
+// the ray meets no basis support of the grid.  FP64, a few dozen operations.
 template <int N>
 __device__ __forceinline__ bool pos_setup(const GridBox &gb, const DirSetup &ds, const double (&s)[3], RaySetup &rs)
 {
@@ -276,19 +281,52 @@ __device__ __forceinline__ bool pos_setup(const GridBox &gb, const DirSetup &ds,
             return false;
         }
     }
-    if (!(jmax >= jmin - 1.0)) return false;
-    // one slab of margin on both ends; extra slabs only add empty windows
-    const double jl = fmax(floor(jmin) - 1.0, (double)rs.lo[0]);
-    const double jh = fmin(ceil(jmax) + 1.0, (double)rs.hi[0]);
-    if (jl > jh) return false;
-    rs.j0 = (int)jl;
-    rs.j1 = (int)jh;
+    // slab range: one slab of margin on both ends; extra slabs only add
+    // empty windows
+    rs.j0 = 0;
+    rs.j1 = -1;
+    if (jmax >= jmin - 1.0) {
+        const double jl = fmax(floor(jmin) - 1.0, (double)rs.lo[0]);
+        const double jh = fmin(ceil(jmax) + 1.0, (double)rs.hi[0]);
+        if (jl <= jh) {
+            rs.j0 = (int)jl;
+            rs.j1 = (int)jh;
+        }
+    }
+    // cell range (cell_march): with v = u + W, the grid's bases meet the
+    // line where v_d is in (lo_d, hi_d + 2W) and each transverse v_e is in
+    // (lo_e, hi_e + 2W); one cell of margin on both ends
+    double vmin = rs.lo[0], vmax = rs.hi[0] + 2.0 * W;
+#pragma unroll
+    for (int q = 1; q < 3; ++q) {
+        if (ds.r[q - 1] > 0.0) {
+            vmin = fmax(vmin, fma(rs.lo[q] - W - sp[q], ds.invr[q - 1], sp[0] + W));
+            vmax = fmin(vmax, fma(rs.hi[q] + W - sp[q], ds.invr[q - 1], sp[0] + W));
+        }
+    }
+    rs.c0 = 0;
+    rs.c1 = -1;
+    if (vmax >= vmin - 1.0) {
+        const double cl = fmax(floor(vmin) - 1.0, (double)rs.lo[0]);
+        const double ch = fmin(floor(vmax) + 1.0, (double)(rs.hi[0] + N));
+        if (cl <= ch) {
+            rs.c0 = (int)cl;
+            rs.c1 = (int)ch;
+        }
+    }
+    if (rs.j0 > rs.j1 && rs.c0 > rs.c1) return false;
     const double A = fma(rs.j0 - sp[0], ds.r[0], sp[1]);
     const double B = fma(rs.j0 - sp[0], ds.r[1], sp[2]);
     rs.Ah = (float)A;
     rs.Al = (float)(A - (double)rs.Ah);
     rs.Bh = (float)B;
     rs.Bl = (float)(B - (double)rs.Bh);
+    const double Va = fma(rs.c0 - W - sp[0], ds.r[0], sp[1]) + W;
+    const double Vb = fma(rs.c0 - W - sp[0], ds.r[1], sp[2]) + W;
+    rs.Vah = (float)Va;
+    rs.Val = (float)(Va - (double)rs.Vah);
+    rs.Vbh = (float)Vb;
+    rs.Vbl = (float)(Vb - (double)rs.Vbh);
     rs.rah = ds.rah;
     rs.ral = ds.ral;
     rs.rbh = ds.rbh;
@@ -495,6 +533,207 @@ __device__ __forceinline__ bool sweep(const RaySetup &rs, int j, const QuadRule 
 {
     if (rs.rb == 0.0f) return slab_sweep<N, Sink, true, true>(rs, j, qr, sink);
     return slab_sweep<N, Sink, true, false>(rs, j, qr, sink);
+}
+
+// ------------------------------------------------------------------ cell march
+// Cells along d*.  With v = u + W the bases of one axis sit at the integers
+// and basis l covers v in (l, l + N + 1), so the N+1 bases whose support
+// contains a point of cell [c, c+1) are l = c - N .. c, weighted by
+// bweights(v - c).  The march walks the cells of a ray along d*.  Inside a
+// cell the ray crosses at most one knot plane per transverse axis (r <= 1),
+// so a cell splits into at most three pieces, and on each piece every factor
+// of every live basis is one polynomial of degree N (product: degree 3N,
+// GL<N>::M nodes).  An (N+1)^3 register window holds the live bases
+// (offsets d, a, b) and all of them share each node's three weight sets:
+// per node 3 (N+1) weights and (N+1)^3 FMAs.  When the ray crosses a
+// transverse knot plane the bases behind it are flushed and the window
+// shifts; at the end of a cell the lowest d-layer is flushed.  Each basis
+// whose support the ray crosses is flushed exactly once, through
+// sink.flush(l_d, l_a, l_b, F) with F = |w_d| Pphi(w, s - l) (the sink
+// scales by 1/|w_d|).  Compared with the slab sweep, which integrates every
+// point of the ray once for each of the N+1 slabs whose d-support holds it,
+// the node weights are evaluated once per point.
+//
+// Transverse positions: v_a at the start of cell c is a double-float
+// (df_coord), exact to ~1e-7 anywhere on the ray.  The window's a-frame QA
+// (it holds l_a = QA - N .. QA) only moves up; the a-crossings inside cell c
+// are the integers in (QA, v_a(c+1)].  The window state at the start of a
+// cell depends only on the cell, so a march over a sub-range of cells that
+// starts before the first cell where a basis is live gives that basis the
+// same value as the full march (the brick adjoint relies on it).
+//
+// FLAT (r_b = 0): the b-weights are constant along the ray; the window keeps
+// the (N+1)^2 integrals over the d- and a-factors (degree 2N, N+1 nodes)
+// and the flush multiplies them by the b-weights.
+//
+// Sink::plane (FLAT only): the sink takes G = F / w_b, one flush per
+// (l_d, l_a), for the plane-matrix path of slice-separable views.
+// Sink: relevant(d0, d1, a0, a1, b0, b1) says whether any basis of the
+// window matters (pieces that reach none are not integrated); piece()
+// counts an integrated piece; cell_end() closes a cell.  The per-cell event
+// loop is bounded by qr.cap; reaching it (or a crossing count that r <= 1
+// rules out) returns false.
+template <int N, class Sink, bool FLAT>
+__device__ __forceinline__ bool cell_march(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sink)
+{
+    constexpr int NB = FLAT ? 1 : N + 1;
+    constexpr int M = FLAT ? N + 1 : GL<N>::M;
+    if (cf > cl) return true;
+    float acc[N + 1][N + 1][NB];
+#pragma unroll
+    for (int d = 0; d <= N; ++d)
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
+#pragma unroll
+            for (int k = 0; k < NB; ++k) acc[d][i][k] = 0.0f;
+    int IA, IB;
+    float fa, fb;
+    df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, cf - rs.c0, IA, fa);
+    df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, cf - rs.c0, IB, fb);
+    int QA = IA, QB = IB;
+    float wbf[N + 1];  // FLAT: the constant b-weights
+    if constexpr (FLAT) bweights<N>(fb, wbf);
+    // plane sinks (FLAT only) take the integrals over the d- and a-factors
+    // themselves, one flush per (l_d, l_a) with l_b = 0
+    constexpr bool PLANE = FLAT && Sink::plane;
+    constexpr int KF = PLANE ? 1 : N + 1;
+#define SPL_CELL_VAL(d, i, k) \
+    (FLAT ? (PLANE ? acc[d][i][0] : acc[d][i][0] * wbf[k]) : acc[d][i][(FLAT ? 0 : k)])
+#pragma unroll 1
+    for (int c = cf; c <= cl; ++c) {
+        int IAn, IBn = IB;
+        float fan, fbn = fb;
+        df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, c + 1 - rs.c0, IAn, fan);
+        if constexpr (!FLAT) df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, c + 1 - rs.c0, IBn, fbn);
+        int na = IAn - QA, nb = IBn - QB;  // knot crossings inside the cell
+        if (na > 2 || nb > 2) return false;
+        float ga = (float)(IA - QA) + fa;  // v - frame at the cell start
+        float gb = (float)(IB - QB) + fb;
+        float ta = na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+        float tb = nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+        float t0 = 0.0f;
+#pragma unroll 1
+        for (int it = 0;; ++it) {
+            if (it >= qr.cap) return false;
+            const float t1 = fminf(fminf(ta, tb), 1.0f);
+            if (t1 > t0 && sink.relevant(c - N, c, QA - N, QA, QB - N, QB)) {
+                const float half = 0.5f * (t1 - t0), mid = 0.5f * (t0 + t1);
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    const float t = fmaf(half, FLAT ? qr.x1[q] : qr.x[q], mid);
+                    float wd[N + 1], wa[N + 1];
+                    bweights<N>(t, wd);
+                    bweights<N>(fmaf(rs.ra, t, ga), wa);
+                    const float cw = half * (FLAT ? qr.w1[q] : qr.w[q]);
+#pragma unroll
+                    for (int d = 0; d <= N; ++d) wd[d] *= cw;
+                    if constexpr (FLAT) {
+#pragma unroll
+                        for (int d = 0; d <= N; ++d)
+#pragma unroll
+                            for (int i = 0; i <= N; ++i) acc[d][i][0] = fmaf(wd[d], wa[i], acc[d][i][0]);
+                    } else {
+                        float wb[N + 1];
+                        bweights<N>(fmaf(rs.rb, t, gb), wb);
+#pragma unroll
+                        for (int i = 0; i <= N; ++i)
+#pragma unroll
+                            for (int k = 0; k <= N; ++k) {
+                                const float pk = wa[i] * wb[k];
+#pragma unroll
+                                for (int d = 0; d <= N; ++d)
+                                    acc[d][i][(FLAT ? 0 : k)] = fmaf(wd[d], pk, acc[d][i][(FLAT ? 0 : k)]);
+                            }
+                    }
+                }
+                sink.piece();
+            }
+            t0 = fmaxf(t0, t1);
+            if (ta <= tb && ta <= 1.0f) {
+                // the lowest a-row leaves the ray's reach
+#pragma unroll
+                for (int d = 0; d <= N; ++d)
+#pragma unroll
+                    for (int k = 0; k < KF; ++k) sink.flush(c - N + d, QA - N, QB - N + k, SPL_CELL_VAL(d, 0, k));
+#pragma unroll
+                for (int d = 0; d <= N; ++d) {
+#pragma unroll
+                    for (int i = 0; i < N; ++i)
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) acc[d][i][k] = acc[d][i + 1][k];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) acc[d][N][k] = 0.0f;
+                }
+                ++QA;
+                ga -= 1.0f;
+                ta = --na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+            } else if (tb <= 1.0f) {
+                // the lowest b-column leaves (never for FLAT: nb == 0)
+#pragma unroll
+                for (int d = 0; d <= N; ++d)
+#pragma unroll
+                    for (int i = 0; i <= N; ++i) sink.flush(c - N + d, QA - N + i, QB - N, SPL_CELL_VAL(d, i, 0));
+                if constexpr (!FLAT) {
+#pragma unroll
+                    for (int d = 0; d <= N; ++d)
+#pragma unroll
+                        for (int i = 0; i <= N; ++i) {
+#pragma unroll
+                            for (int k = 0; k < N; ++k) acc[d][i][(FLAT ? 0 : k)] = acc[d][i][(FLAT ? 0 : k + 1)];
+                            acc[d][i][(FLAT ? 0 : N)] = 0.0f;
+                        }
+                }
+                ++QB;
+                gb -= 1.0f;
+                tb = --nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+            } else {
+                break;
+            }
+        }
+        // end of the cell: the lowest d-layer leaves
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
+#pragma unroll
+            for (int k = 0; k < KF; ++k) sink.flush(c - N, QA - N + i, QB - N + k, SPL_CELL_VAL(0, i, k));
+#pragma unroll
+        for (int d = 0; d < N; ++d)
+#pragma unroll
+            for (int i = 0; i <= N; ++i)
+#pragma unroll
+                for (int k = 0; k < NB; ++k) acc[d][i][k] = acc[d + 1][i][k];
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
+#pragma unroll
+            for (int k = 0; k < NB; ++k) acc[N][i][k] = 0.0f;
+        sink.cell_end();
+        IA = IAn;
+        fa = fan;
+        IB = IBn;
+        fb = fbn;
+    }
+    // what the window still holds (layers l_d = cl+1-N .. cl; the top one is
+    // empty) is flushed once: bases outside the sink's region, or complete
+    // ones when the cell range was clipped
+#pragma unroll
+    for (int d = 0; d < N; ++d)
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
+#pragma unroll
+            for (int k = 0; k < KF; ++k) sink.flush(cl + 1 - N + d, QA - N + i, QB - N + k, SPL_CELL_VAL(d, i, k));
+    sink.cell_end();
+#undef SPL_CELL_VAL
+    return true;
+}
+
+// Cell march over cells [cf, cl] with the form the ray needs: FLAT when the
+// ray has a zero transverse component (r_b = 0).  Every exact-footprint
+// kernel goes through here, so a ray gets the same footprint values in the
+// forward, the adjoint, the pair count and the footprint evaluator.
+template <int N, class Sink>
+__device__ __forceinline__ bool march(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sink)
+{
+    if (rs.rb == 0.0f) return cell_march<N, Sink, true>(rs, cf, cl, qr, sink);
+    return cell_march<N, Sink, false>(rs, cf, cl, qr, sink);
 }
 
 // ------------------------------------------------------------------ rays of a geometry

@@ -18,6 +18,7 @@ SPL_OK = 0
 SPL_RAYS, SPL_PARALLEL, SPL_CONE = 0, 1, 2
 SPL_FP_QUAD, SPL_FP_MLP = 0, 1
 SPL_ADJ_AUTO, SPL_ADJ_GATHER, SPL_ADJ_SCATTER = 0, 1, 2
+SPL_SEP_AUTO, SPL_SEP_OFF = 0, 1
 MLP_PARAMS = 8769
 STATUS_NAMES = {0: "SPL_OK", 1: "SPL_ERR_ARG", 2: "SPL_ERR_NONFINITE", 3: "SPL_ERR_CUDA", 4: "SPL_ERR_STEPCAP",
                 5: "SPL_ERR_OOM", 6: "SPL_ERR_STATE", 7: "SPL_ERR_UNSUPPORTED"}
@@ -44,7 +45,8 @@ class GeometryDesc(C.Structure):
 
 
 class BasisDesc(C.Structure):
-    _fields_ = [("degree", C.c_int), ("mode", C.c_int), ("mlp", _vp), ("kahan", C.c_int), ("adjoint", C.c_int)]
+    _fields_ = [("degree", C.c_int), ("mode", C.c_int), ("mlp", _vp), ("kahan", C.c_int), ("adjoint", C.c_int),
+                ("separable", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -57,6 +59,7 @@ _SIGS = {
     "spl_geometry_rays": (C.c_longlong, [_vp]),
     "spl_geometry_coeffs": (C.c_longlong, [_vp]),
     "spl_geometry_status": (C.c_int, [_vp, _vp]),
+    "spl_prepare": (C.c_int, [_vp, C.POINTER(BasisDesc), _vp]),
     "spl_forward": (C.c_int, [_vp, C.POINTER(BasisDesc), _vp, _vp, _vp]),
     "spl_adjoint": (C.c_int, [_vp, C.POINTER(BasisDesc), _vp, _vp, _vp]),
     "spl_count_pairs": (C.c_int, [_vp, C.c_int, _vp, _vp]),
@@ -197,11 +200,19 @@ class Geometry:
         check(lib().spl_geometry_status(self._h, _stream(stream)))
 
 
-def basis(degree: int, mode: int = SPL_FP_QUAD, mlp=None, kahan: bool = True, adjoint: int = SPL_ADJ_AUTO) -> BasisDesc:
+def basis(degree: int, mode: int = SPL_FP_QUAD, mlp=None, kahan: bool = True, adjoint: int = SPL_ADJ_AUTO,
+          separable: int = SPL_SEP_AUTO) -> BasisDesc:
     b = BasisDesc()
     b.degree, b.mode, b.kahan, b.adjoint = int(degree), int(mode), 1 if kahan else 0, int(adjoint)
+    b.separable = int(separable)
     b.mlp = mlp.handle if mlp is not None else None
     return b
+
+
+def prepare(geom: Geometry, bas: BasisDesc, stream=None):
+    """Build the plane matrices of the geometry's slice-separable views for
+    this basis (done by the first forward/adjoint otherwise)."""
+    check(lib().spl_prepare(geom.handle, C.byref(bas), _stream(stream)))
 
 
 def forward(geom: Geometry, c, y, bas: BasisDesc, stream=None):

@@ -112,4 +112,5 @@ def test_null_arguments_are_rejected(spl):
     assert L.spl_footprint(C.byref(bad), 1, None, None, None, None) == 1
     assert L.spl_dot_f64(4, None, None, None, None, 0, None) == 1
     assert L.spl_count_pairs(None, 3, None, None) == 1
+    assert L.spl_prepare(None, C.byref(b), None) == 1
     assert L.spl_features(7, 1, None, None, None, None) == 1
