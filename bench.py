@@ -7,7 +7,10 @@ random directions, 192x192 detector, pitch 1; data y = A c_true + Gaussian
 noise (sigma = 1% of max).  One step = one CGLS iteration of the
 least-squares problem of Eq. 5: one forward projection A, one matched
 adjoint A^T, two FP64 inner products and the two CG vector updates, all on
-the GPU with the exact quadrature footprint.
+the GPU with the exact quadrature footprint.  The 180 tilt views are
+slice-separable (flat rays, detector rows along e3) and go through the plane
+matrices (built once, outside the timed region); the 64 random views through
+the cell march.  view_classes reports A and A^T of each class alone.
 
 Metric: contributions (ray, basis pairs of Eq. 4) processed per second by
 A and A^T, in G-contributions/s; also seconds per reconstruction iteration.
@@ -315,6 +318,26 @@ def run_ours(args):
     y = y_clean + sigma * torch.randn(y_clean.shape, generator=gen, device=dev)
     pairs, pieces, flat_pieces = spl.count_work(geom, n)
     geom.status()
+    # one-time plane-matrix build of the slice-separable views (outside the
+    # timed region; the first forward above already did it, this reads the
+    # cost on a fresh geometry)
+    g_fresh = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter()
+    spl.prepare(g_fresh, proj.basis)
+    torch.cuda.synchronize()
+    plane_build_s = time.perf_counter() - t_build
+    del g_fresh
+    # view classes: slice-separable (plane matrices) and general (cell march)
+    src = np.asarray(wl.geometry.src)
+    flat = np.any(src == 0.0, axis=1)
+    classes = {}
+    for name, views in (("separable", np.nonzero(flat)[0]), ("general", np.nonzero(~flat)[0])):
+        if len(views) == 0:
+            continue
+        gsub = spl.Geometry(wl.dims, wl.origin, wl.geometry.subset_views(views))
+        p_, pc_, pf_ = spl.count_work(gsub, n)
+        classes[name] = {"views": int(len(views)), "geom": gsub, "pairs": p_, "pieces": pc_, "flat_pieces": pf_}
 
     cg = CGLS(proj, y)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
@@ -377,6 +400,34 @@ def run_ours(args):
     fwd = statistics.median(fwd_ms)
     adj = statistics.median(adj_ms)
 
+    # per view class: A and A^T of the class alone (the same kernels and launch
+    # shapes as inside the step), events around each call after an L2 flush
+    def time_call(fn, reps=3):
+        out = []
+        for _ in range(reps):
+            l2_flush()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            fn()
+            t1.record(stream)
+            torch.cuda.synchronize()
+            out.append(t0.elapsed_time(t1))
+        return statistics.median(out)
+
+    per_class = {}
+    for name, cl in classes.items():
+        gsub = cl["geom"]
+        ysub = torch.empty(gsub.n_rays, dtype=torch.float32, device=dev)
+        csub = torch.empty(gsub.coeff_shape, dtype=torch.float32, device=dev)
+        spl.forward(gsub, c_true, ysub, proj.basis)
+        spl.adjoint(gsub, ysub, csub, proj.basis)
+        a_ms = time_call(lambda: spl.forward(gsub, c_true, ysub, proj.basis))
+        at_ms = time_call(lambda: spl.adjoint(gsub, ysub, csub, proj.basis))
+        gsub.status()
+        per_class[name] = {"views": cl["views"], "contributions_per_A": cl["pairs"], "A_ms": a_ms, "AT_ms": at_ms,
+                           "A_gcontrib_s": cl["pairs"] / (a_ms * 1e-3) / 1e9,
+                           "AT_gcontrib_s": cl["pairs"] / (at_ms * 1e-3) / 1e9}
+
     contrib_step = 2 * pairs  # A and A^T visit the same pairs
     value = ws * contrib_step / (ms * 1e-3) / 1e9
 
@@ -409,16 +460,31 @@ def run_ours(args):
     peaks = measured_peaks()
     max_mhz = (clocks.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
     fp32_peak_tflops = SMS * FP32_LANES * 2 * max_mhz * 1e6 / 1e12
-    flops_fwd = (pieces * NODES_PER_PIECE[n] * FLOP_PER_NODE[n] + flat_pieces * (n + 1) * FLOP_PER_FLAT_NODE[n]
-                 + pairs * FLOP_PER_PAIR)
-    dominant = "k_forward_views" if fwd >= adj else (
-        "k_adjoint_bricks" if args.adjoint == "gather" else "k_adjoint_views_scatter")
-    dom_ms = max(fwd, adj)
-    achieved = flops_fwd / (dom_ms * 1e-3) / 1e12
+    # dominant kernel: the cell march of the general views (one launch per
+    # A or A^T); its algorithmic FP32 work is the nodes it integrates plus
+    # one FMA per contribution
+    gen = classes.get("general", classes.get("separable"))
+    flops_gen = (gen["pieces"] * NODES_PER_PIECE[n] * FLOP_PER_NODE[n]
+                 + gen["flat_pieces"] * (n + 1) * FLOP_PER_FLAT_NODE[n] + gen["pairs"] * FLOP_PER_PAIR)
+    pc_gen = per_class["general" if "general" in per_class else "separable"]
+    if pc_gen["A_ms"] >= pc_gen["AT_ms"]:
+        dominant, dom_ms = "k_forward_views (general views)", pc_gen["A_ms"]
+    else:
+        dominant = ("k_adjoint_bricks" if args.adjoint == "gather" else
+                    "k_adjoint_views_scatter (general views)")
+        dom_ms = pc_gen["AT_ms"]
+    achieved = flops_gen / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get(dominant),
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+                "traffic": NCU_TRAFFIC.get(dominant.split(" ")[0]),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz max SM clock" % max_mhz,
-                "algorithmic_flop_per_launch": flops_fwd}
+                "algorithmic_flop_per_launch": flops_gen,
+                "launch_ms": dom_ms}
+    n_sep = per_class.get("separable", {}).get("views", 0)
+    n_gen = per_class.get("general", {}).get("views", 0)
+    launches_step = ((2 if n_sep else 0) + (1 if n_gen else 0)      # A: z-resample + row gather, cell march
+                     + (3 if n_sep else 0) + (1 if n_gen else 0)    # A^T: transpose + column gather + z-adjoint, scatter
+                     + 2 * 2 + 2)                                   # two FP64 dots (2 kernels each), two CG updates
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -435,7 +501,9 @@ def run_ours(args):
             "A_gcontrib_s": pairs / (fwd * 1e-3) / 1e9, "AT_gcontrib_s": pairs / (adj * 1e-3) / 1e9,
             "e2e": {"value": ws * contrib_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": args.steps * 8,
+            "gpu_launches": args.steps * launches_step,
+            "view_classes": per_class,
+            "plane_build_s": plane_build_s,
             "clocks": clocks,
             "roofline": roofline,
             "wall_s_timed_region": t_wall}
