@@ -10,9 +10,22 @@
 
 namespace spl {
 
+// the region is the single basis (0, 0, 0); it is the only one put() is
+// told is in it, so the strides do not matter
 struct PointSink {
     static constexpr bool plane = false;
     float v;
+    int S0 = 0, S1 = 0, S2 = 0;
+    unsigned off = 0u;
+    struct Box {
+        __device__ __forceinline__ bool in0(int d) const { return d == 0; }
+        __device__ __forceinline__ bool in1(int a) const { return a == 0; }
+        __device__ __forceinline__ bool in2(int b) const { return b == 0; }
+    } bx;
+    __device__ __forceinline__ void put(unsigned, bool in, float val)
+    {
+        if (in) v = val;
+    }
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
@@ -42,7 +55,8 @@ __device__ __forceinline__ float footprint_exact(const double (&w)[3], const dou
 {
     RaySetup rs;
     if (!ray_setup<N>(unit_box(), p, w, rs)) return 0.0f;
-    PointSink sk{0.0f};
+    PointSink sk;
+    sk.v = 0.0f;
     march<N>(rs, rs.c0, rs.c1, qr, sk);
     return sk.v * rs.inv_wd;
 }

@@ -39,6 +39,9 @@ struct SinkBox {
     {
         return (unsigned)(d - lo0) <= ext0 && (unsigned)(a - lo1) <= ext1 && (unsigned)(b - lo2) <= ext2;
     }
+    __device__ __forceinline__ bool in0(int d) const { return (unsigned)(d - lo0) <= ext0; }
+    __device__ __forceinline__ bool in1(int a) const { return (unsigned)(a - lo1) <= ext1; }
+    __device__ __forceinline__ bool in2(int b) const { return (unsigned)(b - lo2) <= ext2; }
     // whether the window [d0, d1] x [a0, a1] x [b0, b1] meets the region
     __device__ __forceinline__ bool meets(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
@@ -60,10 +63,15 @@ __device__ __forceinline__ SinkBox make_box(const int (&lo)[3], const int (&hi)[
 }
 
 // forward: sum of c_l * F_l along the ray, Kahan-compensated per cell
+// Sinks take a basis either by index (flush, the flat cell march) or by its
+// offset in the sink's layout, off + l_d S0 + l_a S1 + l_b S2 in unsigned
+// (wrapping) arithmetic, with a flag that it lies in the region (put, the
+// piece march).
 struct FwdSink {
     static constexpr bool plane = false;
     const float *__restrict__ c;
     int S0, S1, S2;
+    unsigned off;
     SinkBox bx;
     float inv_wd;
     bool kahan;
@@ -77,6 +85,10 @@ struct FwdSink {
     {
         if (bx.holds(ld, la, lb)) acc = fmaf(__ldg(c + (ld * S0 + la * S1 + lb * S2)), v, acc);
     }
+    __device__ __forceinline__ void put(unsigned o, bool in, float v)
+    {
+        if (in) acc = fmaf(__ldg(c + o), v, acc);
+    }
     __device__ __forceinline__ void cell_end()
     {
         const float v = acc * inv_wd;
@@ -88,6 +100,8 @@ struct FwdSink {
 
 struct CountSink {
     static constexpr bool plane = false;
+    int S0, S1, S2;
+    unsigned off;
     SinkBox bx;
     unsigned int n;       // bases with a nonzero footprint
     unsigned int pieces;  // integrated pieces (GL nodes each)
@@ -100,6 +114,7 @@ struct CountSink {
     {
         n += (bx.holds(ld, la, lb) && v > 0.0f) ? 1u : 0u;
     }
+    __device__ __forceinline__ void put(unsigned, bool in, float v) { n += (in && v > 0.0f) ? 1u : 0u; }
     __device__ __forceinline__ void cell_end() {}
 };
 
@@ -108,6 +123,7 @@ struct AtomicSink {
     static constexpr bool plane = false;
     float *__restrict__ c;
     int S0, S1, S2;
+    unsigned off;
     SinkBox bx;
     float yv;
     __device__ __forceinline__ void piece() {}
@@ -119,15 +135,20 @@ struct AtomicSink {
     {
         if (bx.holds(ld, la, lb)) atomicAdd(c + (ld * S0 + la * S1 + lb * S2), yv * v);
     }
+    __device__ __forceinline__ void put(unsigned o, bool in, float v)
+    {
+        if (in) atomicAdd(c + o, yv * v);
+    }
     __device__ __forceinline__ void cell_end() {}
 };
 
 // brick of the gather adjoint: the region is the brick, the target the
-// shared-memory brick array (mirrored strides L, offset Loff)
+// shared-memory brick array (mirrored strides S0..S2, offset off)
 struct BrickSink {
     static constexpr bool plane = false;
     float *part;
-    int L0, L1, L2, Loff;
+    int S0, S1, S2;
+    unsigned off;
     SinkBox bx;
     float yv;
     __device__ __forceinline__ void piece() {}
@@ -137,7 +158,11 @@ struct BrickSink {
     }
     __device__ __forceinline__ void flush(int ld, int la, int lb, float v)
     {
-        if (bx.holds(ld, la, lb)) atomicAdd(part + (ld * L0 + la * L1 + lb * L2 + Loff), yv * v);
+        if (bx.holds(ld, la, lb)) atomicAdd(part + (unsigned)(ld * S0 + la * S1 + lb * S2 + (int)off), yv * v);
+    }
+    __device__ __forceinline__ void put(unsigned o, bool in, float v)
+    {
+        if (in) atomicAdd(part + o, yv * v);
     }
     __device__ __forceinline__ void cell_end() {}
 };
@@ -161,7 +186,7 @@ template <int N, int VM, class Sink>
 __device__ __forceinline__ bool march_vm(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sk)
 {
     if constexpr (VM == VM_FLAT) return cell_march<N, Sink, true>(rs, cf, cl, qr, sk);
-    else if constexpr (VM == VM_GENERAL) return cell_march<N, Sink, false>(rs, cf, cl, qr, sk);
+    else if constexpr (VM == VM_GENERAL) return piece_march<N, Sink>(rs, cf, cl, qr, sk);
     else return march<N>(rs, cf, cl, qr, sk);
 }
 
@@ -186,6 +211,7 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
     sk.S0 = rs.S[0];
     sk.S1 = rs.S[1];
     sk.S2 = rs.S[2];
+    sk.off = 0u;
     sk.bx = make_box(rs.lo, rs.hi);
     sk.inv_wd = rs.inv_wd;
     sk.kahan = kahan;
@@ -228,6 +254,8 @@ __device__ __forceinline__ void march_count(const RaySetup &rs, const QuadRule &
                                             unsigned int &pieces, unsigned int &flat_pieces)
 {
     CountSink sk;
+    sk.S0 = sk.S1 = sk.S2 = 0;
+    sk.off = 0u;
     sk.bx = make_box(rs.lo, rs.hi);
     sk.n = 0u;
     sk.pieces = 0u;
@@ -286,6 +314,7 @@ __device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float 
     sk.S0 = rs.S[0];
     sk.S1 = rs.S[1];
     sk.S2 = rs.S[2];
+    sk.off = 0u;
     sk.bx = make_box(rs.lo, rs.hi);
     sk.yv = yr * rs.inv_wd;
     if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
@@ -484,10 +513,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
             if (cf > cl) continue;
             BrickSink sk;
             sk.part = part;
-            sk.L0 = L[0];
-            sk.L1 = L[1];
-            sk.L2 = L[2];
-            sk.Loff = Loff;
+            sk.S0 = L[0];
+            sk.S1 = L[1];
+            sk.S2 = L[2];
+            sk.off = (unsigned)Loff;
             sk.bx = make_box(blo, bhi);
             sk.yv = yr * rs.inv_wd;
             ok &= march<N>(rs, cf, cl, qr, sk);

@@ -725,15 +725,173 @@ __device__ __forceinline__ bool cell_march(const RaySetup &rs, int cf, int cl, c
     return true;
 }
 
-// Cell march over cells [cf, cl] with the form the ray needs: FLAT when the
-// ray has a zero transverse component (r_b = 0).  Every exact-footprint
-// kernel goes through here, so a ray gets the same footprint values in the
-// forward, the adjoint, the pair count and the footprint evaluator.
+// Piece march: the cell march of a general ray (r_b > 0) with one piece per
+// loop iteration instead of one cell.  The cells, pieces, nodes, window and
+// flushes are those of cell_march<N, Sink, false>; what differs is control
+// flow.  The lanes of a warp hold rays whose cells split into different
+// numbers of pieces (1 + a-crossings + b-crossings), so a loop over cells
+// runs every cell as often as its most-split lane needs; here every lane
+// integrates one piece per iteration whatever cell it is in, and the event
+// that ends the piece (an a- or b-crossing, or the end of the cell) is
+// handled without branches: the leaving face is picked with selects,
+// flushed through sink.put(offset, in_region, F) at offsets in the sink's
+// layout (sink.S0..S2, sink.off, region sink.bx), and the window shifted
+// with selects along the event's axis.  Only the set-up of the next cell
+// is a branch.
+template <int N, class Sink>
+__device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sink)
+{
+    constexpr int M = GL<N>::M;
+    if (cf > cl) return true;
+    float acc[N + 1][N + 1][N + 1];
+#pragma unroll
+    for (int d = 0; d <= N; ++d)
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
+#pragma unroll
+            for (int k = 0; k <= N; ++k) acc[d][i][k] = 0.0f;
+    int c = cf;
+    int IA, IB, IAn, IBn;
+    float fa, fb, fan, fbn;
+    df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, c - rs.c0, IA, fa);
+    df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, c - rs.c0, IB, fb);
+    df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, c + 1 - rs.c0, IAn, fan);
+    df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, c + 1 - rs.c0, IBn, fbn);
+    int QA = IA, QB = IB;
+    int na = IAn - QA, nb = IBn - QB;
+    if (na > 2 || nb > 2) return false;
+    float ga = fa, gb = fb;
+    float ta = na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+    float tb = nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+    float t0 = 0.0f;
+    int ev_in_cell = 0;
+    bool ok = true;
+#pragma unroll 1
+    while (true) {
+        const float t1 = fminf(fminf(ta, tb), 1.0f);
+        if (t1 > t0 && sink.relevant(c - N, c, QA - N, QA, QB - N, QB)) {
+            const float half = 0.5f * (t1 - t0), mid = 0.5f * (t0 + t1);
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                const float t = fmaf(half, qr.x[q], mid);
+                float wd[N + 1], wa[N + 1], wb[N + 1];
+                bweights<N>(t, wd);
+                bweights<N>(fmaf(rs.ra, t, ga), wa);
+                bweights<N>(fmaf(rs.rb, t, gb), wb);
+                const float cw = half * qr.w[q];
+#pragma unroll
+                for (int d = 0; d <= N; ++d) wd[d] *= cw;
+#pragma unroll
+                for (int i = 0; i <= N; ++i)
+#pragma unroll
+                    for (int k = 0; k <= N; ++k) {
+                        const float pk = wa[i] * wb[k];
+#pragma unroll
+                        for (int d = 0; d <= N; ++d) acc[d][i][k] = fmaf(wd[d], pk, acc[d][i][k]);
+                    }
+            }
+            sink.piece();
+        }
+        t0 = fmaxf(t0, t1);
+        const bool evA = ta <= tb && ta <= 1.0f;
+        const bool evB = !evA && tb <= 1.0f;
+        const bool evD = !evA && !evB;
+        // the face that leaves: A: (d = x, i = 0, k = y); B: (d = x, i = y,
+        // k = 0); D: (d = 0, i = x, k = y)
+        {
+            const int bd = c - N, ba = QA - N, bb = QB - N;
+            const unsigned base = sink.off + (unsigned)bd * (unsigned)sink.S0 + (unsigned)ba * (unsigned)sink.S1 +
+                                  (unsigned)bb * (unsigned)sink.S2;
+            const unsigned SX = (unsigned)(evD ? sink.S1 : sink.S0), SY = (unsigned)(evB ? sink.S1 : sink.S2);
+            const bool vf = evA ? sink.bx.in1(ba) : (evB ? sink.bx.in2(bb) : sink.bx.in0(bd));
+            bool vx[N + 1], vy[N + 1];
+#pragma unroll
+            for (int x = 0; x <= N; ++x) {
+                vx[x] = vf && (evD ? sink.bx.in1(ba + x) : sink.bx.in0(bd + x));
+                vy[x] = evB ? sink.bx.in1(ba + x) : sink.bx.in2(bb + x);
+            }
+#pragma unroll
+            for (int x = 0; x <= N; ++x)
+#pragma unroll
+                for (int y = 0; y <= N; ++y) {
+                    const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
+                    sink.put(base + (unsigned)x * SX + (unsigned)y * SY, vx[x] && vy[y], v);
+                }
+        }
+        // shift along the event's axis (in place: reads only higher indices)
+#pragma unroll
+        for (int d = 0; d <= N; ++d)
+#pragma unroll
+            for (int i = 0; i <= N; ++i)
+#pragma unroll
+                for (int k = 0; k <= N; ++k) {
+                    const float nd = d < N ? acc[(d < N ? d + 1 : d)][i][k] : 0.0f;
+                    const float na_ = i < N ? acc[d][(i < N ? i + 1 : i)][k] : 0.0f;
+                    const float nb_ = k < N ? acc[d][i][(k < N ? k + 1 : k)] : 0.0f;
+                    acc[d][i][k] = evD ? nd : (evA ? na_ : nb_);
+                }
+        if (evA) {
+            ++QA;
+            ga -= 1.0f;
+            ta = --na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+        } else if (evB) {
+            ++QB;
+            gb -= 1.0f;
+            tb = --nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+        } else {
+            sink.cell_end();
+            if (++c > cl) break;
+            IA = IAn;
+            fa = fan;
+            IB = IBn;
+            fb = fbn;
+            df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, c + 1 - rs.c0, IAn, fan);
+            df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, c + 1 - rs.c0, IBn, fbn);
+            na = IAn - QA;
+            nb = IBn - QB;
+            if (na > 2 || nb > 2) {
+                ok = false;
+                break;
+            }
+            ga = (float)(IA - QA) + fa;
+            gb = (float)(IB - QB) + fb;
+            ta = na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+            tb = nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+            t0 = 0.0f;
+            ev_in_cell = -1;
+        }
+        if (++ev_in_cell >= qr.cap) {
+            ok = false;
+            break;
+        }
+    }
+    if (!ok) return false;
+    // what the window still holds (layers l_d = cl+1-N .. cl) is flushed once
+#pragma unroll
+    for (int d = 0; d < N; ++d)
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
+#pragma unroll
+            for (int k = 0; k <= N; ++k) {
+                const int ld = cl + 1 - N + d, la = QA - N + i, lb = QB - N + k;
+                const unsigned off = sink.off + (unsigned)ld * (unsigned)sink.S0 + (unsigned)la * (unsigned)sink.S1 +
+                                     (unsigned)lb * (unsigned)sink.S2;
+                sink.put(off, sink.bx.in0(ld) && sink.bx.in1(la) && sink.bx.in2(lb), acc[d][i][k]);
+            }
+    sink.cell_end();
+    return true;
+}
+
+// March over cells [cf, cl] with the form the ray needs: the flat cell march
+// when the ray has a zero transverse component (r_b = 0), the piece march
+// otherwise.  Every exact-footprint kernel goes through here, so a ray gets
+// the same footprint values in the forward, the adjoint, the pair count and
+// the footprint evaluator.
 template <int N, class Sink>
 __device__ __forceinline__ bool march(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sink)
 {
     if (rs.rb == 0.0f) return cell_march<N, Sink, true>(rs, cf, cl, qr, sink);
-    return cell_march<N, Sink, false>(rs, cf, cl, qr, sink);
+    return piece_march<N, Sink>(rs, cf, cl, qr, sink);
 }
 
 // ------------------------------------------------------------------ rays of a geometry
