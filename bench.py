@@ -57,9 +57,11 @@ FLOP_PER_PAIR = 2
 NODES_PER_PIECE = {0: 1, 1: 2, 2: 4, 3: 5}
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) per launch from the ncu capture of each kernel
-# on this workload (profiles/k_*-tilt128-cubic.md); to be reset to None
+# on this workload (profiles/k_*-general-tilt128-cubic.md: the general-view
+# launches); to be reset to None
 # whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"k_forward_views": None, "k_adjoint_views_scatter": None, "k_adjoint_bricks": None}
+NCU_TRAFFIC = {"k_forward_views": 8.938240e6 + 2.304e3, "k_adjoint_views_scatter": 17.908992e6 + 1.024e3,
+               "k_adjoint_bricks": None}
 
 
 def parse():
