@@ -85,17 +85,14 @@ struct FwdSink {
     {
         if (bx.holds(ld, la, lb)) acc = fmaf(__ldg(c + (ld * S0 + la * S1 + lb * S2)), v, acc);
     }
-    // four partial sums (slot j % 4; j is a constant after unrolling) so
-    // that the 16 products of a face do not form one dependency chain
-    float part[4];
-    __device__ __forceinline__ void put(int j, unsigned o, bool in, float v)
+    __device__ __forceinline__ void put(unsigned o, bool in, float v)
     {
-        if (in) part[j & 3] = fmaf(__ldg(c + o), v, part[j & 3]);
+        if (in) acc = fmaf(__ldg(c + o), v, acc);
     }
     __device__ __forceinline__ void cell_end()
     {
-        const float v = (acc + ((part[0] + part[1]) + (part[2] + part[3]))) * inv_wd;
-        acc = part[0] = part[1] = part[2] = part[3] = 0.0f;
+        const float v = acc * inv_wd;
+        acc = 0.0f;
         if (kahan) kahan_add(sum, comp, v);
         else sum += v;
     }
@@ -117,7 +114,7 @@ struct CountSink {
     {
         n += (bx.holds(ld, la, lb) && v > 0.0f) ? 1u : 0u;
     }
-    __device__ __forceinline__ void put(int, unsigned, bool in, float v) { n += (in && v > 0.0f) ? 1u : 0u; }
+    __device__ __forceinline__ void put(unsigned, bool in, float v) { n += (in && v > 0.0f) ? 1u : 0u; }
     __device__ __forceinline__ void cell_end() {}
 };
 
@@ -138,7 +135,7 @@ struct AtomicSink {
     {
         if (bx.holds(ld, la, lb)) atomicAdd(c + (ld * S0 + la * S1 + lb * S2), yv * v);
     }
-    __device__ __forceinline__ void put(int, unsigned o, bool in, float v)
+    __device__ __forceinline__ void put(unsigned o, bool in, float v)
     {
         if (in) atomicAdd(c + o, yv * v);
     }
@@ -163,7 +160,7 @@ struct BrickSink {
     {
         if (bx.holds(ld, la, lb)) atomicAdd(part + (unsigned)(ld * S0 + la * S1 + lb * S2 + (int)off), yv * v);
     }
-    __device__ __forceinline__ void put(int, unsigned o, bool in, float v)
+    __device__ __forceinline__ void put(unsigned o, bool in, float v)
     {
         if (in) atomicAdd(part + o, yv * v);
     }
@@ -219,7 +216,6 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
     sk.inv_wd = rs.inv_wd;
     sk.kahan = kahan;
     sk.acc = sk.sum = sk.comp = 0.0f;
-    sk.part[0] = sk.part[1] = sk.part[2] = sk.part[3] = 0.0f;
     if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
     return sk.sum;
 }

@@ -734,8 +734,7 @@ __device__ __forceinline__ bool cell_march(const RaySetup &rs, int cf, int cl, c
 // integrates one piece per iteration whatever cell it is in, and the event
 // that ends the piece (an a- or b-crossing, or the end of the cell) is
 // handled without branches: the leaving face is picked with selects,
-// flushed through sink.put(j, offset, in_region, F) (j: position in the
-// face, a constant after unrolling) at offsets in the sink's
+// flushed through sink.put(offset, in_region, F) at offsets in the sink's
 // layout (sink.S0..S2, sink.off, region sink.bx), and the window shifted
 // with selects along the event's axis.  Only the set-up of the next cell
 // is a branch.
@@ -816,7 +815,7 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
 #pragma unroll
                 for (int y = 0; y <= N; ++y) {
                     const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
-                    sink.put(x * (N + 1) + y, base + (unsigned)x * SX + (unsigned)y * SY, vx[x] && vy[y], v);
+                    sink.put(base + (unsigned)x * SX + (unsigned)y * SY, vx[x] && vy[y], v);
                 }
         }
         // shift along the event's axis (in place: reads only higher indices)
@@ -877,7 +876,7 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
                 const int ld = cl + 1 - N + d, la = QA - N + i, lb = QB - N + k;
                 const unsigned off = sink.off + (unsigned)ld * (unsigned)sink.S0 + (unsigned)la * (unsigned)sink.S1 +
                                      (unsigned)lb * (unsigned)sink.S2;
-                sink.put(i * (N + 1) + k, off, sink.bx.in0(ld) && sink.bx.in1(la) && sink.bx.in2(lb), acc[d][i][k]);
+                sink.put(off, sink.bx.in0(ld) && sink.bx.in1(la) && sink.bx.in2(lb), acc[d][i][k]);
             }
     sink.cell_end();
     return true;
