@@ -313,6 +313,16 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
                 pg->dz = key.dz;
                 g->plane = pg;
             }
+            g->vconst = (ViewConst *)malloc((d.n_views > 0 ? d.n_views : 1) * sizeof(ViewConst));
+            if (!g->vconst) {
+                free(view_order);
+                plane_free(g->plane);
+                free(g->views_host);
+                free(g);
+                return fail(SPL_ERR_OOM, "host allocation failed");
+            }
+            for (int i = 0; i < d.n_views; ++i)
+                view_const(g->views_host[view_order[i]].dir, view_order[i], dg.n, g->vconst[i]);
             order_off = (payload + 255) & ~(size_t)255;
             payload = order_off + (size_t)d.n_views * sizeof(int);
         }
@@ -329,6 +339,7 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
         free(ray_host);
         free(view_order);
         plane_free(g->plane);
+        free(g->vconst);
         free(g->views_host);
         free(g);
         cudaGetLastError();
@@ -346,6 +357,7 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
     if (ce != cudaSuccess) {
         cudaFree(blk);
         plane_free(g->plane);
+        free(g->vconst);
         free(g->views_host);
         free(g);
         return cuda_check(ce, "geometry upload");
@@ -366,6 +378,7 @@ extern "C" void spl_destroy_geometry(spl_geometry *g)
 {
     if (!g) return;
     plane_free(g->plane);
+    free(g->vconst);
     if (g->dev_block) cudaFree(g->dev_block);
     free(g->views_host);
     free(g);

@@ -23,6 +23,7 @@
 //    coefficient written once.
 // Adjoint, explicit rays: no view structure to gather over: scatter.
 #include <stdio.h>
+#include <string.h>
 
 #include "spl_host.h"
 #include "spl_mlp.cuh"
@@ -190,12 +191,26 @@ __device__ __forceinline__ bool march_vm(const RaySetup &rs, int cf, int cl, con
     else return march<N>(rs, cf, cl, qr, sk);
 }
 
-// view of this block: blockIdx.z (VM_MIXED) or view_order[v_off + blockIdx.z]
-template <int VM>
-__device__ __forceinline__ int view_of(const DevGeom &g, int v_off)
+// Rays of a parallel view: the view's constants replace the set-up's
+// per-thread copies of the same values, so the march reads them from the
+// kernel parameter (uniform across the block).
+__device__ __forceinline__ void use_view_const(const ViewConst &V, RaySetup &rs)
 {
-    if constexpr (VM == VM_MIXED) return blockIdx.z;
-    else return g.view_order[v_off + blockIdx.z];
+    rs.ra = V.ra;
+    rs.rb = V.rb;
+    rs.inv_ra = V.inv_ra;
+    rs.inv_rb = V.inv_rb;
+    rs.inv_wd = V.inv_wd;
+    rs.rah = V.rah;
+    rs.ral = V.ral;
+    rs.rbh = V.rbh;
+    rs.rbl = V.rbl;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        rs.S[q] = V.S[q];
+        rs.lo[q] = V.lo[q];
+        rs.hi[q] = V.hi[q];
+    }
 }
 
 // blocks per SM the register budget is sized for: the flat form needs an
@@ -220,17 +235,39 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
     return sk.sum;
 }
 
-template <int N, int VM>
-__global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
-    k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y, QuadRule qr, int kahan, int v_off)
+// cone views (the march form is chosen per ray)
+template <int N>
+__global__ void __launch_bounds__(128, 3)
+    k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y, QuadRule qr, int kahan)
 {
     int iu, iv;
     tile_pixel(iu, iv);
-    const int k = view_of<VM>(g, v_off);
+    const int k = blockIdx.z;
     if (iu >= g.nu || iv >= g.nv) return;
     RaySetup rs;
     float v = 0.0f;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) v = march_forward<N, VM>(rs, c, qr, kahan != 0, g.err);
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) v = march_forward<N, VM_MIXED>(rs, c, qr, kahan != 0, g.err);
+    y[((long long)k * g.nv + iv) * g.nu + iu] = v;
+}
+
+// parallel views of one class (VM_FLAT or VM_GENERAL): view blockIdx.z of
+// the chunk
+template <int N, int VM>
+__global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
+    k_forward_pviews(DevGeom g, const float *__restrict__ c, float *__restrict__ y, QuadRule qr, int kahan,
+                     const __grid_constant__ ViewChunk vc)
+{
+    int iu, iv;
+    tile_pixel(iu, iv);
+    const ViewConst &V = vc.v[blockIdx.z];
+    const int k = V.view;
+    if (iu >= g.nu || iv >= g.nv) return;
+    RaySetup rs;
+    float v = 0.0f;
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) {
+        use_view_const(V, rs);
+        v = march_forward<N, VM>(rs, c, qr, kahan != 0, g.err);
+    }
     y[((long long)k * g.nv + iv) * g.nu + iu] = v;
 }
 
@@ -335,18 +372,37 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
 }
 
 // view geometries, scatter form: the forward's thread mapping, float atomics
-template <int N, int VM>
-__global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
-    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr, int v_off)
+template <int N>
+__global__ void __launch_bounds__(128, 3)
+    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr)
 {
     int iu, iv;
     tile_pixel(iu, iv);
-    const int k = view_of<VM>(g, v_off);
+    const int k = blockIdx.z;
     if (iu >= g.nu || iv >= g.nv) return;
     const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
     if (yr == 0.0f) return;
     RaySetup rs;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM>(rs, yr, c, qr, g.err);
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM_MIXED>(rs, yr, c, qr, g.err);
+}
+
+template <int N, int VM>
+__global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
+    k_adjoint_pviews_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr,
+                             const __grid_constant__ ViewChunk vc)
+{
+    int iu, iv;
+    tile_pixel(iu, iv);
+    const ViewConst &V = vc.v[blockIdx.z];
+    const int k = V.view;
+    if (iu >= g.nu || iv >= g.nv) return;
+    const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
+    if (yr == 0.0f) return;
+    RaySetup rs;
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) {
+        use_view_const(V, rs);
+        scatter_ray<N, VM>(rs, yr, c, qr, g.err);
+    }
 }
 
 // ---------------------------------------------------------------- adjoint: brick gather (view geometries)
@@ -549,6 +605,19 @@ static spl_status launch_status(const char *what)
     return cuda_check(cudaGetLastError(), what);
 }
 
+// Launch `launch(chunk, n)` for the parallel views view_order[v0 .. v0+count)
+// in chunks of at most kViewChunk, each with its views' constants.
+template <class F>
+static void for_view_chunks(const spl_geometry *g, int v0, int count, F launch)
+{
+    static thread_local ViewChunk ch;
+    for (int s = 0; s < count; s += kViewChunk) {
+        const int n = count - s < kViewChunk ? count - s : kViewChunk;
+        memcpy(ch.v, g->vconst + v0 + s, (size_t)n * sizeof(ViewConst));
+        launch(ch, n);
+    }
+}
+
 // Parallel geometries: the separable group through the plane matrices
 // (when used), the other flat views with the flat kernel, the rest with the
 // general one.  Returns the first view_order index the flat kernel takes.
@@ -581,13 +650,16 @@ static spl_status forward_quad(const spl_geometry *g, const spl_basis_desc *b, c
             s = plane_forward(g, N, kahan, c, y, st);
             if (s != SPL_OK) return s;
         }
-        const int nf = dg.n_flat - v0, ng = dg.n_views - dg.n_flat;
         const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
-        if (nf > 0) k_forward_views<N, VM_FLAT><<<dim3(gx, gy, nf), 128, 0, st>>>(dg, c, y, qr, kahan, v0);
-        if (ng > 0) k_forward_views<N, VM_GENERAL><<<dim3(gx, gy, ng), 128, 0, st>>>(dg, c, y, qr, kahan, dg.n_flat);
+        for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
+            k_forward_pviews<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, c, y, qr, kahan, ch);
+        });
+        for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
+            k_forward_pviews<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, c, y, qr, kahan, ch);
+        });
     } else {
         dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
-        k_forward_views<N, VM_MIXED><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan, 0);
+        k_forward_views<N><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan);
     }
     return launch_status("forward launch");
 }
@@ -622,11 +694,14 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
     if (form != SPL_ADJ_GATHER) {
         const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
         if (dg.kind == SPL_PARALLEL) {
-            const int nf = dg.n_flat - v0, ng = dg.n_views - dg.n_flat;
-            if (nf > 0) k_adjoint_views_scatter<N, VM_FLAT><<<dim3(gx, gy, nf), 128, 0, st>>>(dg, y, c, qr, v0);
-            if (ng > 0) k_adjoint_views_scatter<N, VM_GENERAL><<<dim3(gx, gy, ng), 128, 0, st>>>(dg, y, c, qr, dg.n_flat);
+            for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
+                k_adjoint_pviews_scatter<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
+            });
+            for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
+                k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
+            });
         } else {
-            k_adjoint_views_scatter<N, VM_MIXED><<<dim3(gx, gy, dg.n_views), 128, 0, st>>>(dg, y, c, qr, 0);
+            k_adjoint_views_scatter<N><<<dim3(gx, gy, dg.n_views), 128, 0, st>>>(dg, y, c, qr);
         }
         return launch_status("adjoint launch");
     }

@@ -18,6 +18,7 @@ struct spl_geometry {
     void *dev_block;              // single device allocation: poses/rays + error flag
     int device;
     spl::PlaneGroup *plane;       // slice-separable view group (parallel geometries), or NULL
+    spl::ViewConst *vconst;       // parallel geometries: per-view constants in view_order order (host)
 };
 
 namespace spl {

@@ -109,6 +109,44 @@ __host__ __device__ inline void dir_setup(const double (&w)[3], DirSetup &ds)
     ds.inv_wd = (float)iwd;
 }
 
+// Constants of a parallel view that every ray of the view shares: the
+// float part of its direction set-up, the mirrored strides and the grid
+// bounds in its (d, a, b) frame.  The parallel-view kernels take them as a
+// __grid_constant__ parameter indexed by blockIdx.z, so that they stay in
+// the constant bank (uniform registers) instead of occupying per-thread
+// registers next to the march window.
+struct ViewConst {
+    float ra, rb, inv_ra, inv_rb, inv_wd, rah, ral, rbh, rbl;
+    int view;       // view index
+    int S[3];       // signed linear strides of (d, a, b)
+    int lo[3], hi[3];
+};
+constexpr int kViewChunk = 256;  // views per launch (19.5 KB of parameters)
+struct ViewChunk {
+    ViewConst v[kViewChunk];
+};
+
+__host__ __device__ inline void view_const(const DirSetup &ds, int view, const int (&n)[3], ViewConst &vc)
+{
+    const int stride[3] = {1, n[0], n[0] * n[1]};
+    vc.ra = ds.ra;
+    vc.rb = ds.rb;
+    vc.inv_ra = ds.inv_ra;
+    vc.inv_rb = ds.inv_rb;
+    vc.inv_wd = ds.inv_wd;
+    vc.rah = ds.rah;
+    vc.ral = ds.ral;
+    vc.rbh = ds.rbh;
+    vc.rbl = ds.rbl;
+    vc.view = view;
+    for (int q = 0; q < 3; ++q) {
+        const int e = ds.ax[q];
+        vc.S[q] = ds.sg[q] * stride[e];
+        vc.lo[q] = ds.sg[q] > 0 ? 0 : -(n[e] - 1);
+        vc.hi[q] = ds.sg[q] > 0 ? n[e] - 1 : 0;
+    }
+}
+
 // Per-view pose in FP64 (one entry per view of a view geometry).
 struct ViewPose {
     double src[3];       // parallel: unit ray direction; cone: source position
