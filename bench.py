@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--adjoint", default="scatter", choices=["gather", "scatter"],
                     help="form of A^T: ray-driven scatter (float atomics, the library default) or brick gather")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mlp-steps", type=int, default=40000,
+    ap.add_argument("--mlp-steps", type=int, default=200000,
                     help="Adam steps of the learned footprint trained before the MLP measurement (0: skip it)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU-baseline sample")
     return ap.parse_args()
