@@ -429,6 +429,15 @@ def run_ours(args):
         per_class[name] = {"views": cl["views"], "contributions_per_A": cl["pairs"], "A_ms": a_ms, "AT_ms": at_ms,
                            "A_gcontrib_s": cl["pairs"] / (a_ms * 1e-3) / 1e9,
                            "AT_gcontrib_s": cl["pairs"] / (at_ms * 1e-3) / 1e9}
+        if name == "general":
+            # the same A as the line integral of f itself (SPL_FP_DIRECT, the
+            # exact alternative of the footprint form; not the headline)
+            bd = spl.basis(n, spl.SPL_FP_DIRECT)
+            spl.forward(gsub, c_true, ysub, bd)
+            ad_ms = time_call(lambda: spl.forward(gsub, c_true, ysub, bd))
+            gsub.status()
+            per_class[name]["A_direct_ms"] = ad_ms
+            per_class[name]["A_direct_gcontrib_s"] = cl["pairs"] / (ad_ms * 1e-3) / 1e9
 
     contrib_step = 2 * pairs  # A and A^T visit the same pairs
     value = ws * contrib_step / (ms * 1e-3) / 1e9

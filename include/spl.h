@@ -55,8 +55,12 @@ typedef enum {
 
 /* geometry kinds (Eq. 1 lines) */
 enum { SPL_RAYS = 0, SPL_PARALLEL = 1, SPL_CONE = 2 };
-/* footprint evaluators: exact quadrature, or the learned f_theta (Sec. 2.2) */
-enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1 };
+/* footprint evaluators: exact quadrature, or the learned f_theta (Sec. 2.2);
+ * SPL_FP_DIRECT: exact too, but spl_forward integrates f itself along the
+ * ray (the Gauss nodes of the same pieces, a window of coefficients instead
+ * of footprint accumulators) on rays with three nonzero direction
+ * components; everything else is as SPL_FP_QUAD (same matrix). */
+enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1, SPL_FP_DIRECT = 2 };
 /* adjoint forms for view geometries: SPL_ADJ_AUTO picks the faster one on
  * this GPU (the scatter form); SPL_ADJ_GATHER walks coefficient bricks and
  * accumulates in shared memory (no global atomics); SPL_ADJ_SCATTER walks
@@ -102,8 +106,10 @@ typedef struct {
 
 /* Basis and footprint choice.
  *   degree: n in 0..3 (B-spline degree of the tensor-product basis).
- *   mode:   SPL_FP_QUAD (exact piecewise Gauss-Legendre footprint) or
- *           SPL_FP_MLP (learned footprint f_theta, Algorithm 2's f_theta*);
+ *   mode:   SPL_FP_QUAD (exact piecewise Gauss-Legendre footprint),
+ *           SPL_FP_DIRECT (the same operator; forward as the direct line
+ *           integral of f) or SPL_FP_MLP (learned footprint f_theta,
+ *           Algorithm 2's f_theta*);
  *           SPL_FP_MLP needs `mlp` built for the same degree.
  *   kahan:  nonzero = compensated (Kahan) FP32 sum of the slab partials along
  *           each ray; zero = plain FP32 sum.

@@ -103,7 +103,8 @@ spl_status check_basis(const spl_basis_desc *b)
 {
     if (!b) return fail(SPL_ERR_ARG, "basis descriptor is NULL");
     if (b->degree < 0 || b->degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", b->degree);
-    if (b->mode != SPL_FP_QUAD && b->mode != SPL_FP_MLP) return fail(SPL_ERR_ARG, "unknown footprint mode %d", b->mode);
+    if (b->mode != SPL_FP_QUAD && b->mode != SPL_FP_MLP && b->mode != SPL_FP_DIRECT)
+        return fail(SPL_ERR_ARG, "unknown footprint mode %d", b->mode);
     if (b->mode == SPL_FP_MLP && !b->mlp) return fail(SPL_ERR_ARG, "SPL_FP_MLP needs an MLP");
     if (b->separable != SPL_SEP_AUTO && b->separable != SPL_SEP_OFF)
         return fail(SPL_ERR_ARG, "unknown separable mode %d", b->separable);

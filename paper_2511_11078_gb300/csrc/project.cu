@@ -31,39 +31,6 @@
 namespace spl {
 
 // ---------------------------------------------------------------- sinks
-// Region of bases a sink accepts, in the ray's mirrored (d, a, b)
-// coordinates: lo[q] .. lo[q] + ext[q].
-struct SinkBox {
-    int lo0, lo1, lo2;
-    unsigned ext0, ext1, ext2;
-    __device__ __forceinline__ bool holds(int d, int a, int b) const
-    {
-        return (unsigned)(d - lo0) <= ext0 && (unsigned)(a - lo1) <= ext1 && (unsigned)(b - lo2) <= ext2;
-    }
-    __device__ __forceinline__ bool in0(int d) const { return (unsigned)(d - lo0) <= ext0; }
-    __device__ __forceinline__ bool in1(int a) const { return (unsigned)(a - lo1) <= ext1; }
-    __device__ __forceinline__ bool in2(int b) const { return (unsigned)(b - lo2) <= ext2; }
-    // whether the window [d0, d1] x [a0, a1] x [b0, b1] meets the region
-    __device__ __forceinline__ bool meets(int d0, int d1, int a0, int a1, int b0, int b1) const
-    {
-        return d1 >= lo0 && d0 <= lo0 + (int)ext0 && a1 >= lo1 && a0 <= lo1 + (int)ext1 && b1 >= lo2 &&
-               b0 <= lo2 + (int)ext2;
-    }
-};
-
-__device__ __forceinline__ SinkBox make_box(const int (&lo)[3], const int (&hi)[3])
-{
-    SinkBox b;
-    b.lo0 = lo[0];
-    b.lo1 = lo[1];
-    b.lo2 = lo[2];
-    b.ext0 = (unsigned)(hi[0] - lo[0]);
-    b.ext1 = (unsigned)(hi[1] - lo[1]);
-    b.ext2 = (unsigned)(hi[2] - lo[2]);
-    return b;
-}
-
-// forward: sum of c_l * F_l along the ray, Kahan-compensated per cell
 // Sinks take a basis either by index (flush, the flat cell march) or by its
 // offset in the sink's layout, off + l_d S0 + l_a S1 + l_b S2 in unsigned
 // (wrapping) arithmetic, with a flag that it lies in the region (put, the
@@ -213,14 +180,28 @@ __device__ __forceinline__ void use_view_const(const ViewConst &V, RaySetup &rs)
     }
 }
 
-// blocks per SM the register budget is sized for: the flat form needs an
-// (n+1)^2 window, the general one (n+1)^3
-template <int VM> struct ViewBlocks { static constexpr int value = VM == VM_FLAT ? 6 : 3; };
+// blocks per SM the register budget is sized for (measured): the flat form
+// needs an (n+1)^2 window, the general one (n+1)^3 accumulators plus the
+// flush state (3 blocks x 168 registers; 4 x 128 spills and is slower); the
+// direct march keeps (n+1)^3 coefficients but no flush state (4 x 128)
+template <int VM, bool DIRECT = false> struct ViewBlocks {
+    static constexpr int value = VM == VM_FLAT ? 6 : (DIRECT ? 4 : 3);
+};
 
-template <int N, int VM>
+// DIRECT: rays with three nonzero direction components take the direct
+// march (the line integral of f itself); flat rays keep the footprint form
+template <int N, int VM, bool DIRECT = false>
 __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *__restrict__ c, const QuadRule &qr,
                                                bool kahan, int *err)
 {
+    if constexpr (DIRECT && VM != VM_FLAT) {
+        if (VM == VM_GENERAL || rs.rb != 0.0f) {
+            float out;
+            if (!direct_march<N>(rs, c, rs.S[0], rs.S[1], rs.S[2], make_box(rs.lo, rs.hi), qr, kahan, out))
+                atomicOr(err, 1);
+            return out;
+        }
+    }
     FwdSink sk;
     sk.c = c;
     sk.S0 = rs.S[0];
@@ -236,8 +217,8 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
 }
 
 // cone views (the march form is chosen per ray)
-template <int N>
-__global__ void __launch_bounds__(128, 3)
+template <int N, bool DIRECT>
+__global__ void __launch_bounds__(128, (ViewBlocks<VM_MIXED, DIRECT>::value))
     k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y, QuadRule qr, int kahan)
 {
     int iu, iv;
@@ -246,14 +227,15 @@ __global__ void __launch_bounds__(128, 3)
     if (iu >= g.nu || iv >= g.nv) return;
     RaySetup rs;
     float v = 0.0f;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) v = march_forward<N, VM_MIXED>(rs, c, qr, kahan != 0, g.err);
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs))
+        v = march_forward<N, VM_MIXED, DIRECT>(rs, c, qr, kahan != 0, g.err);
     y[((long long)k * g.nv + iv) * g.nu + iu] = v;
 }
 
 // parallel views of one class (VM_FLAT or VM_GENERAL): view blockIdx.z of
 // the chunk
-template <int N, int VM>
-__global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
+template <int N, int VM, bool DIRECT>
+__global__ void __launch_bounds__(128, (ViewBlocks<VM, DIRECT>::value))
     k_forward_pviews(DevGeom g, const float *__restrict__ c, float *__restrict__ y, QuadRule qr, int kahan,
                      const __grid_constant__ ViewChunk vc)
 {
@@ -266,12 +248,12 @@ __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
     float v = 0.0f;
     if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) {
         use_view_const(V, rs);
-        v = march_forward<N, VM>(rs, c, qr, kahan != 0, g.err);
+        v = march_forward<N, VM, DIRECT>(rs, c, qr, kahan != 0, g.err);
     }
     y[((long long)k * g.nv + iv) * g.nu + iu] = v;
 }
 
-template <int N>
+template <int N, bool DIRECT>
 __global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__restrict__ c, float *__restrict__ y,
                                                       QuadRule qr, int kahan)
 {
@@ -281,7 +263,7 @@ __global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__
     explicit_ray(g, r, s, w);
     RaySetup rs;
     float v = 0.0f;
-    if (ray_setup<N>(grid_of(g), s, w, rs)) v = march_forward<N, VM_RAYS>(rs, c, qr, kahan != 0, g.err);
+    if (ray_setup<N>(grid_of(g), s, w, rs)) v = march_forward<N, VM_RAYS, DIRECT>(rs, c, qr, kahan != 0, g.err);
     y[r] = v;
 }
 
@@ -624,7 +606,7 @@ static void for_view_chunks(const spl_geometry *g, int v0, int count, F launch)
 static int plane_views(const spl_geometry *g, const spl_basis_desc *b, cudaStream_t st, spl_status *err)
 {
     *err = SPL_OK;
-    if (b->separable == SPL_SEP_OFF || b->mode != SPL_FP_QUAD || !g->plane) return 0;
+    if (b->separable == SPL_SEP_OFF || b->mode == SPL_FP_MLP || !g->plane) return 0;
     spl_status e;
     const bool ok = plane_ready(const_cast<spl_geometry *>(g), b->degree, st, &e);
     if (!ok && e != SPL_OK && e != SPL_ERR_OOM) *err = e;  // out of memory: walk the views instead
@@ -632,8 +614,9 @@ static int plane_views(const spl_geometry *g, const spl_basis_desc *b, cudaStrea
     return ok ? g->dev.n_sep : 0;
 }
 
-template <int N>
-static spl_status forward_quad(const spl_geometry *g, const spl_basis_desc *b, const float *c, float *y, cudaStream_t st)
+template <int N, bool DIRECT>
+static spl_status forward_quad_t(const spl_geometry *g, const spl_basis_desc *b, const float *c, float *y,
+                                 cudaStream_t st)
 {
     const DevGeom &dg = g->dev;
     const QuadRule qr = quad_rule(N);
@@ -641,7 +624,7 @@ static spl_status forward_quad(const spl_geometry *g, const spl_basis_desc *b, c
     if (dg.n_rays == 0) return SPL_OK;
     if (dg.kind == SPL_RAYS) {
         const long long blocks = (dg.n_rays + 127) / 128;
-        k_forward_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, c, y, qr, kahan);
+        k_forward_rays<N, DIRECT><<<(unsigned)blocks, 128, 0, st>>>(dg, c, y, qr, kahan);
     } else if (dg.kind == SPL_PARALLEL) {
         spl_status s;
         const int v0 = plane_views(g, b, st, &s);
@@ -652,16 +635,22 @@ static spl_status forward_quad(const spl_geometry *g, const spl_basis_desc *b, c
         }
         const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
         for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
-            k_forward_pviews<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, c, y, qr, kahan, ch);
+            k_forward_pviews<N, VM_FLAT, false><<<dim3(gx, gy, n), 128, 0, st>>>(dg, c, y, qr, kahan, ch);
         });
         for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
-            k_forward_pviews<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, c, y, qr, kahan, ch);
+            k_forward_pviews<N, VM_GENERAL, DIRECT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, c, y, qr, kahan, ch);
         });
     } else {
         dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
-        k_forward_views<N><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan);
+        k_forward_views<N, DIRECT><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan);
     }
     return launch_status("forward launch");
+}
+
+template <int N>
+static spl_status forward_quad(const spl_geometry *g, const spl_basis_desc *b, const float *c, float *y, cudaStream_t st)
+{
+    return b->mode == SPL_FP_DIRECT ? forward_quad_t<N, true>(g, b, c, y, st) : forward_quad_t<N, false>(g, b, c, y, st);
 }
 
 template <int N>

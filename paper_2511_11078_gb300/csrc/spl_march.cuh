@@ -573,6 +573,48 @@ __device__ __forceinline__ bool sweep(const RaySetup &rs, int j, const QuadRule 
     return slab_sweep<N, Sink, true, false>(rs, j, qr, sink);
 }
 
+// Region of bases a sink accepts, in the ray's mirrored (d, a, b)
+// coordinates: lo[q] .. lo[q] + ext[q].
+struct SinkBox {
+    int lo0, lo1, lo2;
+    unsigned ext0, ext1, ext2;
+    __device__ __forceinline__ bool holds(int d, int a, int b) const
+    {
+        return (unsigned)(d - lo0) <= ext0 && (unsigned)(a - lo1) <= ext1 && (unsigned)(b - lo2) <= ext2;
+    }
+    __device__ __forceinline__ bool in0(int d) const { return (unsigned)(d - lo0) <= ext0; }
+    __device__ __forceinline__ bool in1(int a) const { return (unsigned)(a - lo1) <= ext1; }
+    __device__ __forceinline__ bool in2(int b) const { return (unsigned)(b - lo2) <= ext2; }
+    // whether the window [d0, d1] x [a0, a1] x [b0, b1] meets the region
+    __device__ __forceinline__ bool meets(int d0, int d1, int a0, int a1, int b0, int b1) const
+    {
+        return d1 >= lo0 && d0 <= lo0 + (int)ext0 && a1 >= lo1 && a0 <= lo1 + (int)ext1 && b1 >= lo2 &&
+               b0 <= lo2 + (int)ext2;
+    }
+};
+
+__device__ __forceinline__ SinkBox make_box(const int (&lo)[3], const int (&hi)[3])
+{
+    SinkBox b;
+    b.lo0 = lo[0];
+    b.lo1 = lo[1];
+    b.lo2 = lo[2];
+    b.ext0 = (unsigned)(hi[0] - lo[0]);
+    b.ext1 = (unsigned)(hi[1] - lo[1]);
+    b.ext2 = (unsigned)(hi[2] - lo[2]);
+    return b;
+}
+
+// forward: sum of c_l * F_l along the ray, Kahan-compensated per cell
+// compensated (Kahan) FP32 summation
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
+{
+    const float yv = __fsub_rn(v, comp);
+    const float t = __fadd_rn(sum, yv);
+    comp = __fsub_rn(__fsub_rn(t, sum), yv);
+    sum = t;
+}
+
 // ------------------------------------------------------------------ cell march
 // Cells along d*.  With v = u + W the bases of one axis sit at the integers
 // and basis l covers v in (l, l + N + 1), so the N+1 bases whose support
@@ -920,6 +962,153 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
     return true;
 }
 
+// Direct march (the forward only): the line integral of f itself along the
+// ray, f(x) = sum_l c_l phi_l(x), over the same cells, pieces and Gauss
+// nodes as the piece march.  The window holds the coefficients of the live
+// bases (zero outside the grid) instead of their footprint accumulators:
+// each node contracts them with its three weight sets,
+//   f = sum_d wd_d sum_i wa_i sum_k wb_k c[d][i][k],
+// and an event shifts the window and loads the entering face (16 gathers)
+// instead of flushing the leaving one.  The matrix is the same as the
+// footprint form's; only the FP32 rounding differs.
+// CX: coefficient array; S0..S2, bx: mirrored strides and grid bounds.
+template <int N>
+__device__ __forceinline__ bool direct_march(const RaySetup &rs, const float *__restrict__ CX, int S0, int S1, int S2,
+                                             const SinkBox &bx, const QuadRule &qr, bool kahan, float &out)
+{
+    constexpr int M = GL<N>::M;
+    out = 0.0f;
+    const int cf = rs.c0, cl = rs.c1;
+    if (cf > cl) return true;
+    int c = cf;
+    int IA, IB, IAn, IBn;
+    float fa, fb, fan, fbn;
+    df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, c - rs.c0, IA, fa);
+    df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, c - rs.c0, IB, fb);
+    df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, c + 1 - rs.c0, IAn, fan);
+    df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, c + 1 - rs.c0, IBn, fbn);
+    int QA = IA, QB = IB;
+    // the window of cell c: l = (c - N + d, QA - N + i, QB - N + k)
+    float cw[N + 1][N + 1][N + 1];
+#pragma unroll
+    for (int d = 0; d <= N; ++d)
+#pragma unroll
+        for (int i = 0; i <= N; ++i)
+#pragma unroll
+            for (int k = 0; k <= N; ++k) {
+                const int ld = c - N + d, la = QA - N + i, lb = QB - N + k;
+                const unsigned o = (unsigned)ld * (unsigned)S0 + (unsigned)la * (unsigned)S1 + (unsigned)lb * (unsigned)S2;
+                cw[d][i][k] = (bx.in0(ld) && bx.in1(la) && bx.in2(lb)) ? __ldg(CX + o) : 0.0f;
+            }
+    int na = IAn - QA, nb = IBn - QB;
+    if (na > 2 || nb > 2) return false;
+    float ga = fa, gb = fb;
+    float ta = na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+    float tb = nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+    float t0 = 0.0f, cell = 0.0f, sum = 0.0f, comp = 0.0f;
+    int ev_in_cell = 0;
+#pragma unroll 1
+    while (true) {
+        const float t1 = fminf(fminf(ta, tb), 1.0f);
+        if (t1 > t0 && bx.meets(c - N, c, QA - N, QA, QB - N, QB)) {
+            const float half = 0.5f * (t1 - t0), mid = 0.5f * (t0 + t1);
+            float piece = 0.0f;
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                const float t = fmaf(half, qr.x[q], mid);
+                float wd[N + 1], wa[N + 1], wb[N + 1];
+                bweights<N>(t, wd);
+                bweights<N>(fmaf(rs.ra, t, ga), wa);
+                bweights<N>(fmaf(rs.rb, t, gb), wb);
+                float f = 0.0f;
+#pragma unroll
+                for (int d = 0; d <= N; ++d) {
+                    float u = 0.0f;
+#pragma unroll
+                    for (int i = 0; i <= N; ++i) {
+                        float tk = 0.0f;
+#pragma unroll
+                        for (int k = 0; k <= N; ++k) tk = fmaf(wb[k], cw[d][i][k], tk);
+                        u = fmaf(wa[i], tk, u);
+                    }
+                    f = fmaf(wd[d], u, f);
+                }
+                piece = fmaf(qr.w[q], f, piece);
+            }
+            cell = fmaf(half, piece, cell);
+        }
+        t0 = fmaxf(t0, t1);
+        const bool evA = ta <= tb && ta <= 1.0f;
+        const bool evB = !evA && tb <= 1.0f;
+        const bool evD = !evA && !evB;
+        // the entering face after the shift: A: (d = x, i = N, k = y);
+        // B: (d = x, i = y, k = N); D: (d = N, i = x, k = y)
+        float L[N + 1][N + 1];
+        {
+            const int bd = evD ? c + 1 : c - N, ba = evA ? QA + 1 : QA - N, bb = evB ? QB + 1 : QB - N;
+            const unsigned base = (unsigned)bd * (unsigned)S0 + (unsigned)ba * (unsigned)S1 + (unsigned)bb * (unsigned)S2;
+            const unsigned SX = (unsigned)(evD ? S1 : S0), SY = (unsigned)(evB ? S1 : S2);
+            const bool vf = evA ? bx.in1(ba) : (evB ? bx.in2(bb) : bx.in0(bd));
+            bool vx[N + 1], vy[N + 1];
+#pragma unroll
+            for (int x = 0; x <= N; ++x) {
+                vx[x] = vf && (evD ? bx.in1(ba + x) : bx.in0(bd + x));
+                vy[x] = evB ? bx.in1(ba + x) : bx.in2(bb + x);
+            }
+            const bool load = !(evD && c + 1 > cl);  // no cell after the last one
+#pragma unroll
+            for (int x = 0; x <= N; ++x)
+#pragma unroll
+                for (int y = 0; y <= N; ++y)
+                    L[x][y] = (load && vx[x] && vy[y]) ? __ldg(CX + (base + (unsigned)x * SX + (unsigned)y * SY)) : 0.0f;
+        }
+#pragma unroll
+        for (int d = 0; d <= N; ++d)
+#pragma unroll
+            for (int i = 0; i <= N; ++i)
+#pragma unroll
+                for (int k = 0; k <= N; ++k) {
+                    const float nd = d < N ? cw[(d < N ? d + 1 : d)][i][k] : L[i][k];
+                    const float na_ = i < N ? cw[d][(i < N ? i + 1 : i)][k] : L[d][k];
+                    const float nb_ = k < N ? cw[d][i][(k < N ? k + 1 : k)] : L[d][i];
+                    cw[d][i][k] = evD ? nd : (evA ? na_ : nb_);
+                }
+        if (evA) {
+            ++QA;
+            ga -= 1.0f;
+            ta = --na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+        } else if (evB) {
+            ++QB;
+            gb -= 1.0f;
+            tb = --nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+        } else {
+            const float v = cell * rs.inv_wd;
+            cell = 0.0f;
+            if (kahan) kahan_add(sum, comp, v);
+            else sum += v;
+            if (++c > cl) break;
+            IA = IAn;
+            fa = fan;
+            IB = IBn;
+            fb = fbn;
+            df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, c + 1 - rs.c0, IAn, fan);
+            df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, c + 1 - rs.c0, IBn, fbn);
+            na = IAn - QA;
+            nb = IBn - QB;
+            if (na > 2 || nb > 2) return false;
+            ga = (float)(IA - QA) + fa;
+            gb = (float)(IB - QB) + fb;
+            ta = na > 0 ? fminf((1.0f - ga) * rs.inv_ra, 1.0f) : 2.0f;
+            tb = nb > 0 ? fminf((1.0f - gb) * rs.inv_rb, 1.0f) : 2.0f;
+            t0 = 0.0f;
+            ev_in_cell = -1;
+        }
+        if (++ev_in_cell >= qr.cap) return false;
+    }
+    out = sum;
+    return true;
+}
+
 // March over cells [cf, cl] with the form the ray needs: the flat cell march
 // when the ray has a zero transverse component (r_b = 0), the piece march
 // otherwise.  Every exact-footprint kernel goes through here, so a ray gets
@@ -1000,12 +1189,5 @@ __device__ __forceinline__ GridBox grid_of(const DevGeom &g)
     return gb;
 }
 
-__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
-{
-    const float yv = __fsub_rn(v, comp);
-    const float t = __fadd_rn(sum, yv);
-    comp = __fsub_rn(__fsub_rn(t, sum), yv);
-    sum = t;
-}
 
 }  // namespace spl

@@ -131,6 +131,36 @@ def test_forward_explicit_rays(env, orc, degree):
     assert y[-1] == 0.0 and y[-2] == 0.0  # rays that miss the grid
 
 
+@pytest.mark.parametrize("kind", ["parallel", "cone", "rays"])
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_forward_direct(env, orc, kind, degree):
+    """SPL_FP_DIRECT: the forward as the line integral of f itself (same
+    pieces and nodes, a window of coefficients) against the oracle, and
+    adjoint to the footprint-form A^T."""
+    torch, spl = env
+    rng = np.random.default_rng(1250 + degree)
+    origin = I.centred_origin(DIMS)
+    geo = {"parallel": parallel_geometry(rng), "cone": cone_geometry(),
+           "rays": ray_geometry(rng, DIMS, origin)}[kind]
+    c = rng.normal(size=DIMS[::-1]).astype(np.float32)
+    g = spl.Geometry(DIMS, origin, geo)
+    ct = torch.tensor(c, device="cuda")
+    y = torch.full((g.n_rays,), float("nan"), dtype=torch.float32, device="cuda")
+    spl.forward(g, ct, y, spl.basis(degree, spl.SPL_FP_DIRECT))
+    g.status()
+    got = y.cpu().numpy().astype(np.float64)
+    yref = orc.forward(degree, DIMS, origin, c.astype(np.float64), oracle_geom(orc, geo))
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, yref) <= TOL, rel_l2(got, yref)
+    yy = rng.normal(size=g.n_rays).astype(np.float32)
+    ca = torch.empty(g.coeff_shape, dtype=torch.float32, device="cuda")
+    spl.adjoint(g, torch.tensor(yy, device="cuda"), ca, spl.basis(degree, spl.SPL_FP_DIRECT))
+    g.status()
+    lhs = float(got @ yy.astype(np.float64))
+    rhs = float(np.sum(c.astype(np.float64) * ca.cpu().numpy().astype(np.float64)))
+    assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(got) * np.linalg.norm(yy), (lhs, rhs)
+
+
 @pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("degree", [0, 1, 2, 3])
 def test_adjoint_parallel(env, orc, degree, form):
