@@ -106,6 +106,13 @@ def _load():
             lib.orc_features.argtypes = [C.c_int, _dp, _dp, _dp]
             lib.orc_forward_mlp.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_int, _ip, _dp, C.c_int, _dp]
             lib.orc_num_threads.restype = C.c_int
+            lib.orc_table_radius.restype = C.c_int
+            lib.orc_table_radius.argtypes = [C.c_int, C.c_double]
+            lib.orc_table_frame.argtypes = [_dp, _dp, _dp, _dp, _dp]
+            lib.orc_table_footprint.restype = C.c_double
+            lib.orc_table_footprint.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, _dp]
+            lib.orc_forward_table.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_double, _dp]
+            lib.orc_adjoint_table.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_double, _dp]
             _lib = lib
     return _lib
 
@@ -381,3 +388,45 @@ def forward_mlp(n, dims, origin, c, geom: Geometry, sizes, params, mode: int = 1
     y = np.zeros(geom.n_rays)
     _load().orc_forward_mlp(int(n), dp, op, cp, geom.ptr, len(sizes) - 1, sp, pp, int(mode), y.ctypes.data_as(_dp))
     return y
+
+
+# ---------------------------------------------------------------- footprint tables (splat form)
+TABLE_STEP = 1.0 / 32.0
+
+
+def table_radius(n, h=TABLE_STEP) -> int:
+    """M: the table nodes are (i - M) h e1 + (j - M) h e2, i, j = 0..2M."""
+    return int(_load().orc_table_radius(int(n), float(h)))
+
+
+def table_frame(direction, det_u):
+    """(w, e1, e2): unit direction and the orthonormal frame of H_w."""
+    d, dp = _d(np.asarray(direction).reshape(3))
+    u, up = _d(np.asarray(det_u).reshape(3))
+    w, e1, e2 = np.zeros(3), np.zeros(3), np.zeros(3)
+    _load().orc_table_frame(dp, up, w.ctypes.data_as(_dp), e1.ctypes.data_as(_dp), e2.ctypes.data_as(_dp))
+    return w, e1, e2
+
+
+def table_footprint(n, w, e1, e2, p, h=TABLE_STEP) -> float:
+    """Bilinear interpolation of the exact-footprint table at offset p."""
+    args = [_d(np.asarray(a).reshape(3)) for a in (w, e1, e2, p)]
+    return float(_load().orc_table_footprint(int(n), args[0][1], args[1][1], args[2][1], float(h), args[3][1]))
+
+
+def forward_table(n, dims, origin, c, geom: Geometry, h=TABLE_STEP):
+    """y = A_T c: the exact pairs with tabulated footprints (parallel views)."""
+    keep, dp, op = _grid(dims, origin)
+    cc, cp = _d(c.reshape(-1))
+    y = np.zeros(geom.n_rays)
+    _load().orc_forward_table(int(n), dp, op, cp, geom.ptr, float(h), y.ctypes.data_as(_dp))
+    return y
+
+
+def adjoint_table(n, dims, origin, y, geom: Geometry, h=TABLE_STEP):
+    """c = A_T^T y."""
+    keep, dp, op = _grid(dims, origin)
+    yy, yp = _d(np.asarray(y).reshape(-1))
+    c = np.zeros(int(np.prod(dims)))
+    _load().orc_adjoint_table(int(n), dp, op, yp, geom.ptr, float(h), c.ctypes.data_as(_dp))
+    return c.reshape(int(dims[2]), int(dims[1]), int(dims[0]))

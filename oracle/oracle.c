@@ -988,6 +988,107 @@ void orc_forward_mlp(int n, const int *dims, const double *org, const double *c,
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Footprint tables (the splat form: an approximation of Eq. 4's            */
+/* contribution).  For a parallel view the direction w is fixed, so the      */
+/* footprint is one 2-D function on H_w.  With the orthonormal frame         */
+/* e1 = (u - (u.w) w) / |u - (u.w) w| (u = det_u of the view), e2 = w x e1,  */
+/* it is tabulated exactly at the nodes (i - M) h e1 + (j - M) h e2,         */
+/* i, j = 0..2M, M = ceil(sqrt(3) W / h) + 1 (the disc of radius sqrt(3) W   */
+/* that holds the cube's shadow, one node of margin), and the footprint of   */
+/* a pair is the bilinear interpolation of the table at the pair's offset,   */
+/* zero outside the table.  The pairs are the exact ones (for_each_pair).    */
+/* ------------------------------------------------------------------------- */
+int orc_table_radius(int n, double h) { return (int)ceil(sqrt(3.0) * 0.5 * (n + 1) / h) + 1; }
+
+void orc_table_frame(const double *dir, const double *du, double *w, double *e1, double *e2)
+{
+    double nw = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    for (int d = 0; d < 3; ++d) w[d] = dir[d] / nw;
+    double uw = du[0] * w[0] + du[1] * w[1] + du[2] * w[2];
+    double e[3], ne = 0.0;
+    for (int d = 0; d < 3; ++d) { e[d] = du[d] - uw * w[d]; ne += e[d] * e[d]; }
+    ne = sqrt(ne);
+    for (int d = 0; d < 3; ++d) e1[d] = e[d] / ne;
+    e2[0] = w[1] * e1[2] - w[2] * e1[1];
+    e2[1] = w[2] * e1[0] - w[0] * e1[2];
+    e2[2] = w[0] * e1[1] - w[1] * e1[0];
+}
+
+double orc_table_footprint(int n, const double *w, const double *e1, const double *e2, double h, const double *p)
+{
+    const int M = orc_table_radius(n, h);
+    const double a = (p[0] * e1[0] + p[1] * e1[1] + p[2] * e1[2]) / h + M;
+    const double b = (p[0] * e2[0] + p[1] * e2[1] + p[2] * e2[2]) / h + M;
+    const double ia = floor(a), ib = floor(b);
+    if (ia < 0.0 || ib < 0.0 || ia + 1.0 > 2.0 * M || ib + 1.0 > 2.0 * M) return 0.0;
+    const double ta = a - ia, tb = b - ib;
+    double v[2][2];
+    for (int di = 0; di < 2; ++di)
+        for (int dj = 0; dj < 2; ++dj) {
+            double q[3];
+            for (int d = 0; d < 3; ++d) q[d] = (ia + di - M) * h * e1[d] + (ib + dj - M) * h * e2[d];
+            v[di][dj] = orc_footprint(n, w, q);
+        }
+    return (1.0 - ta) * (1.0 - tb) * v[0][0] + ta * (1.0 - tb) * v[1][0] + (1.0 - ta) * tb * v[0][1] +
+           ta * tb * v[1][1];
+}
+
+typedef struct { int n; const double *w, *e1, *e2; double h; const double *c; double yr; double *cout; double sum; } tab_ctx;
+
+static void tabf_visit(void *vctx, long long kidx, const int *k, const double *p)
+{
+    (void)k;
+    tab_ctx *x = (tab_ctx *)vctx;
+    x->sum += x->c[kidx] * orc_table_footprint(x->n, x->w, x->e1, x->e2, x->h, p);
+}
+
+static void taba_visit(void *vctx, long long kidx, const int *k, const double *p)
+{
+    (void)k;
+    tab_ctx *x = (tab_ctx *)vctx;
+    x->cout[kidx] += x->yr * orc_table_footprint(x->n, x->w, x->e1, x->e2, x->h, p);
+}
+
+/* the view of ray r of a parallel geometry and its table frame */
+static void table_ray(const orc_geom *g, long long r, double *s, double *w, double *e1, double *e2)
+{
+    double ww[3];
+    orc_geom_ray(g, r, s, ww);
+    const int v = (int)(r / ((long long)g->nu * g->nv));
+    orc_table_frame(g->dir_or_src + 3 * v, g->det_u + 3 * v, w, e1, e2);
+}
+
+/* y = A_T c over the exact pair set (parallel geometries only) */
+void orc_forward_table(int n, const int *dims, const double *org, const double *c, const orc_geom *g, double h,
+                       double *y)
+{
+    long long nr = orc_geom_rays(g);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long long r = 0; r < nr; ++r) {
+        double s[3], w[3], e1[3], e2[3];
+        table_ray(g, r, s, w, e1, e2);
+        tab_ctx x = {n, w, e1, e2, h, c, 0.0, NULL, 0.0};
+        for_each_pair(n, dims, org, s, w, tabf_visit, &x);
+        y[r] = x.sum;
+    }
+}
+
+/* c = A_T^T y (transpose of the same matrix), overwrites c; serial scatter */
+void orc_adjoint_table(int n, const int *dims, const double *org, const double *y, const orc_geom *g, double h,
+                       double *c)
+{
+    long long nk = (long long)dims[0] * dims[1] * dims[2], nr = orc_geom_rays(g);
+    memset(c, 0, sizeof(double) * nk);
+    for (long long r = 0; r < nr; ++r) {
+        if (y[r] == 0.0) continue;
+        double s[3], w[3], e1[3], e2[3];
+        table_ray(g, r, s, w, e1, e2);
+        tab_ctx x = {n, w, e1, e2, h, NULL, y[r], c, 0.0};
+        for_each_pair(n, dims, org, s, w, taba_visit, &x);
+    }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
