@@ -60,7 +60,19 @@ enum { SPL_RAYS = 0, SPL_PARALLEL = 1, SPL_CONE = 2 };
  * ray (the Gauss nodes of the same pieces, a window of coefficients instead
  * of footprint accumulators) on rays with three nonzero direction
  * components; everything else is as SPL_FP_QUAD (same matrix). */
-enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1, SPL_FP_DIRECT = 2 };
+enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1, SPL_FP_DIRECT = 2, SPL_FP_TABLE = 3 };
+/* SPL_FP_TABLE (parallel-beam geometries only): the splat form, an
+ * approximation.  Each view's footprint, one 2-D function on H_w, is
+ * tabulated exactly on a grid of step h = 1/32 in the frame
+ * e1 = (det_u - (det_u.w) w)/|...|, e2 = w x e1, at the nodes
+ * (i - M) h e1 + (j - M) h e2, i, j = 0..2M, M = ceil(sqrt(3)(n+1)/(2h)) + 1,
+ * and a pair's footprint is the bilinear interpolation of the table at the
+ * pair's offset (second-order accurate in h), over the exact pair set.  The
+ * tables (4 (2M+1)^2 bytes per view, 198 KB for cubic) are built on the
+ * first call per degree (device allocation and kernels, then a
+ * synchronisation).  Forward and adjoint use the same table values; other
+ * geometry kinds return SPL_ERR_UNSUPPORTED.  spl_footprint with this mode,
+ * or with SPL_FP_DIRECT, evaluates the exact footprint. */
 /* adjoint forms for view geometries: SPL_ADJ_AUTO picks the faster one on
  * this GPU (the scatter form); SPL_ADJ_GATHER walks coefficient bricks and
  * accumulates in shared memory (no global atomics); SPL_ADJ_SCATTER walks
@@ -108,8 +120,9 @@ typedef struct {
  *   degree: n in 0..3 (B-spline degree of the tensor-product basis).
  *   mode:   SPL_FP_QUAD (exact piecewise Gauss-Legendre footprint),
  *           SPL_FP_DIRECT (the same operator; forward as the direct line
- *           integral of f) or SPL_FP_MLP (learned footprint f_theta,
- *           Algorithm 2's f_theta*);
+ *           integral of f), SPL_FP_TABLE (tabulated footprints, parallel
+ *           beams) or SPL_FP_MLP (learned footprint f_theta, Algorithm 2's
+ *           f_theta*);
  *           SPL_FP_MLP needs `mlp` built for the same degree.
  *   kahan:  nonzero = compensated (Kahan) FP32 sum of the slab partials along
  *           each ray; zero = plain FP32 sum.

@@ -103,7 +103,7 @@ spl_status check_basis(const spl_basis_desc *b)
 {
     if (!b) return fail(SPL_ERR_ARG, "basis descriptor is NULL");
     if (b->degree < 0 || b->degree > 3) return fail(SPL_ERR_ARG, "degree %d not in 0..3", b->degree);
-    if (b->mode != SPL_FP_QUAD && b->mode != SPL_FP_MLP && b->mode != SPL_FP_DIRECT)
+    if (b->mode != SPL_FP_QUAD && b->mode != SPL_FP_MLP && b->mode != SPL_FP_DIRECT && b->mode != SPL_FP_TABLE)
         return fail(SPL_ERR_ARG, "unknown footprint mode %d", b->mode);
     if (b->mode == SPL_FP_MLP && !b->mlp) return fail(SPL_ERR_ARG, "SPL_FP_MLP needs an MLP");
     if (b->separable != SPL_SEP_AUTO && b->separable != SPL_SEP_OFF)
@@ -269,6 +269,17 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
                 if (!(l > 0.0)) { free(g->views_host); free(g); return fail(SPL_ERR_NONFINITE, "view %d: zero direction", k); }
                 for (int e = 0; e < 3; ++e) P.src[e] /= l;
                 dir_setup(P.src, P.dir);
+                // footprint-table frame: det_u without its w component, and w x e1
+                double e[3];
+                const double uw = dot3(P.du, P.src);
+                for (int q = 0; q < 3; ++q) e[q] = P.du[q] - uw * P.src[q];
+                const double ne = sqrt(dot3(e, e));
+                if (!(ne > 0.0)) {
+                    free(g->views_host); free(g);
+                    return fail(SPL_ERR_ARG, "view %d: det_u is parallel to the ray direction", k);
+                }
+                for (int q = 0; q < 3; ++q) P.e1[q] = e[q] / ne;
+                cross3(P.src, P.e1, P.e2);
                 if (fabs(dot3(P.src, P.nrm)) < 1e-12) {
                     free(g->views_host); free(g);
                     return fail(SPL_ERR_ARG, "view %d: ray direction lies in the detector plane", k);
@@ -322,8 +333,11 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
                 free(g);
                 return fail(SPL_ERR_OOM, "host allocation failed");
             }
-            for (int i = 0; i < d.n_views; ++i)
-                view_const(g->views_host[view_order[i]].dir, view_order[i], dg.n, g->vconst[i]);
+            for (int i = 0; i < d.n_views; ++i) {
+                const ViewPose &P = g->views_host[view_order[i]];
+                view_const(P.dir, view_order[i], dg.n, g->vconst[i]);
+                view_const_frame(P.dir, P.e1, P.e2, g->vconst[i]);
+            }
             order_off = (payload + 255) & ~(size_t)255;
             payload = order_off + (size_t)d.n_views * sizeof(int);
         }
@@ -379,6 +393,7 @@ extern "C" void spl_destroy_geometry(spl_geometry *g)
 {
     if (!g) return;
     plane_free(g->plane);
+    table_free(g->table);
     free(g->vconst);
     if (g->dev_block) cudaFree(g->dev_block);
     free(g->views_host);

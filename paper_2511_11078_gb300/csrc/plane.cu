@@ -553,7 +553,7 @@ extern "C" spl_status spl_prepare(spl_geometry *g, const spl_basis_desc *basis, 
     if (!g) return spl::fail(SPL_ERR_ARG, "geometry is NULL");
     spl_status s = spl::check_basis(basis);
     if (s != SPL_OK) return s;
-    if (basis->mode == SPL_FP_MLP || basis->separable == SPL_SEP_OFF) return SPL_OK;
+    if (basis->mode == SPL_FP_MLP || basis->mode == SPL_FP_TABLE || basis->separable == SPL_SEP_OFF) return SPL_OK;
     spl_status err;
     spl::plane_ready(g, basis->degree, (cudaStream_t)stream, &err);
     return err;

@@ -136,12 +136,6 @@ struct BrickSink {
 };
 
 // ---------------------------------------------------------------- forward
-__device__ __forceinline__ void tile_pixel(int &iu, int &iv)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    iu = blockIdx.x * 16 + (wid & 1) * 8 + (lane & 7);
-    iv = blockIdx.y * 8 + (wid >> 1) * 4 + (lane >> 3);
-}
 
 // View classes of a view-kernel launch.  VM_MIXED: cone views, the march
 // form (flat or general) is chosen per ray.  VM_FLAT / VM_GENERAL: parallel
@@ -156,28 +150,6 @@ __device__ __forceinline__ bool march_vm(const RaySetup &rs, int cf, int cl, con
     if constexpr (VM == VM_FLAT) return cell_march<N, Sink, true>(rs, cf, cl, qr, sk);
     else if constexpr (VM == VM_GENERAL) return piece_march<N, Sink>(rs, cf, cl, qr, sk);
     else return march<N>(rs, cf, cl, qr, sk);
-}
-
-// Rays of a parallel view: the view's constants replace the set-up's
-// per-thread copies of the same values, so the march reads them from the
-// kernel parameter (uniform across the block).
-__device__ __forceinline__ void use_view_const(const ViewConst &V, RaySetup &rs)
-{
-    rs.ra = V.ra;
-    rs.rb = V.rb;
-    rs.inv_ra = V.inv_ra;
-    rs.inv_rb = V.inv_rb;
-    rs.inv_wd = V.inv_wd;
-    rs.rah = V.rah;
-    rs.ral = V.ral;
-    rs.rbh = V.rbh;
-    rs.rbl = V.rbl;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        rs.S[q] = V.S[q];
-        rs.lo[q] = V.lo[q];
-        rs.hi[q] = V.hi[q];
-    }
 }
 
 // blocks per SM the register budget is sized for (measured): the flat form
@@ -606,7 +578,7 @@ static void for_view_chunks(const spl_geometry *g, int v0, int count, F launch)
 static int plane_views(const spl_geometry *g, const spl_basis_desc *b, cudaStream_t st, spl_status *err)
 {
     *err = SPL_OK;
-    if (b->separable == SPL_SEP_OFF || b->mode == SPL_FP_MLP || !g->plane) return 0;
+    if (b->separable == SPL_SEP_OFF || b->mode == SPL_FP_MLP || b->mode == SPL_FP_TABLE || !g->plane) return 0;
     spl_status e;
     const bool ok = plane_ready(const_cast<spl_geometry *>(g), b->degree, st, &e);
     if (!ok && e != SPL_OK && e != SPL_ERR_OOM) *err = e;  // out of memory: walk the views instead
@@ -761,6 +733,7 @@ extern "C" spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *b
     if (s != SPL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (b->mode == SPL_FP_MLP) return spl::forward_mlp(g, b, c_dev, y_dev, st);
+    if (b->mode == SPL_FP_TABLE) return spl::table_forward(g, b, c_dev, y_dev, st);
     SPL_DISPATCH(b->degree, forward_quad, g, b, c_dev, y_dev, st)
 }
 
@@ -771,6 +744,7 @@ extern "C" spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *b
     if (s != SPL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (b->mode == SPL_FP_MLP) return spl::adjoint_mlp(g, b, y_dev, c_dev, st);
+    if (b->mode == SPL_FP_TABLE) return spl::table_adjoint(g, b, y_dev, c_dev, st);
     if (b->adjoint != SPL_ADJ_AUTO && b->adjoint != SPL_ADJ_GATHER && b->adjoint != SPL_ADJ_SCATTER)
         return fail(SPL_ERR_ARG, "unknown adjoint form %d", b->adjoint);
     SPL_DISPATCH(b->degree, adjoint_quad, g, b, y_dev, c_dev, st)

@@ -9,6 +9,7 @@
 
 namespace spl {
 struct PlaneGroup;
+struct TableSet;
 }
 
 struct spl_geometry {
@@ -19,6 +20,7 @@ struct spl_geometry {
     int device;
     spl::PlaneGroup *plane;       // slice-separable view group (parallel geometries), or NULL
     spl::ViewConst *vconst;       // parallel geometries: per-view constants in view_order order (host)
+    spl::TableSet *table;         // footprint tables (SPL_FP_TABLE), built on first use per degree, or NULL
 };
 
 namespace spl {
@@ -82,5 +84,11 @@ spl_status plane_forward(const spl_geometry *g, int degree, int kahan, const flo
 // writes every coefficient (the other views' scatter adds after it)
 spl_status plane_adjoint(const spl_geometry *g, int degree, const float *y, float *c, cudaStream_t st);
 void plane_free(PlaneGroup *pg);
+
+// Footprint tables of the views of a parallel geometry (table.cu), built on
+// first use per degree.
+spl_status table_forward(const spl_geometry *g, const spl_basis_desc *b, const float *c, float *y, cudaStream_t st);
+spl_status table_adjoint(const spl_geometry *g, const spl_basis_desc *b, const float *y, float *c, cudaStream_t st);
+void table_free(TableSet *ts);
 
 }  // namespace spl

@@ -120,8 +120,11 @@ struct ViewConst {
     int view;       // view index
     int S[3];       // signed linear strides of (d, a, b)
     int lo[3], hi[3];
+    // footprint-table frame (e1, e2) of H_w in the mirrored (d, a, b) frame,
+    // as double-float pairs: E1[q] = sg_q e1[ax_q]
+    float E1h[3], E1l[3], E2h[3], E2l[3];
 };
-constexpr int kViewChunk = 256;  // views per launch (19.5 KB of parameters)
+constexpr int kViewChunk = 192;  // views per launch (23.25 KB of parameters)
 struct ViewChunk {
     ViewConst v[kViewChunk];
 };
@@ -147,6 +150,19 @@ __host__ __device__ inline void view_const(const DirSetup &ds, int view, const i
     }
 }
 
+// the footprint-table frame of a parallel view in its mirrored frame
+__host__ __device__ inline void view_const_frame(const DirSetup &ds, const double (&e1)[3], const double (&e2)[3],
+                                                 ViewConst &vc)
+{
+    for (int q = 0; q < 3; ++q) {
+        const double a = ds.sg[q] * e1[ds.ax[q]], b = ds.sg[q] * e2[ds.ax[q]];
+        vc.E1h[q] = (float)a;
+        vc.E1l[q] = (float)(a - (double)vc.E1h[q]);
+        vc.E2h[q] = (float)b;
+        vc.E2l[q] = (float)(b - (double)vc.E2h[q]);
+    }
+}
+
 // Per-view pose in FP64 (one entry per view of a view geometry).
 struct ViewPose {
     double src[3];       // parallel: unit ray direction; cone: source position
@@ -155,6 +171,7 @@ struct ViewPose {
     double nrm[3];       // unit normal of the detector plane
     double ud[3], vd[3]; // dual axes: a = <P - dc, ud>, b = <P - dc, vd> for P on the plane
     DirSetup dir;        // parallel views: direction set-up shared by all rays of the view
+    double e1[3], e2[3]; // parallel views: orthonormal frame of H_w of the footprint tables
 };
 
 struct DevGeom {
@@ -1119,6 +1136,37 @@ __device__ __forceinline__ bool march(const RaySetup &rs, int cf, int cl, const 
 {
     if (rs.rb == 0.0f) return cell_march<N, Sink, true>(rs, cf, cl, qr, sink);
     return piece_march<N, Sink>(rs, cf, cl, qr, sink);
+}
+
+// pixel of this thread in a view kernel: a 128-thread block covers a 16 x 8
+// detector tile, a warp an 8 x 4 sub-tile
+__device__ __forceinline__ void tile_pixel(int &iu, int &iv)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    iu = blockIdx.x * 16 + (wid & 1) * 8 + (lane & 7);
+    iv = blockIdx.y * 8 + (wid >> 1) * 4 + (lane >> 3);
+}
+
+// Rays of a parallel view: the view's constants replace the set-up's
+// per-thread copies of the same values, so the march reads them from the
+// kernel parameter (uniform across the block).
+__device__ __forceinline__ void use_view_const(const ViewConst &V, RaySetup &rs)
+{
+    rs.ra = V.ra;
+    rs.rb = V.rb;
+    rs.inv_ra = V.inv_ra;
+    rs.inv_rb = V.inv_rb;
+    rs.inv_wd = V.inv_wd;
+    rs.rah = V.rah;
+    rs.ral = V.ral;
+    rs.rbh = V.rbh;
+    rs.rbl = V.rbl;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        rs.S[q] = V.S[q];
+        rs.lo[q] = V.lo[q];
+        rs.hi[q] = V.hi[q];
+    }
 }
 
 // ------------------------------------------------------------------ rays of a geometry

@@ -16,7 +16,7 @@ from . import build as _build
 
 SPL_OK = 0
 SPL_RAYS, SPL_PARALLEL, SPL_CONE = 0, 1, 2
-SPL_FP_QUAD, SPL_FP_MLP, SPL_FP_DIRECT = 0, 1, 2
+SPL_FP_QUAD, SPL_FP_MLP, SPL_FP_DIRECT, SPL_FP_TABLE = 0, 1, 2, 3
 SPL_ADJ_AUTO, SPL_ADJ_GATHER, SPL_ADJ_SCATTER = 0, 1, 2
 SPL_SEP_AUTO, SPL_SEP_OFF = 0, 1
 MLP_PARAMS = 8769
