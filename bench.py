@@ -438,6 +438,19 @@ def run_ours(args):
             gsub.status()
             per_class[name]["A_direct_ms"] = ad_ms
             per_class[name]["A_direct_gcontrib_s"] = cl["pairs"] / (ad_ms * 1e-3) / 1e9
+            # the splat form (SPL_FP_TABLE: tabulated footprints, an
+            # approximation) on the same views, and its distance to exact A
+            bt = spl.basis(n, spl.SPL_FP_TABLE)
+            yt = torch.empty_like(ysub)
+            spl.forward(gsub, c_true, yt, bt)
+            spl.adjoint(gsub, yt, csub, bt)
+            at_t = time_call(lambda: spl.forward(gsub, c_true, yt, bt))
+            att_t = time_call(lambda: spl.adjoint(gsub, yt, csub, bt))
+            spl.forward(gsub, c_true, ysub, proj.basis)
+            gsub.status()
+            per_class[name]["A_table_ms"] = at_t
+            per_class[name]["AT_table_ms"] = att_t
+            per_class[name]["table_A_rel_l2_vs_exact"] = float((yt - ysub).norm() / ysub.norm())
 
     contrib_step = 2 * pairs  # A and A^T visit the same pairs
     value = ws * contrib_step / (ms * 1e-3) / 1e9
