@@ -57,10 +57,10 @@ FLOP_PER_PAIR = 2
 NODES_PER_PIECE = {0: 1, 1: 2, 2: 4, 3: 5}
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) per launch from the ncu capture of each kernel
-# on this workload (profiles/k_*-general-tilt128-cubic.md: the general-view
+# on this workload (profiles/k_*_pviews*-general-tilt128-cubic.md: the general-view
 # launches); to be reset to None
 # whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"k_forward_views": None, "k_adjoint_views_scatter": None,
+NCU_TRAFFIC = {"k_forward_pviews": 8.939776e6 + 768.0, "k_adjoint_pviews_scatter": 17.911808e6 + 768.0,
                "k_adjoint_bricks": None}
 
 
@@ -492,10 +492,10 @@ def run_ours(args):
                  + gen["flat_pieces"] * (n + 1) * FLOP_PER_FLAT_NODE[n] + gen["pairs"] * FLOP_PER_PAIR)
     pc_gen = per_class["general" if "general" in per_class else "separable"]
     if pc_gen["A_ms"] >= pc_gen["AT_ms"]:
-        dominant, dom_ms = "k_forward_views (general views)", pc_gen["A_ms"]
+        dominant, dom_ms = "k_forward_pviews (general views)", pc_gen["A_ms"]
     else:
         dominant = ("k_adjoint_bricks" if args.adjoint == "gather" else
-                    "k_adjoint_views_scatter (general views)")
+                    "k_adjoint_pviews_scatter (general views)")
         dom_ms = pc_gen["AT_ms"]
     achieved = flops_gen / (dom_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": fp32_peak_tflops,
