@@ -114,3 +114,19 @@ def test_null_arguments_are_rejected(spl):
     assert L.spl_count_pairs(None, 3, None, None) == 1
     assert L.spl_prepare(None, C.byref(b), None) == 1
     assert L.spl_features(7, 1, None, None, None, None) == 1
+
+
+def test_basis_modes_are_validated_on_the_host(spl):
+    """Every footprint mode the header names passes the descriptor check
+    (count 0: no device work); unknown modes and separable settings fail."""
+    L = spl.lib()
+    for mode in (spl.SPL_FP_QUAD, spl.SPL_FP_DIRECT, spl.SPL_FP_TABLE):
+        b = spl.basis(3, mode)
+        assert L.spl_footprint(C.byref(b), 0, None, None, None, None) == 0
+    bad = spl.basis(3)
+    bad.mode = 9
+    assert L.spl_footprint(C.byref(bad), 0, None, None, None, None) == 1
+    bad = spl.basis(3, separable=7)
+    assert L.spl_footprint(C.byref(bad), 0, None, None, None, None) == 1
+    mlp_without_net = spl.basis(3, spl.SPL_FP_MLP)
+    assert L.spl_footprint(C.byref(mlp_without_net), 0, None, None, None, None) == 1
