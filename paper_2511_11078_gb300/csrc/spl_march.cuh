@@ -632,6 +632,91 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v)
     sum = t;
 }
 
+// Window update of one Gauss node, acc[d][i][k] += wd[d] wa[i] wb[k], with
+// packed FP32x2 multiplies and FMAs two k at a time (__fmul2_rn,
+// __ffma2_rn: each component rounds like the scalar operation, so the sums
+// are those of the scalar loop, in half the instructions).
+template <int N>
+__device__ __forceinline__ void window_update(float (&acc)[N + 1][N + 1][N + 1], const float (&wd)[N + 1],
+                                              const float (&wa)[N + 1], const float (&wb)[N + 1])
+{
+    constexpr int K2 = (N + 1) / 2;
+#pragma unroll
+    for (int i = 0; i <= N; ++i) {
+        float2 pk[K2 > 0 ? K2 : 1];
+#pragma unroll
+        for (int p = 0; p < K2; ++p)
+            pk[p] = __fmul2_rn(make_float2(wa[i], wa[i]), make_float2(wb[2 * p], wb[2 * p + 1]));
+        const float pl = ((N + 1) & 1) ? wa[i] * wb[N] : 0.0f;
+#pragma unroll
+        for (int d = 0; d <= N; ++d) {
+            const float2 w2 = make_float2(wd[d], wd[d]);
+#pragma unroll
+            for (int p = 0; p < K2; ++p) {
+                float2 a = make_float2(acc[d][i][2 * p], acc[d][i][2 * p + 1]);
+                a = __ffma2_rn(w2, pk[p], a);
+                acc[d][i][2 * p] = a.x;
+                acc[d][i][2 * p + 1] = a.y;
+            }
+            if ((N + 1) & 1) acc[d][i][N] = fmaf(wd[d], pl, acc[d][i][N]);
+        }
+    }
+}
+
+// The flat form's update, acc[d][i][0] += wd[d] wa[i], two i at a time.
+template <int N>
+__device__ __forceinline__ void window_update_flat(float (&acc)[N + 1][N + 1][1], const float (&wd)[N + 1],
+                                                   const float (&wa)[N + 1])
+{
+    constexpr int I2 = (N + 1) / 2;
+#pragma unroll
+    for (int d = 0; d <= N; ++d) {
+        const float2 w2 = make_float2(wd[d], wd[d]);
+#pragma unroll
+        for (int p = 0; p < I2; ++p) {
+            float2 a = make_float2(acc[d][2 * p][0], acc[d][2 * p + 1][0]);
+            a = __ffma2_rn(w2, make_float2(wa[2 * p], wa[2 * p + 1]), a);
+            acc[d][2 * p][0] = a.x;
+            acc[d][2 * p + 1][0] = a.y;
+        }
+        if ((N + 1) & 1) acc[d][N][0] = fmaf(wd[d], wa[N], acc[d][N][0]);
+    }
+}
+
+// f = sum_d wd[d] sum_i wa[i] sum_k wb[k] cw[d][i][k] (the direct march's
+// node value), with packed FP32x2 FMAs over pairs of i.
+template <int N>
+__device__ __forceinline__ float window_contract(const float (&cw)[N + 1][N + 1][N + 1], const float (&wd)[N + 1],
+                                                 const float (&wa)[N + 1], const float (&wb)[N + 1])
+{
+    constexpr int I2 = (N + 1) / 2;
+    float f = 0.0f;
+#pragma unroll
+    for (int d = 0; d <= N; ++d) {
+        float u = 0.0f;
+        if constexpr (I2 > 0) {
+            float2 u2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int p = 0; p < I2; ++p) {
+                float2 t2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int k = 0; k <= N; ++k)
+                    t2 = __ffma2_rn(make_float2(wb[k], wb[k]), make_float2(cw[d][2 * p][k], cw[d][2 * p + 1][k]), t2);
+                u2 = __ffma2_rn(make_float2(wa[2 * p], wa[2 * p + 1]), t2, u2);
+            }
+            u = u2.x + u2.y;
+        }
+        if ((N + 1) & 1) {
+            float tk = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= N; ++k) tk = fmaf(wb[k], cw[d][N][k], tk);
+            u = fmaf(wa[N], tk, u);
+        }
+        f = fmaf(wd[d], u, f);
+    }
+    return f;
+}
+
 // ------------------------------------------------------------------ cell march
 // Cells along d*.  With v = u + W the bases of one axis sit at the integers
 // and basis l covers v in (l, l + N + 1), so the N+1 bases whose support
@@ -725,22 +810,11 @@ __device__ __forceinline__ bool cell_march(const RaySetup &rs, int cf, int cl, c
 #pragma unroll
                     for (int d = 0; d <= N; ++d) wd[d] *= cw;
                     if constexpr (FLAT) {
-#pragma unroll
-                        for (int d = 0; d <= N; ++d)
-#pragma unroll
-                            for (int i = 0; i <= N; ++i) acc[d][i][0] = fmaf(wd[d], wa[i], acc[d][i][0]);
+                        window_update_flat<N>(acc, wd, wa);
                     } else {
                         float wb[N + 1];
                         bweights<N>(fmaf(rs.rb, t, gb), wb);
-#pragma unroll
-                        for (int i = 0; i <= N; ++i)
-#pragma unroll
-                            for (int k = 0; k <= N; ++k) {
-                                const float pk = wa[i] * wb[k];
-#pragma unroll
-                                for (int d = 0; d <= N; ++d)
-                                    acc[d][i][(FLAT ? 0 : k)] = fmaf(wd[d], pk, acc[d][i][(FLAT ? 0 : k)]);
-                            }
+                        window_update<N>(acc, wd, wa, wb);
                     }
                 }
                 sink.piece();
@@ -878,14 +952,7 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
                 const float cw = half * qr.w[q];
 #pragma unroll
                 for (int d = 0; d <= N; ++d) wd[d] *= cw;
-#pragma unroll
-                for (int i = 0; i <= N; ++i)
-#pragma unroll
-                    for (int k = 0; k <= N; ++k) {
-                        const float pk = wa[i] * wb[k];
-#pragma unroll
-                        for (int d = 0; d <= N; ++d) acc[d][i][k] = fmaf(wd[d], pk, acc[d][i][k]);
-                    }
+                window_update<N>(acc, wd, wa, wb);
             }
             sink.piece();
         }
@@ -1037,19 +1104,7 @@ __device__ __forceinline__ bool direct_march(const RaySetup &rs, const float *__
                 bweights<N>(t, wd);
                 bweights<N>(fmaf(rs.ra, t, ga), wa);
                 bweights<N>(fmaf(rs.rb, t, gb), wb);
-                float f = 0.0f;
-#pragma unroll
-                for (int d = 0; d <= N; ++d) {
-                    float u = 0.0f;
-#pragma unroll
-                    for (int i = 0; i <= N; ++i) {
-                        float tk = 0.0f;
-#pragma unroll
-                        for (int k = 0; k <= N; ++k) tk = fmaf(wb[k], cw[d][i][k], tk);
-                        u = fmaf(wa[i], tk, u);
-                    }
-                    f = fmaf(wd[d], u, f);
-                }
+                const float f = window_contract<N>(cw, wd, wa, wb);
                 piece = fmaf(qr.w[q], f, piece);
             }
             cell = fmaf(half, piece, cell);
