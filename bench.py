@@ -60,7 +60,7 @@ SMS, FP32_LANES = 152, 128
 # on this workload (profiles/k_*_pviews*-general-tilt128-cubic.md: the general-view
 # launches); to be reset to None
 # whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"k_forward_pviews": None, "k_adjoint_pviews_scatter": None,
+NCU_TRAFFIC = {"k_forward_pviews": 8.487168e6 + 1024.0, "k_adjoint_pviews_scatter": 17.908736e6 + 768.0,
                "k_adjoint_bricks": None}
 
 
