@@ -87,6 +87,26 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """The largest of the ranks' values (the step time of the slowest
+    replica); the value itself at one rank."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ws: int, contributions_per_step: float, ms: float) -> float:
+    """Whole-job throughput of ws independent replicas (weak scaling): the
+    contributions all ranks processed per second at the slowest rank's step
+    time, in G-contributions/s."""
+    return ws * contributions_per_step / (ms * 1e-3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -383,11 +403,7 @@ def run_ours(args):
     geom.status()
     step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
     fwd_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
-    ms = sum(step_ms) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / args.steps, ws, dev)
 
     # adjoint alone (events around one launch, after an L2 flush)
     adj_ms = []
@@ -453,7 +469,7 @@ def run_ours(args):
             per_class[name]["table_A_rel_l2_vs_exact"] = float((yt - ysub).norm() / ysub.norm())
 
     contrib_step = 2 * pairs  # A and A^T visit the same pairs
-    value = ws * contrib_step / (ms * 1e-3) / 1e9
+    value = replica_value(ws, contrib_step, ms)
 
     # end to end through the C ABI with host buffers: H2D of c and y from
     # pinned memory, A c and A^T y, D2H of both results
@@ -523,7 +539,7 @@ def run_ours(args):
             "s_per_recon_iter": ms / 1e3,
             "A_ms": fwd, "AT_ms": adj,
             "A_gcontrib_s": pairs / (fwd * 1e-3) / 1e9, "AT_gcontrib_s": pairs / (adj * 1e-3) / 1e9,
-            "e2e": {"value": ws * contrib_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": replica_value(ws, contrib_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": args.steps * launches_step,
             "view_classes": per_class,

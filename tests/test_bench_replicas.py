@@ -1,0 +1,68 @@
+"""The benchmark's multi-process path on CPU (gloo, world size 2): every rank
+runs its own replica, the step time is the maximum over ranks, the value is
+the whole job's throughput at that time, and the reference arm runs on rank 0
+only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, ws, port, times, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    ms = bench.max_over_ranks(times[rank], ws)
+    out.put((rank, ms, bench.replica_value(ws, 1e9, ms)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_value_with_two_gloo_ranks():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    times = [12.5, 20.0]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, value in res:
+        assert ms == 20.0  # the slowest replica's step time on every rank
+        assert value == pytest.approx(2 * 1e9 / 20e-3 / 1e9)  # both replicas' work over that time
+
+
+def test_one_rank_keeps_its_own_time():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.max_over_ranks(7.0, 1) == 7.0
+    assert bench.replica_value(1, 2e9, 10.0) == pytest.approx(200.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under a launcher, ranks other than 0 exit at once without output."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], env=env, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
