@@ -180,6 +180,36 @@ def test_mlp_projector_matches_oracle(env, orc):
     assert np.linalg.norm(got - yq) <= 0.05 * np.linalg.norm(yq)
 
 
+def test_mlp_projector_full_size_sampled(env, orc):
+    """The learned-footprint projector on the benchmark's 128^3 cubic tilt
+    workload (all 244 views, the launch the benchmark times): sampled rays
+    against the oracle's BF16-contract projector, each sampled ray evaluated
+    as a one-pixel view with the same direction and pixel centre."""
+    torch, spl, learn = env
+    m = _trained(env)
+    wl = I.workload_tilt(3)
+    g = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    y = torch.empty(g.n_rays, dtype=torch.float32, device="cuda")
+    spl.forward(g, torch.tensor(wl.coeffs, device="cuda"), y, spl.basis(3, spl.SPL_FP_MLP, m))
+    g.status()
+    rng = np.random.default_rng(5350)
+    rays = np.sort(rng.choice(g.n_rays, 24, replace=False))
+    got = y.cpu().numpy()[rays].astype(np.float64)
+    prm = m.get_params().astype(np.float64)
+    geo = wl.geometry
+    per = geo.nu * geo.nv
+    ref = np.zeros(len(rays))
+    for t, r in enumerate(rays):
+        k = int(r // per)
+        iv, iu = divmod(int(r - k * per), geo.nu)
+        a, b = iu - 0.5 * (geo.nu - 1), iv - 0.5 * (geo.nv - 1)
+        q = geo.det_center[k] + a * geo.det_u[k] + b * geo.det_v[k]
+        og = orc.Geometry("parallel", direction=geo.src[k:k + 1], det_center=q[None], det_u=geo.det_u[k:k + 1],
+                          det_v=geo.det_v[k:k + 1], nu=1, nv=1)
+        ref[t] = orc.forward_mlp(3, wl.dims, wl.origin, wl.coeffs.astype(np.float64), og, SIZES, prm, mode=1)[0]
+    assert np.linalg.norm(got - ref) <= 2e-3 * np.linalg.norm(ref), np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
 def test_mlp_projector_adjointness(env):
     torch, spl, learn = env
     m = _trained(env)
