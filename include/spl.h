@@ -342,8 +342,9 @@ spl_status spl_cg_step_p(long long n, float *p_dev, const float *s_dev, const do
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *spl_last_error(void);
-/* Fault injection for tests: lower the loop bound of the per-slab sweep to
- * `cap` (1..40; any other value restores the default 40).  With a bound that
+/* Fault injection for tests: lower the loop bound of the per-cell event
+ * loops (and of the per-slab pair enumeration of the learned-footprint
+ * projector) to `cap` (1..40; any other value restores the default 40).  With a bound that
  * is too small the kernels stop early, set the geometry's error flag, and
  * spl_geometry_status() reports SPL_ERR_STEPCAP.  Affects launches issued
  * after the call, process-wide.  Returns the previous bound. */

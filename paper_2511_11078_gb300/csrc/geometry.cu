@@ -60,7 +60,7 @@ static void legendre_rule(int m, double *x, double *w)
 }
 
 static QuadRule g_rules[4];
-static int g_iter_cap = kSlabIterCap;
+static int g_iter_cap = kIterCap;
 static std::once_flag g_rules_once;
 
 static void init_rules()
@@ -93,7 +93,7 @@ QuadRule quad_rule(int degree)
 int set_iter_cap(int cap)
 {
     const int old = g_iter_cap;
-    g_iter_cap = (cap < 1 || cap > kSlabIterCap) ? kSlabIterCap : cap;
+    g_iter_cap = (cap < 1 || cap > kIterCap) ? kIterCap : cap;
     return old;
 }
 

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_views(DevGeom g, MlpDev wts
         if (round < nslab) {
             MlpQueueSink sk{q, &count_s[wid], cap, cin, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2],
                             mr.ua, mr.ub, mr.va, mr.vb, 0, 0, 0.0f, 0.0f, lane, ADJ};
-            ok &= slab_sweep<N, MlpQueueSink, false>(rs, rs.j0 + round, qr, sk);
+            ok &= slab_pairs<N, MlpQueueSink>(rs, rs.j0 + round, qr, sk);
         }
         __syncwarp();
         int n = count_s[wid];

@@ -66,9 +66,9 @@ void clear_error();
 
 // Gauss-Legendre rule that integrates degree-3n polynomials exactly
 // (m = ceil((3n+1)/2) nodes), computed once per process in FP64.
-// (the rule also carries the slab loop bound, see set_iter_cap)
+// (the rule also carries the event-loop bound, see set_iter_cap)
 QuadRule quad_rule(int degree);
-// Lower the per-slab loop bound for fault-injection tests (1..kSlabIterCap;
+// Lower the event-loop bound for fault-injection tests (1..kIterCap;
 // anything else restores the default).  Returns the previous bound.
 int set_iter_cap(int cap);
 int quad_nodes(int degree);

@@ -1,38 +1,33 @@
 // spl_march.cuh -- device core of the B-spline x-ray transform (SplineSplat,
-// arXiv 2511.11078): ray set-up, the dominant-axis slab march and the exact
+// arXiv 2511.11078): ray set-up, the dominant-axis cell march and the exact
 // footprint engine shared by every kernel that walks a ray.
 //
 // Paper mapping
-//   * Definition 2.1 (dominant axis d*): a ray is marched slab by slab along
-//     d* = argmax |w_d| (ties: lowest index).  Every slab l_{d*} = j is
-//     crossed exactly once.
-//   * Algorithm 2 / Algorithm 3: at each DDA cell the bases l with
-//     l_{d*} = k_{d*} and |l - k|_inf <= R are visited, minus the bases of the
-//     two previous steps.  Their union over the (at most three) cells of one
-//     slab is exactly the set of slab bases whose support the ray crosses.
-//     Here that union is produced directly: inside slab j a second DDA runs
-//     over the knot planes of all three axes, and a rolling
-//     (n+1) x (n+1) window holds the bases whose support contains the
-//     current point of the ray.  A basis enters the window when the ray
-//     enters its support and is flushed (c_l * P) exactly once when it
-//     leaves, so no basis is visited twice and none is missed.
-//   * Eq. 4 contribution Pphi(w, s - l): with xi = x_{d*} - j the local
-//     coordinate in the slab and r_e = |w_e| / |w_{d*}|,
-//       Pphi = (1/|w_{d*}|) int_{-W}^{W} beta(xi) beta(A + r_a xi - l_a)
-//                                         beta(B + r_b xi - l_b) dxi,
-//     (A, B) = the ray's transverse coordinates on the plane x_{d*} = j.
-//     Between consecutive knot-plane crossings every factor of every window
-//     basis is one polynomial of degree n, the product has degree 3n, and
-//     m = ceil((3n+1)/2) Gauss-Legendre nodes integrate it exactly.  All
-//     (n+1)^2 window bases share the nodes of a piece: each node costs
-//     3 x (n+1) B-spline weights and one (n+1) x (n+1) outer product.
+//   * Definition 2.1 (dominant axis d*): a ray is marched cell by cell along
+//     d* = argmax |w_d| (ties: lowest index); every cell of d* that the ray's
+//     reach covers is visited exactly once.
+//   * Algorithm 2 / Algorithm 3: at each DDA step the bases of the slab
+//     l_{d*} = k_{d*} within |l - k|_inf <= R are visited, minus those of the
+//     two previous steps; over the ray, that is every basis whose support
+//     the ray crosses, each once.  Here the same set is produced by an
+//     (n+1)^3 register window of the bases whose support contains the
+//     current point: a basis enters when the ray enters its support and is
+//     flushed (c_l * P in the forward, y * P in the adjoint) exactly once
+//     when it leaves, so no basis is visited twice and none is missed.
+//   * Eq. 4 contribution Pphi(w, s - l): the integral along the ray of the
+//     product of three 1-D B-splines.  Between consecutive knot-plane
+//     crossings every factor of every window basis is one polynomial of
+//     degree n, the product has degree 3n, and m = ceil((3n+1)/2)
+//     Gauss-Legendre nodes integrate it exactly.  All (n+1)^3 window bases
+//     share the nodes of a piece: each node costs 3 x (n+1) B-spline weights
+//     and one (n+1)^3 outer product (cell_march, piece_march).
 //
 // Coordinates: index coordinates u = x - origin (bases at integers) are
 // mirrored per axis so that the ray direction is componentwise >= 0
 // (beta is even, so phi_l(x) = phi_{l'}(x') with l'_e = sign_e * l_e).
-// The ray's transverse coordinate on slab j is carried as an unevaluated
-// float pair (double-float) so that positions far from the origin keep
-// ~1e-7 absolute accuracy without FP64 arithmetic in the hot loop.
+// The ray's transverse coordinates are carried as unevaluated float pairs
+// (double-float) so that positions far from the origin keep ~1e-7 absolute
+// accuracy without FP64 arithmetic in the hot loop.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,16 +37,18 @@
 namespace spl {
 
 constexpr int kMaxNodes = 8;
-// loop bound of one slab sweep: (n+1) d-pieces plus at most n+3 events on
-// each transverse axis (r <= 1), with margin
-constexpr int kSlabIterCap = 40;
+// loop bound of the event loops: the knot crossings of one cell of the cell
+// and piece marches (at most one per transverse axis, r <= 1), and the
+// (n+1) d-pieces plus at most n+3 events per transverse axis of one slab of
+// the pair enumeration, with margin
+constexpr int kIterCap = 40;
 
 struct QuadRule {
     float x[kMaxNodes];   // Gauss-Legendre nodes on [-1, 1], m = ceil((3n+1)/2) of them
     float w[kMaxNodes];   // weights
-    float x1[kMaxNodes];  // the (n+1)-node rule: exact for degree 2n (flat rays, see slab_sweep)
+    float x1[kMaxNodes];  // the (n+1)-node rule: exact for degree 2n (flat rays, see cell_march)
     float w1[kMaxNodes];
-    int cap;              // loop bound of one slab sweep (kSlabIterCap)
+    int cap;              // loop bound of the event loops (kIterCap)
 };
 
 // Direction-dependent part of the set-up (Definition 2.1 and the mirrored
@@ -250,38 +247,6 @@ __device__ __forceinline__ void bweights(float g, float (&w)[N + 1])
     }
 }
 
-// Polynomial of the d-factor beta^N(xi) on d-piece id (xi in
-// [id - W, id + 1 - W)), as coefficients pc of B_{N,idx}(arg) with
-// arg = sgn * xi + K.  Pieces in the upper half use the mirror image
-// beta(xi) = beta(-xi) = B_{N,id}(1 - g), so that the polynomial evaluated is
-// always one that is accurate where it approaches zero.
-template <int N>
-__device__ __forceinline__ void piece_coeffs(int id, float (&pc)[N + 1], float &sgn, float &K)
-{
-    constexpr float W = 0.5f * (N + 1);
-    const bool low = 2 * id <= N;
-    const int idx = low ? N - id : id;
-    const float g0 = W - (float)id;  // g = xi + g0
-    sgn = low ? 1.0f : -1.0f;
-    K = low ? g0 : 1.0f - g0;
-#pragma unroll
-    for (int k = 0; k <= N; ++k) {
-        float v = BSpl<N>::c(N, k);
-#pragma unroll
-        for (int i = N - 1; i >= 0; --i) v = (idx == i) ? BSpl<N>::c(i, k) : v;
-        pc[k] = v;
-    }
-}
-
-template <int N>
-__device__ __forceinline__ float horner(const float (&pc)[N + 1], float g)
-{
-    float v = pc[N];
-#pragma unroll
-    for (int k = N - 1; k >= 0; --k) v = fmaf(v, g, pc[k]);
-    return v;
-}
-
 // ------------------------------------------------------------------ ray set-up
 struct GridBox {
     int n[3];
@@ -425,69 +390,20 @@ __device__ __forceinline__ void df_coord(float Ah, float Al, float rh, float rl,
     f = __fsub_rn(fr, adj);
 }
 
-// ------------------------------------------------------------------ slab sweep
-// Integrate one piece [x0, x1] of slab-local xi with M Gauss-Legendre nodes
-// into the (N+1) x (N+1) window accumulators.
-template <int N>
-__device__ __forceinline__ void integrate_piece(float x0, float x1, int id, float Ka, float Kb, float ra, float rb,
-                                                const QuadRule &qr, float (&acc)[N + 1][N + 1])
-{
-    constexpr int M = GL<N>::M;
-    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
-    float pc[N + 1], sgn, Kd;
-    piece_coeffs<N>(id, pc, sgn, Kd);
-#pragma unroll
-    for (int q = 0; q < M; ++q) {
-        const float xi = fmaf(half, qr.x[q], mid);
-        const float bd = horner<N>(pc, fmaf(sgn, xi, Kd));
-        float wa[N + 1], wb[N + 1];
-        bweights<N>(fmaf(ra, xi, Ka), wa);
-        bweights<N>(fmaf(rb, xi, Kb), wb);
-        const float cw = (half * qr.w[q]) * bd;
-#pragma unroll
-        for (int i = 0; i <= N; ++i) {
-            const float t = cw * wa[i];
-#pragma unroll
-            for (int k = 0; k <= N; ++k) acc[i][k] = fmaf(t, wb[k], acc[i][k]);
-        }
-    }
-}
-
-// Flat ray (r_b = 0): the b-factor is constant along the ray, so only the
-// 1-D integrals G_i = int beta(xi) beta(A + r_a xi - l_a(i)) dxi (degree 2N,
-// N+1 nodes) are accumulated; F_ik = G_i * wb_k at the flush.
-template <int N>
-__device__ __forceinline__ void integrate_piece_flat(float x0, float x1, int id, float Ka, float ra,
-                                                     const QuadRule &qr, float (&G)[N + 1])
-{
-    const float half = 0.5f * (x1 - x0), mid = 0.5f * (x0 + x1);
-    float pc[N + 1], sgn, Kd;
-    piece_coeffs<N>(id, pc, sgn, Kd);
-#pragma unroll
-    for (int q = 0; q <= N; ++q) {
-        const float xi = fmaf(half, qr.x1[q], mid);
-        const float bd = horner<N>(pc, fmaf(sgn, xi, Kd));
-        float wa[N + 1];
-        bweights<N>(fmaf(ra, xi, Ka), wa);
-        const float cw = (half * qr.w1[q]) * bd;
-#pragma unroll
-        for (int i = 0; i <= N; ++i) G[i] = fmaf(cw, wa[i], G[i]);
-    }
-}
-
-// Sweep slab j of a ray: every basis l' = (j, la, lb) whose support the ray
-// crosses in this slab is handed to sink.flush(j, la, lb, F) exactly once,
-// with F = |w_d| * Pphi(w, s - l).  sink.relevant(...) tells whether any
-// basis of the current window matters (skips the nodes of pieces that
-// cannot reach the sink); sink.slab(IA, fa, IB, fb, N) receives the ray's
-// transverse coordinates on the slab plane (A_j = IA + fa, B_j = IB + fb);
-// every window of the slab lies in la in [IA - N, IA + 2N + 4] (same for b),
-// which lets a sink skip its per-flush bounds checks on interior slabs.
-// QUAD = false enumerates the pairs only: F = 1 for a basis whose support
-// the ray crosses with positive length, 0 otherwise (no quadrature).
-// Returns false if the loop bound was reached.
-template <int N, class Sink, bool QUAD = true, bool FLAT = false>
-__device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const QuadRule &qr, Sink &sink)
+// ------------------------------------------------------------------ slab pairs
+// Pairs of one slab j of a ray, without quadrature: every basis
+// l' = (j, la, lb) whose support the ray crosses with positive length inside
+// the slab is handed to sink.flush(j, la, lb, 1.0f) exactly once (the other
+// bases of a window get 0).  A second DDA inside the slab runs over the knot
+// planes of the transverse axes with a rolling (N+1) x (N+1) window of the
+// bases whose support holds the current point; sink.relevant(a0, a1, b0, b1)
+// says whether a window can reach the sink, sink.slab(IA, fa, IB, fb, N)
+// receives the ray's transverse coordinates on the slab plane
+// (A_j = IA + fa, B_j = IB + fb).  The learned-footprint projector enumerates
+// its (ray, basis) pairs slab by slab with it, which bounds the pairs one
+// round of a warp produces.  Returns false if the loop bound was reached.
+template <int N, class Sink>
+__device__ __forceinline__ bool slab_pairs(const RaySetup &rs, int j, const QuadRule &qr, Sink &sink)
 {
     constexpr float W = 0.5f * (N + 1);
     int IA, IB;
@@ -500,19 +416,15 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
     int qb = (int)floorf(fmaf(-W, rs.rb, Cb));
     // r <= 1 moves a transverse coordinate by at most N+1 over the slab, so a
     // window shifts at most N+3 times per axis (one extra for a start that
-    // rounds down); more is treated as a loop bound, which keeps every window
-    // inside [IA - N, IA + 2N + 4] (the range sinks rely on)
+    // rounds down); more is treated as a loop bound
     const int qa_lim = qa + N + 3, qb_lim = qb + N + 3;
     float na = rs.ra > 0.0f ? ((float)(qa + 1) - Ca) * rs.inv_ra : INFINITY;
     float nb = rs.rb > 0.0f ? ((float)(qb + 1) - Cb) * rs.inv_rb : INFINITY;
-    float acc[N + 1][N + 1];
+    float hit[N + 1][N + 1];  // 1 once the ray has crossed the basis' support
 #pragma unroll
     for (int i = 0; i <= N; ++i)
 #pragma unroll
-        for (int k = 0; k <= N; ++k) acc[i][k] = 0.0f;
-    // flat ray: constant b-weights, G_i kept in acc[i][0]
-    float wb[N + 1];
-    if constexpr (FLAT) bweights<N>(Cb - (float)qb, wb);
+        for (int k = 0; k <= N; ++k) hit[i][k] = 0.0f;
     float x0 = -W;
     int id = 0;  // d-piece: xi in [id - W, id + 1 - W)
 #pragma unroll 1
@@ -523,21 +435,10 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
         const float x1 = fmaxf(x1r, x0);
         const int la0 = IA + qa - N, lb0 = IB + qb - N;
         if (x1 > x0 && sink.relevant(la0, la0 + N, lb0, lb0 + N)) {
-            if constexpr (QUAD && FLAT) {
-                float G[N + 1];
 #pragma unroll
-                for (int i = 0; i <= N; ++i) G[i] = acc[i][0];
-                integrate_piece_flat<N>(x0, x1, id, Ca - (float)qa, rs.ra, qr, G);
+            for (int i = 0; i <= N; ++i)
 #pragma unroll
-                for (int i = 0; i <= N; ++i) acc[i][0] = G[i];
-            } else if constexpr (QUAD) {
-                integrate_piece<N>(x0, x1, id, Ca - (float)qa, Cb - (float)qb, rs.ra, rs.rb, qr, acc);
-            } else {
-#pragma unroll
-                for (int i = 0; i <= N; ++i)
-#pragma unroll
-                    for (int k = 0; k <= N; ++k) acc[i][k] = 1.0f;
-            }
+                for (int k = 0; k <= N; ++k) hit[i][k] = 1.0f;
             sink.piece();
         }
         x0 = x1;
@@ -546,48 +447,36 @@ __device__ __forceinline__ bool slab_sweep(const RaySetup &rs, int j, const Quad
 #pragma unroll
                 for (int i = 0; i <= N; ++i)
 #pragma unroll
-                    for (int k = 0; k <= N; ++k)
-                        sink.flush(j, la0 + i, lb0 + k, (QUAD && FLAT) ? acc[i][0] * wb[k] : acc[i][k]);
+                    for (int k = 0; k <= N; ++k) sink.flush(j, la0 + i, lb0 + k, hit[i][k]);
                 return true;
             }
         } else if (ev == 1) {
             // the lowest a-row leaves the ray's reach: flush it, shift
 #pragma unroll
-            for (int k = 0; k <= N; ++k) sink.flush(j, la0, lb0 + k, (QUAD && FLAT) ? acc[0][0] * wb[k] : acc[0][k]);
+            for (int k = 0; k <= N; ++k) sink.flush(j, la0, lb0 + k, hit[0][k]);
 #pragma unroll
             for (int i = 0; i < N; ++i)
 #pragma unroll
-                for (int k = 0; k <= N; ++k) acc[i][k] = acc[i + 1][k];
+                for (int k = 0; k <= N; ++k) hit[i][k] = hit[i + 1][k];
 #pragma unroll
-            for (int k = 0; k <= N; ++k) acc[N][k] = 0.0f;
+            for (int k = 0; k <= N; ++k) hit[N][k] = 0.0f;
             if (++qa > qa_lim) return false;
             na = ((float)(qa + 1) - Ca) * rs.inv_ra;
         } else {
             // the lowest b-column leaves
 #pragma unroll
-            for (int i = 0; i <= N; ++i) sink.flush(j, la0 + i, lb0, acc[i][0]);
+            for (int i = 0; i <= N; ++i) sink.flush(j, la0 + i, lb0, hit[i][0]);
 #pragma unroll
             for (int i = 0; i <= N; ++i) {
 #pragma unroll
-                for (int k = 0; k < N; ++k) acc[i][k] = acc[i][k + 1];
-                acc[i][N] = 0.0f;
+                for (int k = 0; k < N; ++k) hit[i][k] = hit[i][k + 1];
+                hit[i][N] = 0.0f;
             }
             if (++qb > qb_lim) return false;
             nb = ((float)(qb + 1) - Cb) * rs.inv_rb;
         }
     }
     return false;
-}
-
-// Quadrature sweep of slab j with the rule the ray needs: the flat rule when
-// the ray has a zero transverse component (r_b = 0), the full one otherwise.
-// Every kernel goes through here, so a ray gets the same footprint values in
-// the forward, the adjoint and the pair count.
-template <int N, class Sink>
-__device__ __forceinline__ bool sweep(const RaySetup &rs, int j, const QuadRule &qr, Sink &sink)
-{
-    if (rs.rb == 0.0f) return slab_sweep<N, Sink, true, true>(rs, j, qr, sink);
-    return slab_sweep<N, Sink, true, false>(rs, j, qr, sink);
 }
 
 // Region of bases a sink accepts, in the ray's mirrored (d, a, b)
@@ -732,7 +621,8 @@ __device__ __forceinline__ float window_contract(const float (&cw)[N + 1][N + 1]
 // shifts; at the end of a cell the lowest d-layer is flushed.  Each basis
 // whose support the ray crosses is flushed exactly once, through
 // sink.flush(l_d, l_a, l_b, F) with F = |w_d| Pphi(w, s - l) (the sink
-// scales by 1/|w_d|).  Compared with the slab sweep, which integrates every
+// scales by 1/|w_d|).  Compared with a march slab by slab (Algorithm 2
+// visits the bases of slab l_d = k_d at each step), which integrates every
 // point of the ray once for each of the N+1 slabs whose d-support holds it,
 // the node weights are evaluated once per point.
 //
