@@ -16,7 +16,7 @@
 
 namespace spl {
 
-constexpr int kMlpWarps = 2;
+constexpr int kMlpWarps = 4;
 constexpr int kMlpThreads = 32 * kMlpWarps;
 
 // most pairs one slab can produce: the initial (N+1)^2 window plus N+1 per
@@ -26,73 +26,89 @@ constexpr int kMlpThreads = 32 * kMlpWarps;
 // flag an error (never written out of bounds).
 template <int N> struct PairCap { static constexpr int value = (N + 1) * (N + 1) + (N + 1) * (2 * N + 6); };
 
-struct MlpWarpQueue {
-    float f3, f4;
-    int val;   // forward: coefficient (float bits); adjoint: coefficient index
-    int lane;  // lane whose ray produced the row
+// Per-lane data of the current round (one slab of each lane's ray), which
+// the rows of the queue refer to by lane.
+struct __align__(16) MlpLaneTab {
+    float wc0[32], wc1[32], wc2[32];  // canonical direction of the ray
+    float ua[32], ub[32], va[32], vb[32];
+    float fa[32], fb[32];  // A_j = IA + fa, B_j = IB + fb on the slab plane
+    int base[32];          // address of basis (j, IA - N, IB - N)
+    int S1[32], S2[32];    // mirrored strides of the ray's a and b axes
+    float yv[32];          // adjoint: the ray's datum
+    float acc[32];         // forward: the ray's sum
+    int count;
 };
 
+// A queue row names one pair in 16 bits: the lane (5 bits) and the pair's
+// basis offsets da = la - IA + N, db = lb - IB + N on the lane's slab
+// (5 bits each; every window of a slab lies in [IA - N, IA + 2N + 4], so
+// they stay below 3N + 5 <= 14).  The features and the coefficient address
+// follow from the lane's table:
+//   Pa = A_j - la = (N - da) + fa,  Pb = (N - db) + fb,
+//   features (wc, ua Pa + ub Pb, va Pa + vb Pb),
+//   address base + da S1 + db S2.
 struct MlpQueueSink {
-    MlpWarpQueue *q;
-    int *count;
+    uint16_t *q;
+    MlpLaneTab *tab;
     int cap;
-    const float *__restrict__ c;
-    int S0, S1, S2;
+    int j, S0, S1, S2;
     int loa, hia, lob, hib;
-    float ua, ub, va, vb;
     int IA, IB;
-    float fa, fb;
     int lane;
-    bool adj;
+    bool bad;  // an offset outside 5 bits (not expected; the row is dropped)
     __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ void slab(int ia, float fa_, int ib, float fb_, int)
+    __device__ __forceinline__ void slab(int ia, float fa, int ib, float fb, int n)
     {
         IA = ia;
-        fa = fa_;
         IB = ib;
-        fb = fb_;
+        tab->fa[lane] = fa;
+        tab->fb[lane] = fb;
+        tab->base[lane] = j * S0 + (ia - n) * S1 + (ib - n) * S2;
     }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
         return a1 >= loa && a0 <= hia && b1 >= lob && b0 <= hib;
     }
-    __device__ __forceinline__ void flush(int j, int la, int lb, float v)
+    template <int N> __device__ __forceinline__ void flush_n(int la, int lb, float v)
     {
         if (v > 0.0f && la >= loa && la <= hia && lb >= lob && lb <= hib) {
-            const float Pa = (float)(IA - la) + fa, Pb = (float)(IB - lb) + fb;
-            const int addr = j * S0 + la * S1 + lb * S2;
-            const int k = atomicAdd(count, 1);
-            if (k < cap) {
-                MlpWarpQueue e;
-                e.f3 = fmaf(ua, Pa, ub * Pb);
-                e.f4 = fmaf(va, Pa, vb * Pb);
-                e.val = adj ? addr : __float_as_int(__ldg(c + addr));
-                e.lane = lane;
-                q[k] = e;
+            const unsigned da = (unsigned)(la - IA + N), db = (unsigned)(lb - IB + N);
+            if (da > 31u || db > 31u) {
+                bad = true;
+                return;
             }
+            const int k = atomicAdd(&tab->count, 1);
+            if (k < cap) q[k] = (uint16_t)((unsigned)lane | (da << 5) | (db << 10));
         }
     }
 };
 
+template <int N> struct MlpSinkN : MlpQueueSink {
+    __device__ __forceinline__ void flush(int, int la, int lb, float v) { flush_n<N>(la, lb, v); }
+};
+
+template <int N> constexpr int mlp_queue_bytes() { return (32 * PairCap<N>::value * 2 + 15) / 16 * 16; }
+template <int N> constexpr size_t mlp_views_smem()
+{
+    return sizeof(MlpSmem) + (size_t)kMlpWarps * (sizeof(MlpLaneTab) + mlp_queue_bytes<N>());
+}
+
 // ADJ = false: y = A_theta c ; ADJ = true: c += A_theta^T y (c zeroed by the host)
 template <int N, bool ADJ>
-__global__ void __launch_bounds__(kMlpThreads) k_mlp_views(DevGeom g, MlpDev wts, const float *__restrict__ cin,
-                                                           float *__restrict__ yout, const float *__restrict__ yin,
-                                                           float *__restrict__ cout, QuadRule qr)
+__global__ void __launch_bounds__(kMlpThreads, 4) k_mlp_views(DevGeom g, MlpDev wts, const float *__restrict__ cin,
+                                                              float *__restrict__ yout, const float *__restrict__ yin,
+                                                              float *__restrict__ cout, QuadRule qr)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem);
     constexpr int cap = 32 * PairCap<N>::value;
-    MlpWarpQueue *queues = reinterpret_cast<MlpWarpQueue *>(smem + sizeof(MlpSmem));
-    __shared__ float wc_s[kMlpWarps][32][3];
-    __shared__ float acc_s[kMlpWarps][32];
-    __shared__ float yv_s[kMlpWarps][32];
-    __shared__ int count_s[kMlpWarps];
     mlp_load_smem(wts, S);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int g4 = lane >> 2, t4 = lane & 3;
-    MlpWarpQueue *q = queues + wid * cap;
-    const int iu = blockIdx.x * 8 + (lane & 7), iv = blockIdx.y * 8 + wid * 4 + (lane >> 3);
+    unsigned char *wbase = smem + sizeof(MlpSmem) + (size_t)wid * (sizeof(MlpLaneTab) + mlp_queue_bytes<N>());
+    MlpLaneTab &T = *reinterpret_cast<MlpLaneTab *>(wbase);
+    uint16_t *q = reinterpret_cast<uint16_t *>(wbase + sizeof(MlpLaneTab));
+    const int iu = blockIdx.x * 8 + (lane & 7), iv = blockIdx.y * (4 * kMlpWarps) + wid * 4 + (lane >> 3);
     const int k = blockIdx.z;
     const bool valid = iu < g.nu && iv < g.nv;
     const long long ray = ((long long)k * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
@@ -115,47 +131,74 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_views(DevGeom g, MlpDev wts
         rs.j1 = -1;
         mr.wc[0] = mr.wc[1] = mr.wc[2] = 0.0f;
         mr.ua = mr.ub = mr.va = mr.vb = 0.0f;
+        rs.S[0] = rs.S[1] = rs.S[2] = 0;
     }
-    wc_s[wid][lane][0] = mr.wc[0];
-    wc_s[wid][lane][1] = mr.wc[1];
-    wc_s[wid][lane][2] = mr.wc[2];
-    acc_s[wid][lane] = 0.0f;
-    yv_s[wid][lane] = yr;
-    if (lane == 0) count_s[wid] = 0;
+    T.wc0[lane] = mr.wc[0];
+    T.wc1[lane] = mr.wc[1];
+    T.wc2[lane] = mr.wc[2];
+    T.ua[lane] = mr.ua;
+    T.ub[lane] = mr.ub;
+    T.va[lane] = mr.va;
+    T.vb[lane] = mr.vb;
+    T.S1[lane] = rs.S[1];
+    T.S2[lane] = rs.S[2];
+    T.acc[lane] = 0.0f;
+    T.yv[lane] = yr;
+    if (lane == 0) T.count = 0;
     __syncthreads();  // weights in shared memory
     const int nslab = rs.j1 - rs.j0 + 1;
     const int rounds = __reduce_max_sync(0xffffffffu, nslab > 0 ? nslab : 0);
     bool ok = true;
     for (int round = 0; round < rounds; ++round) {
         if (round < nslab) {
-            MlpQueueSink sk{q, &count_s[wid], cap, cin, rs.S[0], rs.S[1], rs.S[2], rs.lo[1], rs.hi[1], rs.lo[2], rs.hi[2],
-                            mr.ua, mr.ub, mr.va, mr.vb, 0, 0, 0.0f, 0.0f, lane, ADJ};
-            ok &= slab_pairs<N, MlpQueueSink>(rs, rs.j0 + round, qr, sk);
+            MlpSinkN<N> sk;
+            sk.q = q;
+            sk.tab = &T;
+            sk.cap = cap;
+            sk.j = rs.j0 + round;
+            sk.S0 = rs.S[0];
+            sk.S1 = rs.S[1];
+            sk.S2 = rs.S[2];
+            sk.loa = rs.lo[1];
+            sk.hia = rs.hi[1];
+            sk.lob = rs.lo[2];
+            sk.hib = rs.hi[2];
+            sk.IA = sk.IB = 0;
+            sk.lane = lane;
+            sk.bad = false;
+            ok &= slab_pairs<N, MlpSinkN<N>>(rs, sk.j, qr, sk);
+            ok &= !sk.bad;
         }
         __syncwarp();
-        int n = count_s[wid];
+        int n = T.count;
         if (n > cap) {
             ok = false;
             n = cap;
         }
         for (int base = 0; base < n; base += 16) {
             float x[2][5];
-            MlpWarpQueue e[2];
+            int ln[2], addr[2];
+            float cv[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = base + g4 + 8 * h;
-                if (r < n) {
-                    e[h] = q[r];
-                    const int ln = e[h].lane;
-                    x[h][0] = wc_s[wid][ln][0];
-                    x[h][1] = wc_s[wid][ln][1];
-                    x[h][2] = wc_s[wid][ln][2];
-                    x[h][3] = e[h].f3;
-                    x[h][4] = e[h].f4;
-                } else {
-                    e[h].lane = -1;
+                ln[h] = -1;
+                cv[h] = 0.0f;
+                addr[h] = 0;
 #pragma unroll
-                    for (int i = 0; i < 5; ++i) x[h][i] = 0.0f;
+                for (int i = 0; i < 5; ++i) x[h][i] = 0.0f;
+                if (r < n) {
+                    const unsigned e = q[r];
+                    const int l = (int)(e & 31u), da = (int)((e >> 5) & 31u), db = (int)(e >> 10);
+                    const float Pa = (float)(N - da) + T.fa[l], Pb = (float)(N - db) + T.fb[l];
+                    ln[h] = l;
+                    addr[h] = T.base[l] + da * T.S1[l] + db * T.S2[l];
+                    if (!ADJ) cv[h] = __ldg(cin + addr[h]);
+                    x[h][0] = T.wc0[l];
+                    x[h][1] = T.wc1[l];
+                    x[h][2] = T.wc2[l];
+                    x[h][3] = fmaf(T.ua[l], Pa, T.ub[l] * Pb);
+                    x[h][4] = fmaf(T.va[l], Pa, T.vb[l] * Pb);
                 }
             }
             float o[2];
@@ -163,25 +206,22 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_views(DevGeom g, MlpDev wts
             if (t4 == 0) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    if (e[h].lane < 0) continue;
-                    const int ln = e[h].lane;
-                    if (ADJ) atomicAdd(cout + e[h].val, yv_s[wid][ln] * o[h]);
-                    else atomicAdd(&acc_s[wid][ln], __int_as_float(e[h].val) * o[h]);
+                    if (ln[h] < 0) continue;
+                    if (ADJ) atomicAdd(cout + addr[h], T.yv[ln[h]] * o[h]);
+                    else atomicAdd(&T.acc[ln[h]], cv[h] * o[h]);
                 }
             }
         }
         __syncwarp();
-        if (lane == 0) count_s[wid] = 0;
+        if (lane == 0) T.count = 0;
         __syncwarp();
     }
     if (!ok) atomicOr(g.err, 1);
     if (!ADJ && valid) {
         __syncwarp();
-        yout[ray] = acc_s[wid][lane];
+        yout[ray] = T.acc[lane];
     }
 }
-
-template <int N> constexpr size_t mlp_views_smem() { return sizeof(MlpSmem) + (size_t)kMlpWarps * 32 * PairCap<N>::value * sizeof(MlpWarpQueue); }
 
 template <int N, bool ADJ>
 static spl_status launch_mlp_views(const spl_geometry *g, const spl_mlp *m, const float *cin, float *yout,
@@ -198,7 +238,7 @@ static spl_status launch_mlp_views(const spl_geometry *g, const spl_mlp *m, cons
         if (s != SPL_OK) return s;
         attr_done = true;
     }
-    dim3 grid((dg.nu + 7) / 8, (dg.nv + 7) / 8, dg.n_views);
+    dim3 grid((dg.nu + 7) / 8, (dg.nv + 4 * kMlpWarps - 1) / (4 * kMlpWarps), dg.n_views);
     k_mlp_views<N, ADJ><<<grid, kMlpThreads, sm, st>>>(dg, mlp_dev(m), cin, yout, yin, cout, quad_rule(N));
     return cuda_check(cudaGetLastError(), "mlp projector launch");
 }
