@@ -17,6 +17,9 @@
 namespace spl {
 
 constexpr int kMlpWarps = 4;
+#ifndef SPL_MLP_MIN_BLOCKS
+#define SPL_MLP_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
+#endif
 constexpr int kMlpThreads = 32 * kMlpWarps;
 
 // most pairs one slab can produce: the initial (N+1)^2 window plus N+1 per
@@ -87,6 +90,17 @@ template <int N> struct MlpSinkN : MlpQueueSink {
     __device__ __forceinline__ void flush(int, int la, int lb, float v) { flush_n<N>(la, lb, v); }
 };
 
+// Lane, coefficient address and (Pa, Pb) of queue row e.
+template <int N>
+__device__ __forceinline__ void decode_row(const MlpLaneTab &T, unsigned e, int &l, int &addr, float &Pa, float &Pb)
+{
+    l = (int)(e & 31u);
+    const int da = (int)((e >> 5) & 31u), db = (int)(e >> 10);
+    addr = T.base[l] + da * T.S1[l] + db * T.S2[l];
+    Pa = (float)(N - da) + T.fa[l];
+    Pb = (float)(N - db) + T.fb[l];
+}
+
 template <int N> constexpr int mlp_queue_bytes() { return (32 * PairCap<N>::value * 2 + 15) / 16 * 16; }
 template <int N> constexpr size_t mlp_views_smem()
 {
@@ -95,7 +109,7 @@ template <int N> constexpr size_t mlp_views_smem()
 
 // ADJ = false: y = A_theta c ; ADJ = true: c += A_theta^T y (c zeroed by the host)
 template <int N, bool ADJ>
-__global__ void __launch_bounds__(kMlpThreads, 4) k_mlp_views(DevGeom g, MlpDev wts, const float *__restrict__ cin,
+__global__ void __launch_bounds__(kMlpThreads, SPL_MLP_MIN_BLOCKS) k_mlp_views(DevGeom g, MlpDev wts, const float *__restrict__ cin,
                                                               float *__restrict__ yout, const float *__restrict__ yin,
                                                               float *__restrict__ cout, QuadRule qr)
 {
@@ -177,23 +191,18 @@ __global__ void __launch_bounds__(kMlpThreads, 4) k_mlp_views(DevGeom g, MlpDev 
         }
         for (int base = 0; base < n; base += 16) {
             float x[2][5];
-            int ln[2], addr[2];
             float cv[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = base + g4 + 8 * h;
-                ln[h] = -1;
                 cv[h] = 0.0f;
-                addr[h] = 0;
 #pragma unroll
                 for (int i = 0; i < 5; ++i) x[h][i] = 0.0f;
                 if (r < n) {
-                    const unsigned e = q[r];
-                    const int l = (int)(e & 31u), da = (int)((e >> 5) & 31u), db = (int)(e >> 10);
-                    const float Pa = (float)(N - da) + T.fa[l], Pb = (float)(N - db) + T.fb[l];
-                    ln[h] = l;
-                    addr[h] = T.base[l] + da * T.S1[l] + db * T.S2[l];
-                    if (!ADJ) cv[h] = __ldg(cin + addr[h]);
+                    int l, addr;
+                    float Pa, Pb;
+                    decode_row<N>(T, q[r], l, addr, Pa, Pb);
+                    if (!ADJ) cv[h] = __ldg(cin + addr);
                     x[h][0] = T.wc0[l];
                     x[h][1] = T.wc1[l];
                     x[h][2] = T.wc2[l];
@@ -206,9 +215,13 @@ __global__ void __launch_bounds__(kMlpThreads, 4) k_mlp_views(DevGeom g, MlpDev 
             if (t4 == 0) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    if (ln[h] < 0) continue;
-                    if (ADJ) atomicAdd(cout + addr[h], T.yv[ln[h]] * o[h]);
-                    else atomicAdd(&T.acc[ln[h]], cv[h] * o[h]);
+                    const int r = base + g4 + 8 * h;
+                    if (r >= n) continue;
+                    int l, addr;
+                    float Pa, Pb;
+                    decode_row<N>(T, q[r], l, addr, Pa, Pb);
+                    if (ADJ) atomicAdd(cout + addr, T.yv[l] * o[h]);
+                    else atomicAdd(&T.acc[l], cv[h] * o[h]);
                 }
             }
         }
