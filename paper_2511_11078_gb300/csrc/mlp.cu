@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include "spl_mlp.cuh"
+#include "spl_tc.cuh"
 
 namespace spl {
 
@@ -97,99 +98,90 @@ static spl_status prep(spl_mlp *m, cudaStream_t st)
 // FROM_WP: rows given as (omega, p) -> canonical features and the exact
 // support mask of the basis at the origin; otherwise rows are features.
 template <bool FROM_WP>
-__global__ void __launch_bounds__(kEvalThreads) k_mlp_rows(MlpDev w, int degree, long long count,
-                                                           const float *__restrict__ a, const float *__restrict__ b,
-                                                           float *__restrict__ out)
+__global__ void __launch_bounds__(kTcRows) k_mlp_rows(MlpDev w, int degree, long long count,
+                                                      const float *__restrict__ a, const float *__restrict__ b,
+                                                      float *__restrict__ out)
 {
-    __shared__ MlpSmem S;
-    mlp_load_smem(w, S);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const long long warps = (long long)gridDim.x * (kEvalThreads / 32);
-    const long long wid = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
-    const long long tiles = (count + 15) / 16;
-    for (long long tile = wid; tile < tiles; tile += warps) {
-        float x[2][5];
-        float mask[2] = {1.0f, 1.0f};
-        // FROM_WP: lane t = 0 of a quad prepares row g, lane t = 1 row g + 8
-        // (FP64 work once per row), then the quad shares them by shuffles
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlpSmem &S = *reinterpret_cast<TcMlpSmem *>(tc_smem);
+    tc_mlp_setup(w, S);
+    unsigned phase = 0;
+    const long long tiles = (count + kTcRows - 1) / kTcRows;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const long long r = tile * kTcRows + threadIdx.x;
+        float x[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        float mask = 0.0f;
+        if (r < count) {
+            mask = 1.0f;
+            if (FROM_WP) {
+                float wv[3], pv[3];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long long r = tile * 16 + g + 8 * h;
-            if (FROM_WP && t != h) {
-#pragma unroll
-                for (int e = 0; e < 5; ++e) x[h][e] = 0.0f;
-                mask[h] = 0.0f;
-            } else if (r < count) {
-                if (FROM_WP) {
-                    float wv[3], pv[3];
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        wv[e] = a[3 * r + e];
-                        pv[e] = b[3 * r + e];
-                    }
-                    const float inrm = rsqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) wv[e] *= inrm;
-                    canonical_features_f32(degree, wv, pv, x[h]);
-                    // exact support: the line p + t w meets the open cube
-                    // [-W, W]^3 in a segment of positive length
-                    const float W = 0.5f * (degree + 1);
-                    float lo = -INFINITY, hi = INFINITY;
-                    bool in = true;
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        if (wv[e] == 0.0f) {
-                            in = in && (pv[e] >= -W && pv[e] < W) && (degree == 0 || pv[e] > -W);
-                        } else {
-                            const float iw = 1.0f / wv[e];
-                            const float t1 = (-W - pv[e]) * iw, t2 = (W - pv[e]) * iw;
-                            lo = fmaxf(lo, fminf(t1, t2));
-                            hi = fminf(hi, fmaxf(t1, t2));
-                        }
-                    }
-                    mask[h] = (in && hi > lo) ? 1.0f : 0.0f;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 5; ++e) x[h][e] = a[5 * r + e];
+                for (int e = 0; e < 3; ++e) {
+                    wv[e] = a[3 * r + e];
+                    pv[e] = b[3 * r + e];
                 }
+                const float inrm = rsqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) wv[e] *= inrm;
+                canonical_features_f32(degree, wv, pv, x);
+                // exact support: the line p + t w meets the open cube
+                // [-W, W]^3 in a segment of positive length
+                const float W = 0.5f * (degree + 1);
+                float lo = -INFINITY, hi = INFINITY;
+                bool in = true;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    if (wv[e] == 0.0f) {
+                        in = in && (pv[e] >= -W && pv[e] < W) && (degree == 0 || pv[e] > -W);
+                    } else {
+                        const float iw = 1.0f / wv[e];
+                        const float t1 = (-W - pv[e]) * iw, t2 = (W - pv[e]) * iw;
+                        lo = fmaxf(lo, fminf(t1, t2));
+                        hi = fminf(hi, fmaxf(t1, t2));
+                    }
+                }
+                mask = (in && hi > lo) ? 1.0f : 0.0f;
             } else {
 #pragma unroll
-                for (int e = 0; e < 5; ++e) x[h][e] = 0.0f;
-                mask[h] = 0.0f;
+                for (int e = 0; e < 5; ++e) x[e] = a[5 * r + e];
             }
         }
-        if (FROM_WP) {
-            const int src0 = lane & ~3, src1 = src0 + 1;
-#pragma unroll
-            for (int e = 0; e < 5; ++e) {
-                x[0][e] = __shfl_sync(0xffffffffu, x[0][e], src0);
-                x[1][e] = __shfl_sync(0xffffffffu, x[1][e], src1);
-            }
-            mask[0] = __shfl_sync(0xffffffffu, mask[0], src0);
-            mask[1] = __shfl_sync(0xffffffffu, mask[1], src1);
-        }
-        float o0, o1;
-        mlp_tile16<false>(S, x[0], x[1], o0, o1);
-        if (t == 0) {
-            const long long r0 = tile * 16 + g, r1 = r0 + 8;
-            if (r0 < count) out[r0] = o0 * mask[0];
-            if (r1 < count) out[r1] = o1 * mask[1];
-        }
+        float o;
+        const bool ok = tc_mlp_tile(S, x, o, phase);
+        // a tensor-core wait that gave up (not expected) leaves NaN in the
+        // rows of the tile and stops the CTA
+        const bool bad = __syncthreads_or(!ok);
+        if (r < count) out[r] = bad ? __int_as_float(0x7FC00000) : o * mask;
+        if (bad) break;
     }
+    tc_mlp_teardown(S);
 }
 
 static unsigned eval_blocks(long long count)
 {
-    const long long tiles = (count + 15) / 16;
-    const long long blocks = (tiles + 3) / 4;
-    return (unsigned)(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16);
+    const long long tiles = (count + kTcRows - 1) / kTcRows;
+    return (unsigned)(tiles < 152 * 4 ? (tiles > 0 ? tiles : 1) : 152 * 4);
+}
+
+// dynamic shared memory of the tcgen05 row kernels (set once per process)
+template <bool FROM_WP> static spl_status rows_smem_attr()
+{
+    static bool done = false;
+    if (done) return SPL_OK;
+    spl_status s = cuda_check(cudaFuncSetAttribute(k_mlp_rows<FROM_WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(TcMlpSmem)),
+                              "mlp rows smem attribute");
+    if (s == SPL_OK) done = true;
+    return s;
 }
 
 spl_status footprint_mlp(const spl_basis_desc *b, long long count, const float *w, const float *p, float *out,
                          cudaStream_t st)
 {
-    k_mlp_rows<true><<<eval_blocks(count), kEvalThreads, 0, st>>>(mlp_dev(b->mlp), b->degree, count, w, p, out);
+    spl_status s = rows_smem_attr<true>();
+    if (s != SPL_OK) return s;
+    k_mlp_rows<true><<<eval_blocks(count), kTcRows, sizeof(TcMlpSmem), st>>>(mlp_dev(b->mlp), b->degree, count, w, p,
+                                                                             out);
     return cuda_check(cudaGetLastError(), "mlp footprint launch");
 }
 
@@ -546,8 +538,10 @@ extern "C" spl_status spl_mlp_eval(const spl_mlp *m, long long count, const floa
     if (count < 0) return fail(SPL_ERR_ARG, "bad count");
     if (count == 0) return SPL_OK;
     if (!feat_dev || !out_dev) return fail(SPL_ERR_ARG, "NULL array");
-    k_mlp_rows<false><<<eval_blocks(count), kEvalThreads, 0, (cudaStream_t)stream>>>(mlp_dev(m), m->degree, count,
-                                                                                      feat_dev, nullptr, out_dev);
+    spl_status s = rows_smem_attr<false>();
+    if (s != SPL_OK) return s;
+    k_mlp_rows<false><<<eval_blocks(count), kTcRows, sizeof(TcMlpSmem), (cudaStream_t)stream>>>(
+        mlp_dev(m), m->degree, count, feat_dev, nullptr, out_dev);
     return cuda_check(cudaGetLastError(), "mlp eval launch");
 }
 
