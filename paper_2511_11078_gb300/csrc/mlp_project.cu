@@ -1,26 +1,21 @@
 // mlp_project.cu -- forward projection and adjoint with the learned
 // footprint f_theta in place of the exact one (Algorithm 2 with f_theta*).
 //
-// A warp owns 32 rays (an 8 x 4 detector sub-tile).  The warp walks the
-// rays' slabs in lock-step rounds: in each round every lane sweeps one slab
-// of its ray in pair-enumeration mode (the same dominant-axis slab march and
-// window as the exact path, so the pair set is the exact support of every
-// basis -- f_theta is kept only where the ray meets the basis), and appends
-// one row per pair to a per-warp queue in shared memory: the two ray-
-// dependent features (the canonical direction is per ray) and the
-// coefficient (forward) or its address (adjoint).  The warp then drains the
-// queue in 16-row tiles through the BF16 tensor-core MLP and accumulates
-// c * f_theta per ray (forward) or y_r * f_theta per coefficient with float
-// atomics (adjoint).
-#include "spl_mlp.cuh"
+// A CTA owns 128 rays (an 8 x 16 detector tile).  It walks the rays' slabs
+// in lock-step rounds: in each round every thread sweeps one slab of its ray
+// in pair-enumeration mode (the same dominant-axis slab march and window as
+// the exact path, so the pair set is the exact support of every basis --
+// f_theta is kept only where the ray meets the basis) and appends one 16-bit
+// row per pair to the CTA's queue in shared memory.  The CTA then drains the
+// queue in tiles of 128 rows through the tcgen05 network (one row per
+// thread, accumulator in TMEM) and accumulates c * f_theta per ray (forward,
+// shared-memory atomics) or y_r * f_theta per coefficient (adjoint, float
+// atomics in global memory).
+#include "spl_tc.cuh"
 
 namespace spl {
 
-constexpr int kMlpWarps = 4;
-#ifndef SPL_MLP_MIN_BLOCKS
-#define SPL_MLP_MIN_BLOCKS 4  // resident blocks per SM the register budget is sized for
-#endif
-constexpr int kMlpThreads = 32 * kMlpWarps;
+constexpr int kMlpThreads = kTcRows;
 
 // most pairs one slab can produce: the initial (N+1)^2 window plus N+1 per
 // window shift; a transverse axis crosses at most N+2 knot planes in a slab
@@ -29,44 +24,45 @@ constexpr int kMlpThreads = 32 * kMlpWarps;
 // flag an error (never written out of bounds).
 template <int N> struct PairCap { static constexpr int value = (N + 1) * (N + 1) + (N + 1) * (2 * N + 6); };
 
-// Per-lane data of the current round (one slab of each lane's ray), which
-// the rows of the queue refer to by lane.
-struct __align__(16) MlpLaneTab {
-    float wc0[32], wc1[32], wc2[32];  // canonical direction of the ray
-    float ua[32], ub[32], va[32], vb[32];
-    float fa[32], fb[32];  // A_j = IA + fa, B_j = IB + fb on the slab plane
-    int base[32];          // address of basis (j, IA - N, IB - N)
-    int S1[32], S2[32];    // mirrored strides of the ray's a and b axes
-    float yv[32];          // adjoint: the ray's datum
-    float acc[32];         // forward: the ray's sum
-    int count;
+// Per-ray data of the current round (one slab of each thread's ray), which
+// the rows of the queue refer to by ray.
+struct __align__(16) MlpRayTab {
+    float wc0[kMlpThreads], wc1[kMlpThreads], wc2[kMlpThreads];  // canonical direction
+    float ua[kMlpThreads], ub[kMlpThreads], va[kMlpThreads], vb[kMlpThreads];
+    float fa[kMlpThreads], fb[kMlpThreads];  // A_j = IA + fa, B_j = IB + fb on the slab plane
+    int base[kMlpThreads];                   // address of basis (j, IA - N, IB - N)
+    int S1[kMlpThreads], S2[kMlpThreads];    // mirrored strides of the ray's a and b axes
+    float yv[kMlpThreads];                   // adjoint: the ray's datum
+    float acc[kMlpThreads];                  // forward: the ray's sum
+    int count;                               // rows in the queue
+    int rounds;                              // slabs of the longest ray of the CTA
 };
 
-// A queue row names one pair in 16 bits: the lane (5 bits) and the pair's
-// basis offsets da = la - IA + N, db = lb - IB + N on the lane's slab
-// (5 bits each; every window of a slab lies in [IA - N, IA + 2N + 4], so
+// A queue row names one pair in 15 bits: the ray (7 bits) and the pair's
+// basis offsets da = la - IA + N, db = lb - IB + N on the ray's slab
+// (4 bits each; every window of a slab lies in [IA - N, IA + 2N + 4], so
 // they stay below 3N + 5 <= 14).  The features and the coefficient address
-// follow from the lane's table:
+// follow from the ray's table entry:
 //   Pa = A_j - la = (N - da) + fa,  Pb = (N - db) + fb,
 //   features (wc, ua Pa + ub Pb, va Pa + vb Pb),
 //   address base + da S1 + db S2.
 struct MlpQueueSink {
     uint16_t *q;
-    MlpLaneTab *tab;
+    MlpRayTab *tab;
     int cap;
     int j, S0, S1, S2;
     int loa, hia, lob, hib;
     int IA, IB;
-    int lane;
-    bool bad;  // an offset outside 5 bits (not expected; the row is dropped)
+    int ray;
+    bool bad;  // an offset outside 4 bits (not expected; the row is dropped)
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ void slab(int ia, float fa, int ib, float fb, int n)
     {
         IA = ia;
         IB = ib;
-        tab->fa[lane] = fa;
-        tab->fb[lane] = fb;
-        tab->base[lane] = j * S0 + (ia - n) * S1 + (ib - n) * S2;
+        tab->fa[ray] = fa;
+        tab->fb[ray] = fb;
+        tab->base[ray] = j * S0 + (ia - n) * S1 + (ib - n) * S2;
     }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
@@ -76,12 +72,12 @@ struct MlpQueueSink {
     {
         if (v > 0.0f && la >= loa && la <= hia && lb >= lob && lb <= hib) {
             const unsigned da = (unsigned)(la - IA + N), db = (unsigned)(lb - IB + N);
-            if (da > 31u || db > 31u) {
+            if (da > 15u || db > 15u) {
                 bad = true;
                 return;
             }
             const int k = atomicAdd(&tab->count, 1);
-            if (k < cap) q[k] = (uint16_t)((unsigned)lane | (da << 5) | (db << 10));
+            if (k < cap) q[k] = (uint16_t)((unsigned)ray | (da << 7) | (db << 11));
         }
     }
 };
@@ -90,39 +86,41 @@ template <int N> struct MlpSinkN : MlpQueueSink {
     __device__ __forceinline__ void flush(int, int la, int lb, float v) { flush_n<N>(la, lb, v); }
 };
 
-// Lane, coefficient address and (Pa, Pb) of queue row e.
+// Ray, coefficient address and (Pa, Pb) of queue row e.
 template <int N>
-__device__ __forceinline__ void decode_row(const MlpLaneTab &T, unsigned e, int &l, int &addr, float &Pa, float &Pb)
+__device__ __forceinline__ void decode_row(const MlpRayTab &T, unsigned e, int &l, int &addr, float &Pa, float &Pb)
 {
-    l = (int)(e & 31u);
-    const int da = (int)((e >> 5) & 31u), db = (int)(e >> 10);
+    l = (int)(e & 127u);
+    const int da = (int)((e >> 7) & 15u), db = (int)(e >> 11);
     addr = T.base[l] + da * T.S1[l] + db * T.S2[l];
     Pa = (float)(N - da) + T.fa[l];
     Pb = (float)(N - db) + T.fb[l];
 }
 
-template <int N> constexpr int mlp_queue_bytes() { return (32 * PairCap<N>::value * 2 + 15) / 16 * 16; }
+template <int N> constexpr int mlp_queue_bytes() { return (kMlpThreads * PairCap<N>::value * 2 + 15) / 16 * 16; }
 template <int N> constexpr size_t mlp_views_smem()
 {
-    return sizeof(MlpSmem) + (size_t)kMlpWarps * (sizeof(MlpLaneTab) + mlp_queue_bytes<N>());
+    return sizeof(TcMlpSmem) + sizeof(MlpRayTab) + (size_t)mlp_queue_bytes<N>();
 }
 
 // ADJ = false: y = A_theta c ; ADJ = true: c += A_theta^T y (c zeroed by the host)
 template <int N, bool ADJ>
-__global__ void __launch_bounds__(kMlpThreads, SPL_MLP_MIN_BLOCKS) k_mlp_views(DevGeom g, MlpDev wts, const float *__restrict__ cin,
-                                                              float *__restrict__ yout, const float *__restrict__ yin,
-                                                              float *__restrict__ cout, QuadRule qr)
+__global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_views(DevGeom g, MlpDev wts, const float *__restrict__ cin,
+                                                           float *__restrict__ yout, const float *__restrict__ yin,
+                                                           float *__restrict__ cout, QuadRule qr)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem);
-    constexpr int cap = 32 * PairCap<N>::value;
-    mlp_load_smem(wts, S);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int g4 = lane >> 2, t4 = lane & 3;
-    unsigned char *wbase = smem + sizeof(MlpSmem) + (size_t)wid * (sizeof(MlpLaneTab) + mlp_queue_bytes<N>());
-    MlpLaneTab &T = *reinterpret_cast<MlpLaneTab *>(wbase);
-    uint16_t *q = reinterpret_cast<uint16_t *>(wbase + sizeof(MlpLaneTab));
-    const int iu = blockIdx.x * 8 + (lane & 7), iv = blockIdx.y * (4 * kMlpWarps) + wid * 4 + (lane >> 3);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    TcMlpSmem &S = *reinterpret_cast<TcMlpSmem *>(smem);
+    MlpRayTab &T = *reinterpret_cast<MlpRayTab *>(smem + sizeof(TcMlpSmem));
+    uint16_t *q = reinterpret_cast<uint16_t *>(smem + sizeof(TcMlpSmem) + sizeof(MlpRayTab));
+    constexpr int cap = kMlpThreads * PairCap<N>::value;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        T.count = 0;
+        T.rounds = 0;
+    }
+    tc_mlp_setup(wts, S);  // ends with a CTA barrier
+    const int iu = blockIdx.x * 8 + (lane & 7), iv = blockIdx.y * 16 + wid * 4 + (lane >> 3);
     const int k = blockIdx.z;
     const bool valid = iu < g.nu && iv < g.nv;
     const long long ray = ((long long)k * g.nv + (valid ? iv : 0)) * g.nu + (valid ? iu : 0);
@@ -147,23 +145,24 @@ __global__ void __launch_bounds__(kMlpThreads, SPL_MLP_MIN_BLOCKS) k_mlp_views(D
         mr.ua = mr.ub = mr.va = mr.vb = 0.0f;
         rs.S[0] = rs.S[1] = rs.S[2] = 0;
     }
-    T.wc0[lane] = mr.wc[0];
-    T.wc1[lane] = mr.wc[1];
-    T.wc2[lane] = mr.wc[2];
-    T.ua[lane] = mr.ua;
-    T.ub[lane] = mr.ub;
-    T.va[lane] = mr.va;
-    T.vb[lane] = mr.vb;
-    T.S1[lane] = rs.S[1];
-    T.S2[lane] = rs.S[2];
-    T.acc[lane] = 0.0f;
-    T.yv[lane] = yr;
-    if (lane == 0) T.count = 0;
-    __syncthreads();  // weights in shared memory
+    T.wc0[tid] = mr.wc[0];
+    T.wc1[tid] = mr.wc[1];
+    T.wc2[tid] = mr.wc[2];
+    T.ua[tid] = mr.ua;
+    T.ub[tid] = mr.ub;
+    T.va[tid] = mr.va;
+    T.vb[tid] = mr.vb;
+    T.S1[tid] = rs.S[1];
+    T.S2[tid] = rs.S[2];
+    T.acc[tid] = 0.0f;
+    T.yv[tid] = yr;
     const int nslab = rs.j1 - rs.j0 + 1;
-    const int rounds = __reduce_max_sync(0xffffffffu, nslab > 0 ? nslab : 0);
-    bool ok = true;
-    for (int round = 0; round < rounds; ++round) {
+    if (nslab > 0) atomicMax(&T.rounds, nslab);
+    __syncthreads();
+    const int rounds = T.rounds;
+    unsigned phase = 0;
+    bool ok = true, stop = false;
+    for (int round = 0; round < rounds && !stop; ++round) {
         if (round < nslab) {
             MlpSinkN<N> sk;
             sk.q = q;
@@ -178,62 +177,51 @@ __global__ void __launch_bounds__(kMlpThreads, SPL_MLP_MIN_BLOCKS) k_mlp_views(D
             sk.lob = rs.lo[2];
             sk.hib = rs.hi[2];
             sk.IA = sk.IB = 0;
-            sk.lane = lane;
+            sk.ray = tid;
             sk.bad = false;
             ok &= slab_pairs<N, MlpSinkN<N>>(rs, sk.j, qr, sk);
             ok &= !sk.bad;
         }
-        __syncwarp();
+        __syncthreads();
         int n = T.count;
         if (n > cap) {
             ok = false;
             n = cap;
         }
-        for (int base = 0; base < n; base += 16) {
-            float x[2][5];
-            float cv[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = base + g4 + 8 * h;
-                cv[h] = 0.0f;
-#pragma unroll
-                for (int i = 0; i < 5; ++i) x[h][i] = 0.0f;
-                if (r < n) {
-                    int l, addr;
-                    float Pa, Pb;
-                    decode_row<N>(T, q[r], l, addr, Pa, Pb);
-                    if (!ADJ) cv[h] = __ldg(cin + addr);
-                    x[h][0] = T.wc0[l];
-                    x[h][1] = T.wc1[l];
-                    x[h][2] = T.wc2[l];
-                    x[h][3] = fmaf(T.ua[l], Pa, T.ub[l] * Pb);
-                    x[h][4] = fmaf(T.va[l], Pa, T.vb[l] * Pb);
-                }
+        for (int base = 0; base < n; base += kMlpThreads) {
+            const int r = base + tid;
+            float x[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            float cv = 0.0f;
+            int l = 0, addr = 0;
+            if (r < n) {
+                float Pa, Pb;
+                decode_row<N>(T, q[r], l, addr, Pa, Pb);
+                if (!ADJ) cv = __ldg(cin + addr);
+                x[0] = T.wc0[l];
+                x[1] = T.wc1[l];
+                x[2] = T.wc2[l];
+                x[3] = fmaf(T.ua[l], Pa, T.ub[l] * Pb);
+                x[4] = fmaf(T.va[l], Pa, T.vb[l] * Pb);
             }
-            float o[2];
-            mlp_tile16<false>(S, x[0], x[1], o[0], o[1]);
-            if (t4 == 0) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int r = base + g4 + 8 * h;
-                    if (r >= n) continue;
-                    int l, addr;
-                    float Pa, Pb;
-                    decode_row<N>(T, q[r], l, addr, Pa, Pb);
-                    if (ADJ) atomicAdd(cout + addr, T.yv[l] * o[h]);
-                    else atomicAdd(&T.acc[l], cv[h] * o[h]);
-                }
+            float o;
+            const bool tok = tc_mlp_tile(S, x, o, phase);
+            if (__syncthreads_or(!tok)) {  // a tensor-core wait gave up (not expected)
+                ok = false;
+                stop = true;
+                break;
+            }
+            if (r < n) {
+                if (ADJ) atomicAdd(cout + addr, T.yv[l] * o);
+                else atomicAdd(&T.acc[l], cv * o);
             }
         }
-        __syncwarp();
-        if (lane == 0) T.count = 0;
-        __syncwarp();
+        __syncthreads();  // queue drained
+        if (tid == 0) T.count = 0;
+        __syncthreads();
     }
     if (!ok) atomicOr(g.err, 1);
-    if (!ADJ && valid) {
-        __syncwarp();
-        yout[ray] = T.acc[lane];
-    }
+    if (!ADJ && valid) yout[ray] = T.acc[tid];
+    tc_mlp_teardown(S);
 }
 
 template <int N, bool ADJ>
@@ -251,7 +239,7 @@ static spl_status launch_mlp_views(const spl_geometry *g, const spl_mlp *m, cons
         if (s != SPL_OK) return s;
         attr_done = true;
     }
-    dim3 grid((dg.nu + 7) / 8, (dg.nv + 4 * kMlpWarps - 1) / (4 * kMlpWarps), dg.n_views);
+    dim3 grid((dg.nu + 7) / 8, (dg.nv + 15) / 16, dg.n_views);
     k_mlp_views<N, ADJ><<<grid, kMlpThreads, sm, st>>>(dg, mlp_dev(m), cin, yout, yin, cout, quad_rule(N));
     return cuda_check(cudaGetLastError(), "mlp projector launch");
 }
