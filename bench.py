@@ -294,7 +294,7 @@ def mlp_measure(args, wl, geom, c_true, y, pairs, proj, dev):
     a_ms, at_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     proj.adjoint(y, out=cq)
     torch.cuda.synchronize()
-    return {"footprint": "f_theta 5-64-64-64-1 SiLU, BF16 weights/activations, FP32 accumulation (mma.sync)",
+    return {"footprint": "f_theta 5-64-64-64-1 SiLU, BF16 weights/activations, FP32 accumulation (tcgen05, accumulator in TMEM)",
             "A_ms": a_ms, "AT_ms": at_ms, "A_gcontrib_s": pairs / a_ms / 1e6, "AT_gcontrib_s": pairs / at_ms / 1e6,
             "s_per_recon_iter_est": (a_ms + at_ms) / 1e3,
             "tensor_tflops_A": pairs * MLP_FLOP_PER_PAIR / a_ms / 1e9,

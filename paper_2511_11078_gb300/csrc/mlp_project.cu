@@ -26,16 +26,18 @@ template <int N> struct PairCap { static constexpr int value = (N + 1) * (N + 1)
 
 // Per-ray data of the current round (one slab of each thread's ray), which
 // the rows of the queue refer to by ray.
+struct __align__(16) MlpRayRec {
+    float4 a;  // canonical direction wc0, wc1, wc2; ua
+    float4 b;  // ub, va, vb; fa (A_j = IA + fa on the slab plane)
+    int4 c;    // fb (float bits; B_j = IB + fb); address of basis (j, IA - N, IB - N);
+               // mirrored strides S1, S2 of the ray's a and b axes
+};
 struct __align__(16) MlpRayTab {
-    float wc0[kMlpThreads], wc1[kMlpThreads], wc2[kMlpThreads];  // canonical direction
-    float ua[kMlpThreads], ub[kMlpThreads], va[kMlpThreads], vb[kMlpThreads];
-    float fa[kMlpThreads], fb[kMlpThreads];  // A_j = IA + fa, B_j = IB + fb on the slab plane
-    int base[kMlpThreads];                   // address of basis (j, IA - N, IB - N)
-    int S1[kMlpThreads], S2[kMlpThreads];    // mirrored strides of the ray's a and b axes
-    float yv[kMlpThreads];                   // adjoint: the ray's datum
-    float acc[kMlpThreads];                  // forward: the ray's sum
-    int count;                               // rows in the queue
-    int rounds;                              // slabs of the longest ray of the CTA
+    MlpRayRec rec[kMlpThreads];
+    float yv[kMlpThreads];   // adjoint: the ray's datum
+    float acc[kMlpThreads];  // forward: the ray's sum
+    int count;               // rows in the queue
+    int rounds;              // slabs of the longest ray of the CTA
 };
 
 // A queue row names one pair in 15 bits: the ray (7 bits) and the pair's
@@ -60,9 +62,9 @@ struct MlpQueueSink {
     {
         IA = ia;
         IB = ib;
-        tab->fa[ray] = fa;
-        tab->fb[ray] = fb;
-        tab->base[ray] = j * S0 + (ia - n) * S1 + (ib - n) * S2;
+        tab->rec[ray].b.w = fa;
+        tab->rec[ray].c.x = __float_as_int(fb);
+        tab->rec[ray].c.y = j * S0 + (ia - n) * S1 + (ib - n) * S2;
     }
     __device__ __forceinline__ bool relevant(int a0, int a1, int b0, int b1) const
     {
@@ -86,15 +88,21 @@ template <int N> struct MlpSinkN : MlpQueueSink {
     __device__ __forceinline__ void flush(int, int la, int lb, float v) { flush_n<N>(la, lb, v); }
 };
 
-// Ray, coefficient address and (Pa, Pb) of queue row e.
+// Ray, coefficient address and features of queue row e.
 template <int N>
-__device__ __forceinline__ void decode_row(const MlpRayTab &T, unsigned e, int &l, int &addr, float &Pa, float &Pb)
+__device__ __forceinline__ void decode_row(const MlpRayTab &T, unsigned e, int &l, int &addr, float (&x)[5])
 {
     l = (int)(e & 127u);
     const int da = (int)((e >> 7) & 15u), db = (int)(e >> 11);
-    addr = T.base[l] + da * T.S1[l] + db * T.S2[l];
-    Pa = (float)(N - da) + T.fa[l];
-    Pb = (float)(N - db) + T.fb[l];
+    const float4 A = T.rec[l].a, B = T.rec[l].b;
+    const int4 C = T.rec[l].c;
+    addr = C.y + da * C.z + db * C.w;
+    const float Pa = (float)(N - da) + B.w, Pb = (float)(N - db) + __int_as_float(C.x);
+    x[0] = A.x;
+    x[1] = A.y;
+    x[2] = A.z;
+    x[3] = fmaf(A.w, Pa, B.x * Pb);
+    x[4] = fmaf(B.y, Pa, B.z * Pb);
 }
 
 template <int N> constexpr int mlp_queue_bytes() { return (kMlpThreads * PairCap<N>::value * 2 + 15) / 16 * 16; }
@@ -145,15 +153,9 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_views(DevGeom g, MlpDev 
         mr.ua = mr.ub = mr.va = mr.vb = 0.0f;
         rs.S[0] = rs.S[1] = rs.S[2] = 0;
     }
-    T.wc0[tid] = mr.wc[0];
-    T.wc1[tid] = mr.wc[1];
-    T.wc2[tid] = mr.wc[2];
-    T.ua[tid] = mr.ua;
-    T.ub[tid] = mr.ub;
-    T.va[tid] = mr.va;
-    T.vb[tid] = mr.vb;
-    T.S1[tid] = rs.S[1];
-    T.S2[tid] = rs.S[2];
+    T.rec[tid].a = make_float4(mr.wc[0], mr.wc[1], mr.wc[2], mr.ua);
+    T.rec[tid].b = make_float4(mr.ub, mr.va, mr.vb, 0.0f);
+    T.rec[tid].c = make_int4(0, 0, rs.S[1], rs.S[2]);
     T.acc[tid] = 0.0f;
     T.yv[tid] = yr;
     const int nslab = rs.j1 - rs.j0 + 1;
@@ -194,14 +196,8 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_views(DevGeom g, MlpDev 
             float cv = 0.0f;
             int l = 0, addr = 0;
             if (r < n) {
-                float Pa, Pb;
-                decode_row<N>(T, q[r], l, addr, Pa, Pb);
+                decode_row<N>(T, q[r], l, addr, x);
                 if (!ADJ) cv = __ldg(cin + addr);
-                x[0] = T.wc0[l];
-                x[1] = T.wc1[l];
-                x[2] = T.wc2[l];
-                x[3] = fmaf(T.ua[l], Pa, T.ub[l] * Pb);
-                x[4] = fmaf(T.va[l], Pa, T.vb[l] * Pb);
             }
             float o;
             const bool tok = tc_mlp_tile(S, x, o, phase);

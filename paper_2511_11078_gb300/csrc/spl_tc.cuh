@@ -262,6 +262,41 @@ __device__ __forceinline__ void tc_row(const TcMlpSmem &S, float (&z)[64])
     tc::wait_ld();
 }
 
+// SiLU of two values with the reciprocal 1 / d, d = 1 + 2^(-z log2 e), by
+// Newton-Raphson steps r <- r + r (1 - d r) on the FMA pipe instead of the
+// MUFU.  The seed negates the IEEE-754 exponent by an integer subtraction
+// from the bit pattern of 2^127 (bits(2^127) - bits(d) ~ bits(1/d) for
+// d >= 1) and lies within 12.5 % above 1/d; each step squares the relative
+// error, so three take it to 0.125^8 ~ 6e-8.  d is capped at 2^126
+// (z < -87, where SiLU is below 1e-36 either way) so the seed stays normal.
+__device__ __forceinline__ float2 silu2_nr(float2 z)
+{
+    constexpr float kNegLog2e = -1.4426950408889634f;
+    const float2 m = __fmul2_rn(z, make_float2(kNegLog2e, kNegLog2e));
+    float2 d = __fadd2_rn(make_float2(ex2_approx(m.x), ex2_approx(m.y)), make_float2(1.0f, 1.0f));
+    d.x = fminf(d.x, 0x1p126f);
+    d.y = fminf(d.y, 0x1p126f);
+    float2 r = make_float2(__int_as_float(0x7F000000 - __float_as_int(d.x)),
+                           __int_as_float(0x7F000000 - __float_as_int(d.y)));
+    const float2 nd = __fmul2_rn(d, make_float2(-1.0f, -1.0f));
+#pragma unroll
+    for (int it = 0; it < 3; ++it) r = __ffma2_rn(r, __ffma2_rn(nd, r, make_float2(1.0f, 1.0f)), r);
+    return __fmul2_rn(z, r);
+}
+
+// The SiLU pairs of a row (p = 0..31 per layer) are split between the MUFU
+// reciprocal and the Newton form so that the MUFU queue and the FMA pipe
+// share the work: pair p takes the Newton form when bit (p mod 8) of
+// kTcNrMask is set.
+#ifndef SPL_TC_NR_MASK
+#define SPL_TC_NR_MASK 0x11
+#endif
+constexpr unsigned kTcNrMask = SPL_TC_NR_MASK;
+__device__ __forceinline__ float2 tc_silu2(int p, float2 z)
+{
+    return ((kTcNrMask >> (p & 7)) & 1u) ? silu2_nr(z) : silu2(z);
+}
+
 // SiLU of the row, rounded to BF16 into this thread's row of the A operand
 // of the next layer.
 __device__ __forceinline__ void tc_silu_store(TcMlpSmem &S, const float (&z)[64])
@@ -272,7 +307,7 @@ __device__ __forceinline__ void tc_silu_store(TcMlpSmem &S, const float (&z)[64]
         uint32_t w[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float2 h = silu2(make_float2(z[8 * j + 2 * q], z[8 * j + 2 * q + 1]));
+            const float2 h = tc_silu2(4 * j + q, make_float2(z[8 * j + 2 * q], z[8 * j + 2 * q + 1]));
             w[q] = pack_bf16(h.x, h.y);
         }
         *reinterpret_cast<uint4 *>(S.a2 + kmaj_off(kTcRows, m, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -308,7 +343,7 @@ __device__ __forceinline__ bool tc_mlp_tile(TcMlpSmem &S, const float (&x)[5], f
     float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < 64; k += 2) {
-        const float2 h = silu2(make_float2(z[k], z[k + 1]));
+        const float2 h = tc_silu2(k >> 1, make_float2(z[k], z[k + 1]));
         acc = __ffma2_rn(h, make_float2(S.w4[k], S.w4[k + 1]), acc);
     }
     out = acc.x + acc.y + S.b4;
