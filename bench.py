@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--mlp-steps", type=int, default=200000,
                     help="Adam steps of the learned footprint trained before the MLP measurement (0: skip it)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU-baseline sample")
+    ap.add_argument("--mlp-views", default=None, metavar="START:STOP",
+                    help="only run the learned-footprint projector (untrained f_theta, seed 5) once forward and "
+                         "once adjoint on views START..STOP-1 of the workload and print their times (a small case "
+                         "for profiling)")
     return ap.parse_args()
 
 
@@ -561,10 +565,45 @@ def run_ours(args):
     return 0
 
 
+def run_mlp_views(args):
+    """The learned-footprint projector alone on a subset of the workload's
+    views: one forward and one adjoint, timed with CUDA events."""
+    import torch
+
+    from paper_2511_11078_gb300 import build as B
+    from paper_2511_11078_gb300 import inputs as I
+    from paper_2511_11078_gb300 import spl
+
+    B.build()
+    spl.lib()
+    a, b = (int(v) for v in args.mlp_views.split(":"))
+    wl = I.workload_tilt(args.degree)
+    geom = spl.Geometry(wl.dims, wl.origin, wl.geometry.subset_views(np.arange(a, b)))
+    c = torch.tensor(wl.coeffs, device="cuda")
+    mlp = spl.Mlp(args.degree, max_batch=8192, seed=5)
+    bas = spl.basis(args.degree, spl.SPL_FP_MLP, mlp)
+    y = torch.empty(geom.n_rays, device="cuda")
+    cb = torch.empty(geom.coeff_shape, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    spl.forward(geom, c, y, bas)
+    ev[1].record()
+    spl.adjoint(geom, y, cb, bas)
+    ev[2].record()
+    torch.cuda.synchronize()
+    geom.status()
+    print(json.dumps({"mlp_views": [a, b], "A_ms": ev[0].elapsed_time(ev[1]), "AT_ms": ev[1].elapsed_time(ev[2]),
+                      "pairs": spl.count_pairs(geom, args.degree)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mlp_views:
+        return run_mlp_views(args)
     return run_ours(args)
 
 
