@@ -78,6 +78,30 @@ def test_mlp_eval_matches_oracle(env, orc):
     assert 0 < np.max(np.abs(got - ref0)) <= 5e-2 * np.max(np.abs(ref0))
 
 
+@pytest.mark.parametrize("count", [1, 127, 129, 200003])
+def test_mlp_eval_tile_tails_and_many_tiles(env, orc, count):
+    # The evaluation runs 128-row tiles on a grid of at most 608 CTAs: one
+    # row, a tile minus one, a tile plus one, and enough rows for every CTA
+    # to run several tiles (the tensor-core completion barrier then cycles
+    # through its phases).
+    torch, spl, learn = env
+    rng = np.random.default_rng(5100 + count)
+    m = spl.Mlp(3, max_batch=1024, seed=2)
+    prm = random_params(rng)
+    m.set_params(prm)
+    X = random_features(rng, count)
+    out = torch.full((count,), float("nan"), dtype=torch.float32, device="cuda")
+    m.eval(torch.tensor(X, device="cuda"), out)
+    ref = orc.mlp_forward(SIZES, prm.astype(np.float64), X.astype(np.float64), mode=1)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    fmax = np.max(np.abs(ref))
+    d = np.abs(got - ref)
+    assert np.median(d) <= 1e-5 * fmax
+    assert np.count_nonzero(d > 1e-4 * fmax) <= max(1, 0.005 * d.size)
+    assert np.max(d) <= 1e-2 * fmax
+
+
 def test_mlp_params_roundtrip_and_init(env):
     torch, spl, learn = env
     m = spl.Mlp(2, max_batch=64, seed=123)
