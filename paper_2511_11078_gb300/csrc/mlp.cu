@@ -4,9 +4,9 @@
 // loss and Adam.
 //
 // Training step (all kernels here, one stream, no host sync):
-//   k_train_forward  -- the inference tile (BF16 MMAs) on the batch, saving
-//                       pre-activations and the activations that entered
-//                       each layer;
+//   k_train_forward  -- the inference tile (tcgen05 BF16 MMAs) on the batch,
+//                       saving pre-activations and the activations that
+//                       entered each layer;
 //   k_train_backward -- one thread per row: dL/dz of every layer (FP32, the
 //                       BF16 roundings passed straight through);
 //   k_train_wgrad    -- per batch chunk, dL/dW = sum_b dz_b x h_b^T and
@@ -24,7 +24,6 @@
 
 namespace spl {
 
-constexpr int kEvalThreads = 128;  // 4 warps, one 16-row tile per warp at a time
 constexpr int kChunkRows = 256;    // rows per weight-gradient partial
 constexpr int kWgThreads = 256;
 
@@ -41,6 +40,7 @@ struct spl_mlp {
     float *grad;      // [kParams]
     uint32_t *w23;    // evaluation copy, BF16 hidden layers
     float *f32;       // evaluation copy, FP32 first/last layers and biases
+    void *tc_img;     // evaluation copy in the tcgen05 tile's operand layout
     float *act;       // [6][max_batch][64] z1 h1 z2 h2 z3 h3
     float *out;       // [max_batch] outputs
     float *dz;        // [3][max_batch][64] dz1 dz2 dz3
@@ -57,15 +57,19 @@ MlpDev mlp_dev(const spl_mlp *m)
     MlpDev d;
     d.w23 = m->w23;
     d.f32 = m->f32;
+    d.tc_img = m->tc_img;
     return d;
 }
 
 // ---------------------------------------------------------------- evaluation copy
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-__global__ void k_prep(const float *__restrict__ P, uint32_t *__restrict__ w23, float *__restrict__ f32)
+__global__ void k_prep(const float *__restrict__ P, uint32_t *__restrict__ w23, float *__restrict__ f32,
+                       TcMlpImage *img)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // the tcgen05 tile's image of the same roundings
+    tc_mlp_image(P, *img, i, gridDim.x * blockDim.x);
     // hidden layers: rows of W2 / W3 as BF16 pairs, padded stride
     if (i < 2 * kHid * kRowWords) {
         const int layer = i / (kHid * kRowWords), rem = i % (kHid * kRowWords);
@@ -90,7 +94,7 @@ __global__ void k_prep(const float *__restrict__ P, uint32_t *__restrict__ w23, 
 static spl_status prep(spl_mlp *m, cudaStream_t st)
 {
     const int n = 2 * kHid * kRowWords;
-    k_prep<<<(n + 255) / 256, 256, 0, st>>>(m->master, m->w23, m->f32);
+    k_prep<<<(n + 255) / 256, 256, 0, st>>>(m->master, m->w23, m->f32, reinterpret_cast<TcMlpImage *>(m->tc_img));
     return cuda_check(cudaGetLastError(), "mlp prep launch");
 }
 
@@ -98,17 +102,18 @@ static spl_status prep(spl_mlp *m, cudaStream_t st)
 // FROM_WP: rows given as (omega, p) -> canonical features and the exact
 // support mask of the basis at the origin; otherwise rows are features.
 template <bool FROM_WP>
-__global__ void __launch_bounds__(kTcRows) k_mlp_rows(MlpDev w, int degree, long long count,
+__global__ void __launch_bounds__(2 * kTcRows, 2) k_mlp_rows(MlpDev w, int degree, long long count,
                                                       const float *__restrict__ a, const float *__restrict__ b,
                                                       float *__restrict__ out)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     TcMlpSmem &S = *reinterpret_cast<TcMlpSmem *>(tc_smem);
+    __shared__ float part[2 * kTcRows];
     tc_mlp_setup(w, S);
     unsigned phase = 0;
     const long long tiles = (count + kTcRows - 1) / kTcRows;
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const long long r = tile * kTcRows + threadIdx.x;
+        const long long r = tile * kTcRows + tc_rowid<2>();
         float x[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         float mask = 0.0f;
         if (r < count) {
@@ -147,11 +152,11 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_rows(MlpDev w, int degree, long
             }
         }
         float o;
-        const bool ok = tc_mlp_tile(S, x, o, phase);
+        const bool ok = tc_mlp_tile<2>(S, x, o, phase, part);
         // a tensor-core wait that gave up (not expected) leaves NaN in the
         // rows of the tile and stops the CTA
         const bool bad = __syncthreads_or(!ok);
-        if (r < count) out[r] = bad ? __int_as_float(0x7FC00000) : o * mask;
+        if (r < count && tc_half<2>() == 0) out[r] = bad ? __int_as_float(0x7FC00000) : o * mask;
         if (bad) break;
     }
     tc_mlp_teardown(S);
@@ -180,42 +185,37 @@ spl_status footprint_mlp(const spl_basis_desc *b, long long count, const float *
 {
     spl_status s = rows_smem_attr<true>();
     if (s != SPL_OK) return s;
-    k_mlp_rows<true><<<eval_blocks(count), kTcRows, sizeof(TcMlpSmem), st>>>(mlp_dev(b->mlp), b->degree, count, w, p,
+    k_mlp_rows<true><<<eval_blocks(count), 2 * kTcRows, sizeof(TcMlpSmem), st>>>(mlp_dev(b->mlp), b->degree, count, w, p,
                                                                              out);
     return cuda_check(cudaGetLastError(), "mlp footprint launch");
 }
 
 // ---------------------------------------------------------------- training
-__global__ void __launch_bounds__(kEvalThreads) k_train_forward(MlpDev w, int B, const float *__restrict__ X,
-                                                                float *act, float *out, int max_batch)
+__global__ void __launch_bounds__(2 * kTcRows, 2) k_train_forward(MlpDev w, int B, const float *__restrict__ X,
+                                                               float *act, float *out, int max_batch)
 {
-    __shared__ MlpSmem S;
-    mlp_load_smem(w, S);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int warps = gridDim.x * (kEvalThreads / 32);
-    const int wid = blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
-    const int tiles = (B + 15) / 16;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlpSmem &S = *reinterpret_cast<TcMlpSmem *>(tc_smem);
+    __shared__ float part[2 * kTcRows];
+    tc_mlp_setup(w, S);
+    unsigned phase = 0;
     const size_t L = (size_t)max_batch * 64;
-    for (int tile = wid; tile < tiles; tile += warps) {
-        float x[2][5];
-        MlpSave sv{act, act + L, act + 2 * L, act + 3 * L, act + 4 * L, act + 5 * L, -1, -1};
+    const int tiles = (B + kTcRows - 1) / kTcRows;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int r = tile * kTcRows + tc_rowid<2>();
+        float x[5];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = tile * 16 + g + 8 * h;
-#pragma unroll
-            for (int e = 0; e < 5; ++e) x[h][e] = r < B ? X[5 * r + e] : 0.0f;
-        }
-        // every lane of a quad saves its own columns of the quad's two rows
-        sv.row_g = tile * 16 + g < B ? tile * 16 + g : -1;
-        sv.row_g8 = tile * 16 + g + 8 < B ? tile * 16 + g + 8 : -1;
-        float o0, o1;
-        mlp_tile16<true>(S, x[0], x[1], o0, o1, &sv);
-        if (t == 0) {
-            if (sv.row_g >= 0) out[sv.row_g] = o0;
-            if (sv.row_g8 >= 0) out[sv.row_g8] = o1;
-        }
+        for (int e = 0; e < 5; ++e) x[e] = r < B ? X[5 * r + e] : 0.0f;
+        const TcSave sv{act, act + L, act + 2 * L, act + 3 * L, act + 4 * L, act + 5 * L, r < B ? r : -1};
+        float o;
+        const bool ok = tc_mlp_tile<2, true>(S, x, o, phase, part, &sv);
+        // a tensor-core wait that gave up (not expected) leaves NaN outputs,
+        // so the loss and the gradient come out NaN
+        const bool bad = __syncthreads_or(!ok);
+        if (r < B && tc_half<2>() == 0) out[r] = bad ? __int_as_float(0x7FC00000) : o;
+        if (bad) break;
     }
+    tc_mlp_teardown(S);
 }
 
 __device__ __forceinline__ float silu_grad(float z)
@@ -401,9 +401,15 @@ static spl_status grad_impl(spl_mlp *m, int B, const float *X, const float *Y, f
                             cudaStream_t st)
 {
     const MlpDev w = mlp_dev(m);
-    const int tiles = (B + 15) / 16;
-    const int fblocks = (tiles + 3) / 4;
-    k_train_forward<<<fblocks, kEvalThreads, 0, st>>>(w, B, X, m->act, m->out, m->max_batch);
+    static bool attr_done = false;
+    if (!attr_done) {
+        spl_status s = cuda_check(cudaFuncSetAttribute(k_train_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)sizeof(TcMlpSmem)),
+                                  "train forward smem attribute");
+        if (s != SPL_OK) return s;
+        attr_done = true;
+    }
+    k_train_forward<<<eval_blocks(B), 2 * kTcRows, sizeof(TcMlpSmem), st>>>(w, B, X, m->act, m->out, m->max_batch);
     const int bblocks = (B + kBwdThreads - 1) / kBwdThreads;
     k_train_backward<<<bblocks, kBwdThreads, 0, st>>>(m->master, B, Y, m->act, m->out, m->dz, m->dz4, m->loss_part,
                                                       m->max_batch);
@@ -450,6 +456,7 @@ extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long lo
     };
     const size_t o_master = take(kParams * 4), o_m = take(kParams * 4), o_v = take(kParams * 4),
                  o_grad = take(kParams * 4), o_w23 = take(2 * kHid * kRowWords * 4), o_f32 = take(kF32Size * 4),
+                 o_img = take(sizeof(TcMlpImage)),
                  o_act = take((size_t)6 * max_batch * 64 * 4), o_out = take((size_t)max_batch * 4),
                  o_dz = take((size_t)3 * max_batch * 64 * 4), o_dz4 = take((size_t)max_batch * 4),
                  o_part = take((size_t)chunks * (kParams + 1) * 4), o_loss = take((size_t)nloss * 8);
@@ -468,6 +475,7 @@ extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long lo
     m->grad = (float *)(base + o_grad);
     m->w23 = (uint32_t *)(base + o_w23);
     m->f32 = (float *)(base + o_f32);
+    m->tc_img = base + o_img;
     m->act = (float *)(base + o_act);
     m->out = (float *)(base + o_out);
     m->dz = (float *)(base + o_dz);
@@ -540,7 +548,7 @@ extern "C" spl_status spl_mlp_eval(const spl_mlp *m, long long count, const floa
     if (!feat_dev || !out_dev) return fail(SPL_ERR_ARG, "NULL array");
     spl_status s = rows_smem_attr<false>();
     if (s != SPL_OK) return s;
-    k_mlp_rows<false><<<eval_blocks(count), kTcRows, sizeof(TcMlpSmem), (cudaStream_t)stream>>>(
+    k_mlp_rows<false><<<eval_blocks(count), 2 * kTcRows, sizeof(TcMlpSmem), (cudaStream_t)stream>>>(
         mlp_dev(m), m->degree, count, feat_dev, nullptr, out_dev);
     return cuda_check(cudaGetLastError(), "mlp eval launch");
 }

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_views(DevGeom g, MlpDev 
                 if (!ADJ) cv = __ldg(cin + addr);
             }
             float o;
-            const bool tok = tc_mlp_tile(S, x, o, phase);
+            const bool tok = tc_mlp_tile<1>(S, x, o, phase);
             if (__syncthreads_or(!tok)) {  // a tensor-core wait gave up (not expected)
                 ok = false;
                 stop = true;

@@ -137,17 +137,24 @@ __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.
 constexpr int kTcRows = 128;  // rows of a tile = threads of a CTA
 constexpr int kTcCols = 64;   // TMEM columns of the accumulator (N = 64, FP32)
 
-// Shared-memory image of the network and the operands of one tile.
-struct __align__(1024) TcMlpSmem {
-    uint8_t a2[kTcRows * 64 * 2];  // A of layers 2 and 3: 128 x 64
-    uint8_t w2[64 * 64 * 2];       // B of layer 2: 64 (N) x 64 (K)
+// The network in the tile's operand layout (built once per parameter
+// update in global memory, copied into every CTA's shared memory).
+struct __align__(16) TcMlpImage {
+    uint8_t w2[64 * 64 * 2];        // B of layer 2: 64 (N) x 64 (K)
     uint8_t w3[64 * 64 * 2];
-    uint8_t a1[kTcRows * 16 * 2];  // A of layer 1: 128 x 16
-    uint8_t one[kTcRows * 16 * 2]; // A of the bias steps: rows (1, 1, 1, 0 ...)
-    uint8_t w1[64 * 16 * 2];       // B of layer 1: 64 x 16, [W1; W1; W1; 0]
-    uint8_t bias[3][64 * 16 * 2];  // B of the bias steps of layers 1-3
+    uint8_t w1[64 * 16 * 2];        // B of layer 1: 64 x 16, [W1; W1; W1; 0]
+    uint8_t bias[3][64 * 16 * 2];   // B of the bias steps of layers 1-3
+    uint8_t one[kTcRows * 16 * 2];  // A of the bias steps: rows (1, 1, 1, 0 ...)
     float w4[64];
     float b4;
+    float pad[3];
+};
+
+// Shared memory of a CTA: the network image and the operands of one tile.
+struct __align__(1024) TcMlpSmem {
+    TcMlpImage img;
+    uint8_t a2[kTcRows * 64 * 2];  // A of layers 2 and 3: 128 x 64
+    uint8_t a1[kTcRows * 16 * 2];  // A of layer 1: 128 x 16
     uint32_t tmem;
     uint64_t mbar;
 };
@@ -175,38 +182,53 @@ __device__ __forceinline__ void split3(float x, uint16_t &hi, uint16_t &mid, uin
     lo = bf16_bits_rn(r2);
 }
 
-// Weights (from the evaluation copy) into the tile's layout, the constant
-// bias-step operand, the completion barrier and the TMEM accumulator.
-// Called by all 128 threads; ends with a CTA barrier.
+// The network image from the FP32 parameter vector P (layout kOff*): the
+// same BF16 roundings as the evaluation copy (W1, W2, W3, W4 rounded to
+// nearest BF16, the biases split, b4 unrounded); grid-stride over the
+// calling threads (tid of nthreads).
+__device__ __forceinline__ void tc_mlp_image(const float *__restrict__ P, TcMlpImage &I, int tid, int nthreads)
+{
+    uint16_t *w1 = reinterpret_cast<uint16_t *>(I.w1);
+    for (int i = tid; i < 64 * 16; i += nthreads) {
+        const int n = i >> 4, k = i & 15;
+        w1[kmaj_off(64, n, k) / 2] = bf16_bits_rn(k < 15 ? P[kOffW1 + n * kIn + k % 5] : 0.0f);
+    }
+    // hidden layers: 16-byte units (row n, columns 8j .. 8j+7)
+    for (int i = tid; i < 2 * 64 * 8; i += nthreads) {
+        const int layer = i >> 9, n = (i >> 3) & 63, j = i & 7;
+        const float *W = P + (layer == 0 ? kOffW2 : kOffW3) + n * kHid + 8 * j;
+        const uint4 v = make_uint4(pack_bf16(W[0], W[1]), pack_bf16(W[2], W[3]), pack_bf16(W[4], W[5]),
+                                   pack_bf16(W[6], W[7]));
+        *reinterpret_cast<uint4 *>((layer == 0 ? I.w2 : I.w3) + kmaj_off(64, n, 8 * j)) = v;
+    }
+    for (int i = tid; i < 3 * 64 * 16; i += nthreads) {
+        const int layer = i >> 10, n = (i >> 4) & 63, k = i & 15;
+        uint16_t hi, mid, lo;
+        split3(P[(layer == 0 ? kOffB1 : (layer == 1 ? kOffB2 : kOffB3)) + n], hi, mid, lo);
+        const uint16_t v = k == 0 ? hi : (k == 1 ? mid : (k == 2 ? lo : (uint16_t)0));
+        reinterpret_cast<uint16_t *>(I.bias[layer])[kmaj_off(64, n, k) / 2] = v;
+    }
+    for (int i = tid; i < kTcRows * 16; i += nthreads) {
+        const int m = i >> 4, k = i & 15;
+        reinterpret_cast<uint16_t *>(I.one)[kmaj_off(kTcRows, m, k) / 2] = k < 3 ? (uint16_t)0x3F80u : (uint16_t)0;
+    }
+    for (int i = tid; i < 64; i += nthreads) I.w4[i] = __bfloat162float(__float2bfloat16_rn(P[kOffW4 + i]));
+    if (tid == 0) {
+        I.b4 = P[kOffB4];
+        I.pad[0] = I.pad[1] = I.pad[2] = 0.0f;
+    }
+}
+
+// The network image into shared memory (16-byte copies), the completion
+// barrier and the TMEM accumulator.  Called by all threads of the CTA; ends
+// with a CTA barrier.
 __device__ __forceinline__ void tc_mlp_setup(const MlpDev &w, TcMlpSmem &S)
 {
     const int tid = threadIdx.x;
-    uint16_t *w1 = reinterpret_cast<uint16_t *>(S.w1);
-    for (int i = tid; i < 64 * 16; i += blockDim.x) {
-        const int n = i >> 4, k = i & 15;
-        const float v = k < 15 ? w.f32[kF32W1 + n * 5 + k % 5] : 0.0f;  // BF16 numbers already
-        w1[kmaj_off(64, n, k) / 2] = bf16_bits_rn(v);
-    }
-    // hidden layers: 16-byte units (row n, columns 8j .. 8j+7) of the padded rows
-    for (int i = tid; i < 2 * 64 * 8; i += blockDim.x) {
-        const int layer = i >> 9, n = (i >> 3) & 63, j = i & 7;
-        const uint4 v = *reinterpret_cast<const uint4 *>(w.w23 + layer * kHid * kRowWords + n * kRowWords + 4 * j);
-        *reinterpret_cast<uint4 *>((layer == 0 ? S.w2 : S.w3) + kmaj_off(64, n, 8 * j)) = v;
-    }
-    for (int i = tid; i < 3 * 64 * 16; i += blockDim.x) {
-        const int layer = i >> 10, n = (i >> 4) & 63, k = i & 15;
-        uint16_t hi, mid, lo;
-        split3(w.f32[(layer == 0 ? kF32B1 : (layer == 1 ? kF32B2 : kF32B3)) + n], hi, mid, lo);
-        const uint16_t v = k == 0 ? hi : (k == 1 ? mid : (k == 2 ? lo : (uint16_t)0));
-        reinterpret_cast<uint16_t *>(S.bias[layer])[kmaj_off(64, n, k) / 2] = v;
-    }
-    for (int i = tid; i < kTcRows * 16; i += blockDim.x) {
-        const int m = i >> 4, k = i & 15;
-        reinterpret_cast<uint16_t *>(S.one)[kmaj_off(kTcRows, m, k) / 2] = k < 3 ? (uint16_t)0x3F80u : (uint16_t)0;
-    }
-    for (int i = tid; i < 64; i += blockDim.x) S.w4[i] = w.f32[kF32W4 + i];
+    const uint4 *src = reinterpret_cast<const uint4 *>(w.tc_img);
+    uint4 *dst = reinterpret_cast<uint4 *>(&S.img);
+    for (int i = tid; i < (int)(sizeof(TcMlpImage) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
     if (tid == 0) {
-        S.b4 = w.f32[kF32B4];
         tc::mbar_init(&S.mbar, 1);
         tc::fence_mbar_init();
     }
@@ -243,8 +265,8 @@ __device__ __forceinline__ bool tc_layer(TcMlpSmem &S, const uint8_t *a, const u
         for (int s = 0; s < nk; ++s)
             tc::mma(S.tmem, tc::desc(sa + s * (kTcRows / 8) * 256, (kTcRows / 8) * 128, 128),
                     tc::desc(sb + s * 8 * 256, 8 * 128, 128), idesc, s > 0);
-        tc::mma(S.tmem, tc::desc(tc::saddr(S.one), (kTcRows / 8) * 128, 128),
-                tc::desc(tc::saddr(S.bias[layer]), 8 * 128, 128), idesc, 1);
+        tc::mma(S.tmem, tc::desc(tc::saddr(S.img.one), (kTcRows / 8) * 128, 128),
+                tc::desc(tc::saddr(S.img.bias[layer]), 8 * 128, 128), idesc, 1);
         tc::commit(&S.mbar);
     }
     const bool ok = tc::mbar_wait(&S.mbar, phase);
@@ -253,12 +275,21 @@ __device__ __forceinline__ bool tc_layer(TcMlpSmem &S, const uint8_t *a, const u
     return ok;
 }
 
-// This thread's row of the accumulator (64 FP32 values) after a layer.
-__device__ __forceinline__ void tc_row(const TcMlpSmem &S, float (&z)[64])
+// Threads per row of a tile: TPR = 1 (128 threads, a whole row each) or
+// TPR = 2 (256 threads; warps w and w + 4 read the same TMEM lane quarter,
+// w % 4, and take columns 0..31 and 32..63 of its rows): half the serial
+// work per thread, for batches too small to fill the GPU with 128-row tiles.
+template <int TPR> __device__ __forceinline__ int tc_rowid() { return threadIdx.x & (kTcRows - 1); }
+template <int TPR> __device__ __forceinline__ int tc_half() { return TPR == 1 ? 0 : (int)(threadIdx.x >> 7); }
+
+// This thread's columns of its row of the accumulator after a layer:
+// 64 / TPR FP32 values, from column 64 / TPR * half.
+template <int TPR>
+__device__ __forceinline__ void tc_row(const TcMlpSmem &S, float (&z)[64 / TPR])
 {
-    const uint32_t t = S.tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
+    const uint32_t t = S.tmem + ((uint32_t)(threadIdx.x & 96) << 16) + (uint32_t)(tc_half<TPR>() * 32);
     tc::ld32<0>(t, z);
-    tc::ld32<32>(t + 32, z);
+    if (TPR == 1) tc::ld32<(TPR == 1 ? 32 : 0)>(t + 32, z);
     tc::wait_ld();
 }
 
@@ -297,29 +328,62 @@ __device__ __forceinline__ float2 tc_silu2(int p, float2 z)
     return ((kTcNrMask >> (p & 7)) & 1u) ? silu2_nr(z) : silu2(z);
 }
 
-// SiLU of the row, rounded to BF16 into this thread's row of the A operand
-// of the next layer.
-__device__ __forceinline__ void tc_silu_store(TcMlpSmem &S, const float (&z)[64])
+// SiLU of this thread's columns, rounded to BF16 into its part of the row
+// of the A operand of the next layer (and, with SAVE, z and the rounded
+// activations to zb / hb, which point at the row).
+template <int TPR, bool SAVE>
+__device__ __forceinline__ void tc_silu_store(TcMlpSmem &S, const float (&z)[64 / TPR], float *zb, float *hb)
 {
-    const int m = threadIdx.x;
+    constexpr int NC = 64 / TPR;  // columns of this thread
+    const int m = tc_rowid<TPR>(), c0 = NC * tc_half<TPR>();
+    if (SAVE) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+        for (int k = 0; k < NC; k += 4)
+            *reinterpret_cast<float4 *>(zb + c0 + k) = make_float4(z[k], z[k + 1], z[k + 2], z[k + 3]);
+    }
+#pragma unroll
+    for (int j = 0; j < NC / 8; ++j) {
         uint32_t w[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const float2 h = tc_silu2(4 * j + q, make_float2(z[8 * j + 2 * q], z[8 * j + 2 * q + 1]));
             w[q] = pack_bf16(h.x, h.y);
         }
-        *reinterpret_cast<uint4 *>(S.a2 + kmaj_off(kTcRows, m, 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(S.a2 + kmaj_off(kTcRows, m, c0 + 8 * j)) = make_uint4(w[0], w[1], w[2], w[3]);
+        if (SAVE) {
+            float4 *d = reinterpret_cast<float4 *>(hb + c0 + 8 * j);
+            d[0] = make_float4(__uint_as_float(w[0] << 16), __uint_as_float(w[0] & 0xFFFF0000u),
+                               __uint_as_float(w[1] << 16), __uint_as_float(w[1] & 0xFFFF0000u));
+            d[1] = make_float4(__uint_as_float(w[2] << 16), __uint_as_float(w[2] & 0xFFFF0000u),
+                               __uint_as_float(w[3] << 16), __uint_as_float(w[3] & 0xFFFF0000u));
+        }
     }
 }
 
+// Optional capture of a tile's activations for training: z1, h1, z2, h2,
+// z3, h3 of this thread's row (FP32; h1, h2 as the BF16-rounded values that
+// entered the tensor-core layers), 64 values each at row * 64 of the arrays
+// (row < 0: nothing is stored).
+struct TcSave {
+    float *z1, *h1, *z2, *h2, *z3, *h3;
+    int row;
+};
+
 // f_theta of this thread's row x (5 features) in a tile of 128 rows; every
-// thread of the CTA calls it.  Returns false if a tensor-core wait gave up
-// (the output is then meaningless).
-__device__ __forceinline__ bool tc_mlp_tile(TcMlpSmem &S, const float (&x)[5], float &out, unsigned &phase)
+// thread of the CTA (128 * TPR) calls it, the TPR threads of a row with the
+// same x.  Returns false if a tensor-core wait gave up (the output is then
+// meaningless).  The output is valid in every thread of the row.  part:
+// 2 x 128 floats of shared memory for combining the halves of the output
+// layer (TPR = 2; rewritten only after the next tile's first barrier).
+// SAVE stores the activations of the row (sv->row >= 0).
+template <int TPR, bool SAVE = false>
+__device__ __forceinline__ bool tc_mlp_tile(TcMlpSmem &S, const float (&x)[5], float &out, unsigned &phase,
+                                            float *part = nullptr, const TcSave *sv = nullptr)
 {
-    const int m = threadIdx.x;
+    constexpr int NC = 64 / TPR;
+    const int m = tc_rowid<TPR>(), half = tc_half<TPR>();
+    const bool save = SAVE && sv->row >= 0;
+    const size_t ro = SAVE ? (size_t)(sv->row < 0 ? 0 : sv->row) * 64 : 0;
     {
         uint16_t p[16];
 #pragma unroll
@@ -328,25 +392,39 @@ __device__ __forceinline__ bool tc_mlp_tile(TcMlpSmem &S, const float (&x)[5], f
         uint32_t v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[q] = (uint32_t)p[2 * q] | ((uint32_t)p[2 * q + 1] << 16);
-        *reinterpret_cast<uint4 *>(S.a1 + kmaj_off(kTcRows, m, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<uint4 *>(S.a1 + kmaj_off(kTcRows, m, 8)) = make_uint4(v[4], v[5], v[6], v[7]);
+        if (TPR == 1 || half == 0)
+            *reinterpret_cast<uint4 *>(S.a1 + kmaj_off(kTcRows, m, 0)) = make_uint4(v[0], v[1], v[2], v[3]);
+        if (TPR == 1 || half == 1)
+            *reinterpret_cast<uint4 *>(S.a1 + kmaj_off(kTcRows, m, 8)) = make_uint4(v[4], v[5], v[6], v[7]);
     }
-    bool ok = tc_layer(S, S.a1, S.w1, 1, 0, phase);
-    float z[64];
-    tc_row(S, z);
-    tc_silu_store(S, z);
-    ok &= tc_layer(S, S.a2, S.w2, 4, 1, phase);
-    tc_row(S, z);
-    tc_silu_store(S, z);
-    ok &= tc_layer(S, S.a2, S.w3, 4, 2, phase);
-    tc_row(S, z);
+    bool ok = tc_layer(S, S.a1, S.img.w1, 1, 0, phase);
+    float z[NC];
+    tc_row<TPR>(S, z);
+    if (save) tc_silu_store<TPR, true>(S, z, sv->z1 + ro, sv->h1 + ro);
+    else tc_silu_store<TPR, false>(S, z, nullptr, nullptr);
+    ok &= tc_layer(S, S.a2, S.img.w2, 4, 1, phase);
+    tc_row<TPR>(S, z);
+    if (save) tc_silu_store<TPR, true>(S, z, sv->z2 + ro, sv->h2 + ro);
+    else tc_silu_store<TPR, false>(S, z, nullptr, nullptr);
+    ok &= tc_layer(S, S.a2, S.img.w3, 4, 2, phase);
+    tc_row<TPR>(S, z);
+    const int c0 = NC * half;
     float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int k = 0; k < 64; k += 2) {
+    for (int k = 0; k < NC; k += 2) {
+        if (save) *reinterpret_cast<float2 *>(sv->z3 + ro + c0 + k) = make_float2(z[k], z[k + 1]);
         const float2 h = tc_silu2(k >> 1, make_float2(z[k], z[k + 1]));
-        acc = __ffma2_rn(h, make_float2(S.w4[k], S.w4[k + 1]), acc);
+        if (save) *reinterpret_cast<float2 *>(sv->h3 + ro + c0 + k) = h;
+        acc = __ffma2_rn(h, make_float2(S.img.w4[c0 + k], S.img.w4[c0 + k + 1]), acc);
     }
-    out = acc.x + acc.y + S.b4;
+    float o = acc.x + acc.y;
+    if (TPR == 2) {
+        // both threads of the row add the two halves in the same order
+        part[half * kTcRows + m] = o;
+        __syncthreads();
+        o = part[m] + part[kTcRows + m];
+    }
+    out = o + S.img.b4;
     return ok;
 }
 
