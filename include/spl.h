@@ -281,7 +281,10 @@ spl_status spl_mlp_set_params(spl_mlp *m, const float *host_params);
 spl_status spl_mlp_get_params(const spl_mlp *m, float *host_params);
 
 /* f_theta on `count` feature rows (float32 [count][5]) -> out_dev [count],
- * with the BF16 tensor-core inference kernel. */
+ * on the tcgen05 tensor cores (128-row tiles, BF16 operands, FP32
+ * accumulation in tensor memory; layer 1 and the biases at FP32 accuracy).
+ * A tensor-core completion wait that exceeds its bound (not expected)
+ * leaves NaN in the rows of the affected tile. */
 spl_status spl_mlp_eval(const spl_mlp *m, long long count, const float *feat_dev, float *out_dev, void *stream);
 
 /* Gradient of L = (1/B) sum_b (f_theta(x_b) - y_b)^2 (Algorithm 1's loss)

@@ -11,7 +11,7 @@
 // the other threads and no registers: what is left to the threads is SiLU,
 // the BF16 packing and the 64 -> 1 output layer.
 //
-// Precision contract (the same as the mma.sync tile): layers 2 and 3 multiply
+// Precision contract (the one the oracle emulates): layers 2 and 3 multiply
 // BF16 weights with the BF16-rounded activations, accumulating in FP32;
 // layer 1 and the biases keep FP32 accuracy through three-part BF16 splits
 // x = hi + mid + lo (hi and mid truncate the mantissa to 8 bits, the
