@@ -78,9 +78,9 @@ def parse():
                     help="Adam steps of the learned footprint trained before the MLP measurement (0: skip it)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target seconds of the CPU-baseline sample")
     ap.add_argument("--mlp-views", default=None, metavar="START:STOP",
-                    help="only run the learned-footprint projector (untrained f_theta, seed 5) once forward and "
-                         "once adjoint on views START..STOP-1 of the workload and print their times (a small case "
-                         "for profiling)")
+                    help="only run the learned-footprint projector (f_theta seeded 5, trained for --mlp-steps "
+                         "steps first) once forward and once adjoint on views START..STOP-1 of the workload and "
+                         "print their times (a small case for profiling)")
     return ap.parse_args()
 
 
@@ -581,6 +581,16 @@ def run_mlp_views(args):
     geom = spl.Geometry(wl.dims, wl.origin, wl.geometry.subset_views(np.arange(a, b)))
     c = torch.tensor(wl.coeffs, device="cuda")
     mlp = spl.Mlp(args.degree, max_batch=8192, seed=5)
+    train_us = None
+    if args.mlp_steps > 0:
+        from paper_2511_11078_gb300 import learn
+
+        data = learn.FootprintSet(args.degree, 1 << 22, seed=31, device=torch.device("cuda"))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        learn.train(mlp, data, steps=args.mlp_steps, batch=8192, lr0=3e-3, lr_min=1e-6)
+        torch.cuda.synchronize()
+        train_us = (time.perf_counter() - t0) / args.mlp_steps * 1e6
     bas = spl.basis(args.degree, spl.SPL_FP_MLP, mlp)
     y = torch.empty(geom.n_rays, device="cuda")
     cb = torch.empty(geom.coeff_shape, device="cuda")
@@ -594,7 +604,8 @@ def run_mlp_views(args):
     torch.cuda.synchronize()
     geom.status()
     print(json.dumps({"mlp_views": [a, b], "A_ms": ev[0].elapsed_time(ev[1]), "AT_ms": ev[1].elapsed_time(ev[2]),
-                      "pairs": spl.count_pairs(geom, args.degree)}), flush=True)
+                      "pairs": spl.count_pairs(geom, args.degree), "train_steps": args.mlp_steps,
+                      "train_us_per_step": train_us}), flush=True)
     return 0
 
 

@@ -24,7 +24,7 @@
 
 namespace spl {
 
-constexpr int kChunkRows = 256;    // rows per weight-gradient partial
+constexpr int kChunkRows = 64;     // rows per weight-gradient partial
 constexpr int kWgThreads = 256;
 
 }  // namespace spl
@@ -224,34 +224,49 @@ __device__ __forceinline__ float silu_grad(float z)
     return s * (1.0f + z * (1.0f - s));
 }
 
-// dL/dz of every layer for L = (1/B) sum (f(x_b) - y_b)^2; one thread per
-// row, the layer's gradient vector in registers, weights read as float4
-// from shared memory (four independent FMA chains).  Weights as used in the
-// forward (BF16-rounded) come from the FP32 master rounded on the fly;
-// roundings of activations pass straight through.
+// dL/dz of every layer for L = (1/B) sum (f(x_b) - y_b)^2.  Four threads
+// per row (consecutive lanes), each owning 16 of the 64 units of a layer;
+// a layer's gradient vector passes between them through shared memory
+// (rows padded to 65 floats: the 8 rows of a warp hit distinct banks).
+// Weights as used in the forward (BF16-rounded) come from the FP32 master
+// rounded on the fly; roundings of activations pass straight through.
 constexpr int kBwdThreads = 64;
+constexpr int kBwdSplit = 4;                         // threads per row
+constexpr int kBwdRows = kBwdThreads / kBwdSplit;    // rows per block
+constexpr int kBwdUnits = kHid / kBwdSplit;          // units per thread
 
-__device__ __forceinline__ void back_layer(const float *__restrict__ Wt, const float (&gin)[kHid],
-                                           const float *__restrict__ z, float *__restrict__ gout_g, float (&gout)[kHid])
+// gout[i] = silu'(z[i]) * sum_c W[c][i] gin[c] for this thread's units
+// i = i0 .. i0 + 15; W as [c][i] (row c = output unit of the layer above)
+__device__ __forceinline__ void back_layer(const float *__restrict__ W, const float *__restrict__ gin, int i0,
+                                           const float *__restrict__ z, float *__restrict__ gout_g,
+                                           float *__restrict__ gout_s)
 {
-    // gout[i] = silu'(z[i]) * sum_c W[c][i] gin[c]; Wt is W transposed, row i
+    float acc[kBwdUnits];
 #pragma unroll
-    for (int i0 = 0; i0 < kHid; i0 += 4) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < kBwdUnits; ++q) acc[q] = 0.0f;
+#pragma unroll 8
+    for (int c = 0; c < kHid; ++c) {
+        const float g = gin[c];
+        const float4 *w = reinterpret_cast<const float4 *>(W + c * kHid + i0);
 #pragma unroll
-        for (int c = 0; c < kHid; ++c) {
-            const float4 w = *reinterpret_cast<const float4 *>(Wt + c * kHid + i0);
-            acc.x = fmaf(w.x, gin[c], acc.x);
-            acc.y = fmaf(w.y, gin[c], acc.y);
-            acc.z = fmaf(w.z, gin[c], acc.z);
-            acc.w = fmaf(w.w, gin[c], acc.w);
+        for (int q4 = 0; q4 < kBwdUnits / 4; ++q4) {
+            const float4 v = w[q4];
+            acc[4 * q4] = fmaf(v.x, g, acc[4 * q4]);
+            acc[4 * q4 + 1] = fmaf(v.y, g, acc[4 * q4 + 1]);
+            acc[4 * q4 + 2] = fmaf(v.z, g, acc[4 * q4 + 2]);
+            acc[4 * q4 + 3] = fmaf(v.w, g, acc[4 * q4 + 3]);
         }
-        const float4 zz = *reinterpret_cast<const float4 *>(z + i0);
-        gout[i0] = acc.x * silu_grad(zz.x);
-        gout[i0 + 1] = acc.y * silu_grad(zz.y);
-        gout[i0 + 2] = acc.z * silu_grad(zz.z);
-        gout[i0 + 3] = acc.w * silu_grad(zz.w);
-        *reinterpret_cast<float4 *>(gout_g + i0) = make_float4(gout[i0], gout[i0 + 1], gout[i0 + 2], gout[i0 + 3]);
+    }
+#pragma unroll
+    for (int q4 = 0; q4 < kBwdUnits / 4; ++q4) {
+        const float4 zz = *reinterpret_cast<const float4 *>(z + i0 + 4 * q4);
+        const float4 g = make_float4(acc[4 * q4] * silu_grad(zz.x), acc[4 * q4 + 1] * silu_grad(zz.y),
+                                     acc[4 * q4 + 2] * silu_grad(zz.z), acc[4 * q4 + 3] * silu_grad(zz.w));
+        *reinterpret_cast<float4 *>(gout_g + i0 + 4 * q4) = g;
+        gout_s[i0 + 4 * q4] = g.x;
+        gout_s[i0 + 4 * q4 + 1] = g.y;
+        gout_s[i0 + 4 * q4 + 2] = g.z;
+        gout_s[i0 + 4 * q4 + 3] = g.w;
     }
 }
 
@@ -266,6 +281,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_train_backward(const float *__r
     __shared__ __align__(16) float W2[kHid * kHid];
     __shared__ __align__(16) float W3[kHid * kHid];
     __shared__ float W4[kHid];
+    __shared__ float gbuf[2][kBwdRows][kHid + 1];
     __shared__ double red[kBwdThreads / 32];
     for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
         W2[i] = bf16r(P[kOffW2 + i]);
@@ -273,28 +289,35 @@ __global__ void __launch_bounds__(kBwdThreads) k_train_backward(const float *__r
     }
     if (threadIdx.x < kHid) W4[threadIdx.x] = bf16r(P[kOffW4 + threadIdx.x]);
     __syncthreads();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lr = threadIdx.x / kBwdSplit, i0 = (threadIdx.x % kBwdSplit) * kBwdUnits;
+    const int r = blockIdx.x * kBwdRows + lr;
     const size_t L = (size_t)max_batch * 64;
     double l2 = 0.0;
-    if (r < B) {
+    const bool live = r < B;  // the four threads of a row agree
+    if (live) {
         const float res = out[r] - Y[r];
-        l2 = (double)res * res;
-        const float d4 = 2.0f * res / (float)B;
-        dz4[r] = d4;
-        const float *z3 = act + 4 * L + (size_t)r * 64;
-        float g3[kHid], g2[kHid], g1[kHid];
-#pragma unroll
-        for (int c = 0; c < kHid; c += 4) {
-            const float4 zz = *reinterpret_cast<const float4 *>(z3 + c);
-            g3[c] = W4[c] * d4 * silu_grad(zz.x);
-            g3[c + 1] = W4[c + 1] * d4 * silu_grad(zz.y);
-            g3[c + 2] = W4[c + 2] * d4 * silu_grad(zz.z);
-            g3[c + 3] = W4[c + 3] * d4 * silu_grad(zz.w);
-            *reinterpret_cast<float4 *>(dz + 2 * L + (size_t)r * 64 + c) = make_float4(g3[c], g3[c + 1], g3[c + 2], g3[c + 3]);
+        if (i0 == 0) {
+            l2 = (double)res * res;
+            dz4[r] = 2.0f * res / (float)B;
         }
-        back_layer(W3, g3, act + 2 * L + (size_t)r * 64, dz + L + (size_t)r * 64, g2);
-        back_layer(W2, g2, act + (size_t)r * 64, dz + (size_t)r * 64, g1);
+        const float d4 = 2.0f * res / (float)B;
+        const float *z3 = act + 4 * L + (size_t)r * 64;
+#pragma unroll
+        for (int c = i0; c < i0 + kBwdUnits; c += 4) {
+            const float4 zz = *reinterpret_cast<const float4 *>(z3 + c);
+            const float4 g = make_float4(W4[c] * d4 * silu_grad(zz.x), W4[c + 1] * d4 * silu_grad(zz.y),
+                                         W4[c + 2] * d4 * silu_grad(zz.z), W4[c + 3] * d4 * silu_grad(zz.w));
+            *reinterpret_cast<float4 *>(dz + 2 * L + (size_t)r * 64 + c) = g;
+            gbuf[0][lr][c] = g.x;
+            gbuf[0][lr][c + 1] = g.y;
+            gbuf[0][lr][c + 2] = g.z;
+            gbuf[0][lr][c + 3] = g.w;
+        }
     }
+    __syncwarp();
+    if (live) back_layer(W3, gbuf[0][lr], i0, act + 2 * L + (size_t)r * 64, dz + L + (size_t)r * 64, gbuf[1][lr]);
+    __syncwarp();
+    if (live) back_layer(W2, gbuf[1][lr], i0, act + (size_t)r * 64, dz + (size_t)r * 64, gbuf[0][lr]);
     // per-block loss partial (fixed order)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l2 += __shfl_down_sync(0xffffffffu, l2, o);
@@ -410,7 +433,7 @@ static spl_status grad_impl(spl_mlp *m, int B, const float *X, const float *Y, f
         attr_done = true;
     }
     k_train_forward<<<eval_blocks(B), 2 * kTcRows, sizeof(TcMlpSmem), st>>>(w, B, X, m->act, m->out, m->max_batch);
-    const int bblocks = (B + kBwdThreads - 1) / kBwdThreads;
+    const int bblocks = (B + kBwdRows - 1) / kBwdRows;
     k_train_backward<<<bblocks, kBwdThreads, 0, st>>>(m->master, B, Y, m->act, m->out, m->dz, m->dz4, m->loss_part,
                                                       m->max_batch);
     const int chunks = (B + kChunkRows - 1) / kChunkRows;
@@ -447,7 +470,7 @@ extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long lo
     m->max_batch = max_batch;
     cudaGetDevice(&m->device);
     const int chunks = (max_batch + kChunkRows - 1) / kChunkRows;
-    const int nloss = (max_batch + kBwdThreads - 1) / kBwdThreads;
+    const int nloss = (max_batch + kBwdRows - 1) / kBwdRows;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
