@@ -11,7 +11,7 @@
 //                       BF16 roundings passed straight through);
 //   k_train_wgrad    -- per batch chunk, dL/dW = sum_b dz_b x h_b^T and
 //                       dL/db (FP32), into fixed partial slots;
-//   k_train_reduce   -- adds the chunk partials in index order (deterministic)
+//   k_train_reduce   -- adds the chunk partials in a fixed order (deterministic)
 //                       and the loss;
 //   k_adam           -- Adam on the FP32 master copy, then k_prep refreshes
 //                       the BF16 evaluation copy.
@@ -391,19 +391,45 @@ __global__ void __launch_bounds__(kWgThreads) k_train_wgrad(int B, const float *
     }
 }
 
-__global__ void k_train_reduce(const float *__restrict__ part, int chunks, const double *__restrict__ loss_part,
-                               int nloss, int B, float *grad, float *loss_out)
+// Gradient and loss from the partials in a fixed order: block b owns 32
+// parameters; warp w sums chunks w, w + 8, ... in order, then warp 0 adds
+// the 8 sums in order.  Block 0 also sums the loss partials (thread t:
+// partials t, t + 256, ...; then 8 per lane and a fixed shuffle tree).
+constexpr int kRedThreads = 256;
+__global__ void __launch_bounds__(kRedThreads) k_train_reduce(const float *__restrict__ part, int chunks,
+                                                              const double *__restrict__ loss_part, int nloss, int B,
+                                                              float *grad, float *loss_out)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kParams) {
-        float acc = 0.0f;
-        for (int c = 0; c < chunks; ++c) acc += part[(size_t)c * (kParams + 1) + i];
-        grad[i] = acc;
-    }
-    if (i == 0 && loss_out) {
+    __shared__ float ps[kRedThreads / 32][32];
+    __shared__ double ls[kRedThreads];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    float acc = 0.0f;
+    if (i < kParams)
+        for (int c = w; c < chunks; c += kRedThreads / 32) acc += part[(size_t)c * (kParams + 1) + i];
+    ps[w][lane] = acc;
+    const bool do_loss = blockIdx.x == 0 && loss_out != nullptr;
+    if (do_loss) {
         double l = 0.0;
-        for (int k = 0; k < nloss; ++k) l += loss_part[k];
-        loss_out[0] = (float)(l / (double)B);
+        for (int k = threadIdx.x; k < nloss; k += kRedThreads) l += loss_part[k];
+        ls[threadIdx.x] = l;
+    }
+    __syncthreads();
+    if (w == 0) {
+        if (i < kParams) {
+            float t = 0.0f;
+#pragma unroll
+            for (int g = 0; g < kRedThreads / 32; ++g) t += ps[g][lane];
+            grad[i] = t;
+        }
+        if (do_loss) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < kRedThreads / 32; ++k) t += ls[lane * (kRedThreads / 32) + k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) loss_out[0] = (float)(t / (double)B);
+        }
     }
 }
 
@@ -438,7 +464,7 @@ static spl_status grad_impl(spl_mlp *m, int B, const float *X, const float *Y, f
                                                       m->max_batch);
     const int chunks = (B + kChunkRows - 1) / kChunkRows;
     k_train_wgrad<<<dim3(chunks, 4), kWgThreads, 0, st>>>(B, X, m->act, m->dz, m->dz4, m->part, m->max_batch);
-    k_train_reduce<<<(kParams + 255) / 256, 256, 0, st>>>(m->part, chunks, m->loss_part, bblocks, B, grad, loss);
+    k_train_reduce<<<(kParams + 31) / 32, kRedThreads, 0, st>>>(m->part, chunks, m->loss_part, bblocks, B, grad, loss);
     return cuda_check(cudaGetLastError(), "mlp gradient launch");
 }
 
