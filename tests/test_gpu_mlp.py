@@ -142,6 +142,28 @@ def test_mlp_gradient_matches_oracle(env, orc, batch):
         assert np.linalg.norm(g[a:b] - gref[a:b]) <= 5e-3 * np.linalg.norm(gref[a:b]) + 1e-9
 
 
+@pytest.mark.parametrize("batch", [100, 8192])
+def test_mlp_gradient_parameter_groups(env, orc, batch):
+    # Each weight matrix and each bias vector on its own, so that an error in
+    # a small group (a bias, the output layer) cannot hide in a layer's norm;
+    # batch 8192 spans many weight-gradient chunks and reduction blocks.
+    torch, spl, learn = env
+    rng = np.random.default_rng(5300 + batch)
+    m = spl.Mlp(3, max_batch=8192, seed=3)
+    prm = random_params(rng, 0.8)
+    m.set_params(prm)
+    X = random_features(rng, batch)
+    Y = rng.normal(size=batch).astype(np.float32) * 0.2
+    grad = torch.empty(spl.MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    m.grad(torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"), grad, loss)
+    L, gref = orc.mlp_loss_grad(SIZES, prm.astype(np.float64), X.astype(np.float64), Y.astype(np.float64), mode=1)
+    g = grad.cpu().numpy().astype(np.float64)
+    groups = [(0, 320), (320, 384), (384, 4480), (4480, 4544), (4544, 8640), (8640, 8704), (8704, 8768), (8768, 8769)]
+    for a, b in groups:
+        assert np.linalg.norm(g[a:b] - gref[a:b]) <= 1e-4 * np.linalg.norm(gref[a:b]) + 1e-12, (a, b)
+
+
 def test_sampler_distribution(env, orc):
     torch, spl, learn = env
     n = 200000
