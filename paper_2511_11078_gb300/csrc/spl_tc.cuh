@@ -30,6 +30,8 @@
 // byte offset, (R / 8) * 128) and along the rows (stride byte offset, 128).
 #pragma once
 
+#include <stddef.h>
+
 #include "spl_mlp.cuh"
 
 namespace spl {
@@ -134,8 +136,11 @@ __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.
 
 }  // namespace tc
 
-constexpr int kTcRows = 128;  // rows of a tile = threads of a CTA
+constexpr int kTcRows = 128;  // rows of a tile (threads of a CTA: 128 or 256)
 constexpr int kTcCols = 64;   // TMEM columns of the accumulator (N = 64, FP32)
+// TMEM allocation never waits: every CTA that allocates holds at least
+// sizeof(TcMlpSmem) (49 KB) of shared memory, so at most 4 of them are
+// resident on an SM (228 KB), and 4 x 64 columns stay below the SM's 512.
 
 // The network in the tile's operand layout (built once per parameter
 // update in global memory, copied into every CTA's shared memory).
@@ -158,6 +163,11 @@ struct __align__(1024) TcMlpSmem {
     uint32_t tmem;
     uint64_t mbar;
 };
+
+static_assert(sizeof(TcMlpImage) % 16 == 0, "the image is copied in 16-byte units");
+static_assert(offsetof(TcMlpSmem, a2) % 16 == 0 && offsetof(TcMlpSmem, a1) % 16 == 0,
+              "operands start on 16-byte boundaries (shared-memory descriptors)");
+static_assert(5 * (sizeof(TcMlpSmem) + 1024) > 228 * 1024, "at most 4 allocating CTAs per SM");
 
 // byte offset of element (row, k) in an operand of R rows (K-major, no swizzle)
 __host__ __device__ constexpr uint32_t kmaj_off(int R, int row, int k)
@@ -279,6 +289,7 @@ __device__ __forceinline__ bool tc_layer(TcMlpSmem &S, const uint8_t *a, const u
 // TPR = 2 (256 threads; warps w and w + 4 read the same TMEM lane quarter,
 // w % 4, and take columns 0..31 and 32..63 of its rows): half the serial
 // work per thread, for batches too small to fill the GPU with 128-row tiles.
+// (threadIdx.x & 96 is the warp's TMEM lane quarter, 32 * (warp % 4).)
 template <int TPR> __device__ __forceinline__ int tc_rowid() { return threadIdx.x & (kTcRows - 1); }
 template <int TPR> __device__ __forceinline__ int tc_half() { return TPR == 1 ? 0 : (int)(threadIdx.x >> 7); }
 
