@@ -323,6 +323,17 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
                 pg->ncol = (long long)dg.n[pg->p] * dg.n[pg->q];
                 pg->z0 = key.z0;
                 pg->dz = key.dz;
+                pg->side = nullptr;
+                pg->fork = pg->join = nullptr;
+                if (cudaStreamCreateWithFlags(&pg->side, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&pg->fork, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&pg->join, cudaEventDisableTiming) != cudaSuccess) {
+                    cudaGetLastError();
+                    if (pg->fork) cudaEventDestroy(pg->fork);
+                    if (pg->side) cudaStreamDestroy(pg->side);
+                    pg->side = nullptr;
+                    pg->fork = pg->join = nullptr;
+                }
                 g->plane = pg;
             }
             g->vconst = (ViewConst *)malloc((d.n_views > 0 ? d.n_views : 1) * sizeof(ViewConst));

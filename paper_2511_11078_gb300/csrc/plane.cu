@@ -488,6 +488,9 @@ void plane_free(PlaneGroup *pg)
         if (pg->pack[n].block2) cudaFree(pg->pack[n].block2);
         if (pg->pack[n].block) cudaFree(pg->pack[n].block);
     }
+    if (pg->join) cudaEventDestroy(pg->join);
+    if (pg->fork) cudaEventDestroy(pg->fork);
+    if (pg->side) cudaStreamDestroy(pg->side);
     delete pg;
 }
 

@@ -601,9 +601,24 @@ static spl_status forward_quad_t(const spl_geometry *g, const spl_basis_desc *b,
         spl_status s;
         const int v0 = plane_views(g, b, st, &s);
         if (s != SPL_OK) return s;
+        // the plane path (memory-latency bound) runs beside the march of the
+        // other views (arithmetic bound) when both have work: the two write
+        // disjoint rows of y
+        const bool overlap = v0 > 0 && v0 < dg.n_views && g->plane->side;
         if (v0 > 0) {
-            s = plane_forward(g, N, kahan, c, y, st);
+            cudaStream_t ps = st;
+            if (overlap) {
+                s = cuda_check(cudaEventRecord(g->plane->fork, st), "fork record");
+                if (s == SPL_OK) s = cuda_check(cudaStreamWaitEvent(g->plane->side, g->plane->fork, 0), "fork wait");
+                if (s != SPL_OK) return s;
+                ps = g->plane->side;
+            }
+            s = plane_forward(g, N, kahan, c, y, ps);
             if (s != SPL_OK) return s;
+            if (overlap) {
+                s = cuda_check(cudaEventRecord(g->plane->join, ps), "join record");
+                if (s != SPL_OK) return s;
+            }
         }
         const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
         for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
@@ -612,6 +627,10 @@ static spl_status forward_quad_t(const spl_geometry *g, const spl_basis_desc *b,
         for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
             k_forward_pviews<N, VM_GENERAL, DIRECT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, c, y, qr, kahan, ch);
         });
+        if (overlap) {
+            s = cuda_check(cudaStreamWaitEvent(st, g->plane->join, 0), "join wait");
+            if (s != SPL_OK) return s;
+        }
     } else {
         dim3 grid((dg.nu + 15) / 16, (dg.nv + 7) / 8, dg.n_views);
         k_forward_views<N, DIRECT><<<grid, 128, 0, st>>>(dg, c, y, qr, kahan);

@@ -55,6 +55,11 @@ struct PlaneGroup {
     long long ncol;            // n_p * n_q
     double z0, dz;             // b index coordinate of detector row v: z0 + v * dz
     PlanePack pack[4];         // per degree
+    // The forward runs the plane path on `side` beside the march of the other
+    // views (fork and join through the events); NULL when they could not be
+    // created (the two then run one after the other).
+    cudaStream_t side;
+    cudaEvent_t fork, join;
 };
 
 // Record `msg` as the calling thread's last error and return `st`.
