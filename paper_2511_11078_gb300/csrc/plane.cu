@@ -278,8 +278,9 @@ __global__ void __launch_bounds__(256) k_plane_ytrans(const float *__restrict__ 
     }
 }
 
-// c(col, lb) = sum_(v in vr[lb]) wz[v][lb - lb0[v]] * T[col][v]  (every coefficient written)
-template <int N>
+// c(col, lb) = sum_(v in vr[lb]) wz[v][lb - lb0[v]] * T[col][v]  (every
+// coefficient written; ADD: added to what c holds)
+template <int N, bool ADD>
 __global__ void __launch_bounds__(256) k_plane_zadj(PlaneCall pc, const float *__restrict__ T, const int *lb0,
                                                     const float *wz, const int *vr, float *__restrict__ c)
 {
@@ -294,7 +295,8 @@ __global__ void __launch_bounds__(256) k_plane_zadj(PlaneCall pc, const float *_
         const int i = lb - lb0[v];
         if (i >= 0 && i <= N) s = fmaf(wz[v * (N + 1) + i], __ldg(T + col * pc.nv + v), s);
     }
-    c[ip * pc.st_p + iq * pc.st_q + (long long)lb * pc.st_b] = s;
+    float *dst = c + (ip * pc.st_p + iq * pc.st_q + (long long)lb * pc.st_b);
+    *dst = ADD ? *dst + s : s;
 }
 
 // ---------------------------------------------------------------- host side
@@ -512,8 +514,9 @@ static spl_status plane_forward_n(const spl_geometry *g, int kahan, const float 
     return cuda_check(cudaGetLastError(), "plane forward launch");
 }
 
+// the adjoint's first stage: y transposed per view, then T = column gather
 template <int N>
-static spl_status plane_adjoint_n(const spl_geometry *g, const float *y, float *c, cudaStream_t st)
+static spl_status plane_adjoint_t_n(const spl_geometry *g, const float *y, cudaStream_t st)
 {
     const PlaneGroup &pg = *g->plane;
     const PlanePack &pk = pg.pack[N];
@@ -523,9 +526,26 @@ static spl_status plane_adjoint_n(const spl_geometry *g, const float *y, float *
     const unsigned blocks = (unsigned)((pg.ncol + kPlaneWarps - 1) / kPlaneWarps);
     k_plane_gather<true, false><<<blocks, 32 * kPlaneWarps, 0, st>>>(pg.ncol, pk.col_ptr, pk.col_row, pk.col_val, pk.yt,
                                                                      pk.T, pc.nv, pc.nu, nullptr);
-    const long long nc = pc.ncol * pc.n_b;
-    k_plane_zadj<N><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(pc, pk.T, pk.lb0, pk.wz, pk.vr, c);
     return cuda_check(cudaGetLastError(), "plane adjoint launch");
+}
+
+// the adjoint's second stage: c from T (written, or added with ADD)
+template <int N, bool ADD>
+static spl_status plane_adjoint_c_n(const spl_geometry *g, float *c, cudaStream_t st)
+{
+    const PlanePack &pk = g->plane->pack[N];
+    const PlaneCall pc = call_of(g);
+    const long long nc = pc.ncol * pc.n_b;
+    k_plane_zadj<N, ADD><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(pc, pk.T, pk.lb0, pk.wz, pk.vr, c);
+    return cuda_check(cudaGetLastError(), "plane adjoint launch");
+}
+
+template <int N>
+static spl_status plane_adjoint_n(const spl_geometry *g, const float *y, float *c, cudaStream_t st)
+{
+    spl_status s = plane_adjoint_t_n<N>(g, y, st);
+    if (s != SPL_OK) return s;
+    return plane_adjoint_c_n<N, false>(g, c, st);
 }
 
 spl_status plane_forward(const spl_geometry *g, int degree, int kahan, const float *c, float *y, cudaStream_t st)
@@ -545,6 +565,26 @@ spl_status plane_adjoint(const spl_geometry *g, int degree, const float *y, floa
     case 1: return plane_adjoint_n<1>(g, y, c, st);
     case 2: return plane_adjoint_n<2>(g, y, c, st);
     default: return plane_adjoint_n<3>(g, y, c, st);
+    }
+}
+
+spl_status plane_adjoint_t(const spl_geometry *g, int degree, const float *y, cudaStream_t st)
+{
+    switch (degree) {
+    case 0: return plane_adjoint_t_n<0>(g, y, st);
+    case 1: return plane_adjoint_t_n<1>(g, y, st);
+    case 2: return plane_adjoint_t_n<2>(g, y, st);
+    default: return plane_adjoint_t_n<3>(g, y, st);
+    }
+}
+
+spl_status plane_adjoint_add(const spl_geometry *g, int degree, float *c, cudaStream_t st)
+{
+    switch (degree) {
+    case 0: return plane_adjoint_c_n<0, true>(g, c, st);
+    case 1: return plane_adjoint_c_n<1, true>(g, c, st);
+    case 2: return plane_adjoint_c_n<2, true>(g, c, st);
+    default: return plane_adjoint_c_n<3, true>(g, c, st);
     }
 }
 

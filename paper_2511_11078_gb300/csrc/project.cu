@@ -657,8 +657,21 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
         v0 = plane_views(g, b, st, &s);
         if (s != SPL_OK) return s;
     }
-    if (v0 > 0) {
-        // the plane path writes every coefficient; the other views add
+    // With the scatter form the plane path's gather (T, memory-latency
+    // bound) runs on the geometry's side stream beside the march's scatter
+    // into the cleared c (arithmetic bound); after the join, T's
+    // contribution is added to c.  Otherwise the plane path writes every
+    // coefficient first and the other views add.
+    const bool overlap = dg.kind == SPL_PARALLEL && dg.n_rays > 0 && v0 > 0 && v0 < dg.n_views && form != SPL_ADJ_GATHER &&
+                         g->plane->side;
+    if (overlap) {
+        s = cuda_check(cudaEventRecord(g->plane->fork, st), "fork record");
+        if (s == SPL_OK) s = cuda_check(cudaStreamWaitEvent(g->plane->side, g->plane->fork, 0), "fork wait");
+        if (s == SPL_OK) s = plane_adjoint_t(g, N, y, g->plane->side);
+        if (s == SPL_OK) s = cuda_check(cudaEventRecord(g->plane->join, g->plane->side), "join record");
+        if (s == SPL_OK) s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
+        if (s != SPL_OK) return s;
+    } else if (v0 > 0) {
         s = plane_adjoint(g, N, y, c, st);
         if (s != SPL_OK) return s;
     } else if (dg.kind == SPL_RAYS || form != SPL_ADJ_GATHER) {
@@ -680,6 +693,11 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
             for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
                 k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
             });
+            if (overlap) {
+                s = cuda_check(cudaStreamWaitEvent(st, g->plane->join, 0), "join wait");
+                if (s == SPL_OK) s = plane_adjoint_add(g, N, c, st);
+                if (s != SPL_OK) return s;
+            }
         } else {
             k_adjoint_views_scatter<N><<<dim3(gx, gy, dg.n_views), 128, 0, st>>>(dg, y, c, qr);
         }

@@ -88,6 +88,11 @@ bool plane_ready(spl_geometry *g, int degree, cudaStream_t st, spl_status *err);
 spl_status plane_forward(const spl_geometry *g, int degree, int kahan, const float *c, float *y, cudaStream_t st);
 // writes every coefficient (the other views' scatter adds after it)
 spl_status plane_adjoint(const spl_geometry *g, int degree, const float *y, float *c, cudaStream_t st);
+// The adjoint's two stages: T (the column gather of y) into the pack's
+// scratch, then c += the b-resampled T (the forward of the same geometry
+// must not run in between).
+spl_status plane_adjoint_t(const spl_geometry *g, int degree, const float *y, cudaStream_t st);
+spl_status plane_adjoint_add(const spl_geometry *g, int degree, float *c, cudaStream_t st);
 void plane_free(PlaneGroup *pg);
 
 // Footprint tables of the views of a parallel geometry (table.cu), built on
