@@ -144,7 +144,10 @@ typedef struct {
 /* Build a device-resident geometry (Eq. 1) from `desc`.  Validates every
  * direction and position (finite, nonzero direction) and the grid
  * (1 <= n <= 2048 per axis, nx*ny*nz < 2^31).  Allocates device memory owned
- * by the returned object.  Uses the current CUDA device.
+ * by the returned object; a parallel geometry with slice-separable views also
+ * owns a CUDA stream and two events on which spl_forward / spl_adjoint run
+ * the plane path beside the march of the other views (joined back into the
+ * caller's stream before they return).  Uses the current CUDA device.
  * Errors: SPL_ERR_ARG, SPL_ERR_NONFINITE, SPL_ERR_UNSUPPORTED, SPL_ERR_OOM,
  * SPL_ERR_CUDA; *out is NULL on error. */
 spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geometry **out);
