@@ -146,8 +146,9 @@ typedef struct {
  * (1 <= n <= 2048 per axis, nx*ny*nz < 2^31).  Allocates device memory owned
  * by the returned object; a parallel geometry with slice-separable views also
  * owns a CUDA stream and two events on which spl_forward / spl_adjoint run
- * the plane path beside the march of the other views (joined back into the
- * caller's stream before they return).  Uses the current CUDA device.
+ * the plane path beside the march of the other views (the caller's stream
+ * waits for it, so each call stays one ordered operation on that stream).
+ * Uses the current CUDA device.
  * Errors: SPL_ERR_ARG, SPL_ERR_NONFINITE, SPL_ERR_UNSUPPORTED, SPL_ERR_OOM,
  * SPL_ERR_CUDA; *out is NULL on error. */
 spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geometry **out);
