@@ -476,7 +476,11 @@ def run_ours(args):
     value = replica_value(ws, contrib_step, ms)
 
     # end to end through the C ABI with host buffers: H2D of c and y from
-    # pinned memory, A c and A^T y, D2H of both results
+    # pinned memory, A c and A^T y, D2H of both results, every step.  The
+    # copies run on a copy stream: y's upload overlaps A, the download of
+    # A c overlaps A^T; each step's uploads wait for the previous step's
+    # downloads, which wait for its A and A^T (no buffer is overwritten
+    # while in use).
     c_host = torch.tensor(wl.coeffs).pin_memory()
     y_host = y.cpu().pin_memory()
     out_y = torch.empty_like(y_host).pin_memory()
@@ -484,19 +488,40 @@ def run_ours(args):
     c_dev = torch.empty_like(c_true)
     y_dev = torch.empty_like(y)
     e2e_steps = max(3, min(args.steps, 5))
+    copy_s = torch.cuda.Stream()
+    ev = {k: torch.cuda.Event() for k in ("c", "y", "a", "at")}
     torch.cuda.synchronize()
     e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_start.record(stream)
+    copy_s.wait_event(e_start)
     for _ in range(e2e_steps):
-        c_dev.copy_(c_host, non_blocking=True)
-        y_dev.copy_(y_host, non_blocking=True)
+        with torch.cuda.stream(copy_s):
+            c_dev.copy_(c_host, non_blocking=True)
+            ev["c"].record(copy_s)
+            y_dev.copy_(y_host, non_blocking=True)
+            ev["y"].record(copy_s)
+        stream.wait_event(ev["c"])
         proj.forward(c_dev, out=cg.q)
+        ev["a"].record(stream)
+        stream.wait_event(ev["y"])
         proj.adjoint(y_dev, out=cg.s)
-        out_y.copy_(cg.q, non_blocking=True)
-        out_c.copy_(cg.s, non_blocking=True)
+        ev["at"].record(stream)
+        with torch.cuda.stream(copy_s):
+            copy_s.wait_event(ev["a"])
+            out_y.copy_(cg.q, non_blocking=True)
+            copy_s.wait_event(ev["at"])
+            out_c.copy_(cg.s, non_blocking=True)
+    stream.wait_stream(copy_s)
     e_stop.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e_start.elapsed_time(e_stop) / e2e_steps
+    # the downloaded results against the same operators on device buffers
+    ref_y, ref_c = torch.empty_like(y), torch.empty_like(c_true)
+    proj.forward(c_true, out=ref_y)
+    proj.adjoint(y, out=ref_c)
+    torch.cuda.synchronize()
+    e2e_diff = max(float((out_y.to(dev) - ref_y).norm() / ref_y.norm()),
+                   float((out_c.to(dev) - ref_c).norm() / ref_c.norm()))
     h2d = c_host.numel() * 4 + y_host.numel() * 4
     d2h = out_y.numel() * 4 + out_c.numel() * 4
 
@@ -544,7 +569,7 @@ def run_ours(args):
             "A_ms": fwd, "AT_ms": adj,
             "A_gcontrib_s": pairs / (fwd * 1e-3) / 1e9, "AT_gcontrib_s": pairs / (adj * 1e-3) / 1e9,
             "e2e": {"value": replica_value(ws, contrib_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "result_rel_diff": e2e_diff},
             "gpu_launches": args.steps * launches_step,
             "view_classes": per_class,
             "plane_build_s": plane_build_s,
