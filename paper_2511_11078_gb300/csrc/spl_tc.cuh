@@ -2,14 +2,15 @@
 // tensor cores: tcgen05.mma with operands in shared memory and the FP32
 // accumulator in tensor memory (TMEM).
 //
-// A CTA of 128 threads evaluates tiles of 128 rows (one row per thread).
-// Each layer is one M=128 x N=64 product: the threads write their rows of
-// the A operand (BF16) to shared memory, one thread issues the MMAs, the
-// tensor core accumulates the 128 x 64 FP32 result in 64 TMEM columns, and
-// every thread reads its row back with tcgen05.ld (TMEM lane = row), applies
-// SiLU and writes the next layer's A row.  The MMAs take no issue slots of
-// the other threads and no registers: what is left to the threads is SiLU,
-// the BF16 packing and the 64 -> 1 output layer.
+// A CTA evaluates tiles of 128 rows, with one thread per row (128 threads)
+// or two (256 threads, each taking half of the row's 64 columns).  Each
+// layer is one M=128 x N=64 product: the threads write their parts of the A
+// operand (BF16) to shared memory, one thread issues the MMAs, the tensor
+// core accumulates the 128 x 64 FP32 result in 64 TMEM columns, and every
+// thread reads its part back with tcgen05.ld (TMEM lane = row), applies
+// SiLU and writes the next layer's A operand.  The MMAs take no issue slots
+// of the other threads and no registers: what is left to the threads is
+// SiLU, the BF16 packing and the 64 -> 1 output layer.
 //
 // Precision contract (the one the oracle emulates): layers 2 and 3 multiply
 // BF16 weights with the BF16-rounded activations, accumulating in FP32;
