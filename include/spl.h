@@ -27,13 +27,20 @@
  *     then launches nothing.
  *   - spl_forward, spl_adjoint, spl_footprint, spl_dot_f64 and the CG updates
  *     allocate no memory.  Objects (geometry, MLP) own the device memory they
- *     allocate at creation and free it on destroy.
+ *     allocate at creation (and, for a geometry, in spl_prepare) and free it
+ *     on destroy.  A basis whose structures a geometry has not built
+ *     (spl_prepare) is refused by spl_forward / spl_adjoint with
+ *     SPL_ERR_STATE.
  *   - Errors are returned as spl_status values; the library never aborts.
  *     spl_last_error() gives a message for the last failing call of the
  *     calling thread.
  *   - Kernels never spin on a condition another agent sets; every loop has a
  *     fixed bound.  A kernel that reaches a bound sets the error flag of the
- *     geometry it ran on; spl_geometry_status() reads and clears it.
+ *     geometry it ran on; spl_geometry_status() reads and clears it.  The
+ *     tensor-core kernels wait for their MMAs with a bounded poll; a wait
+ *     that gives up sets the error flag of the geometry (projector) or of
+ *     the network (spl_footprint, spl_mlp_eval, training), reported as
+ *     SPL_ERR_TIMEOUT by spl_geometry_status() / spl_mlp_status().
  */
 #ifndef SPL_H
 #define SPL_H
@@ -50,7 +57,8 @@ typedef enum {
     SPL_ERR_STEPCAP = 4,     /* a kernel reached one of its loop bounds         */
     SPL_ERR_OOM = 5,         /* device allocation failed (object creation only) */
     SPL_ERR_STATE = 6,       /* object in the wrong state for this call         */
-    SPL_ERR_UNSUPPORTED = 7  /* size or option outside what the kernels handle  */
+    SPL_ERR_UNSUPPORTED = 7, /* size or option outside what the kernels handle  */
+    SPL_ERR_TIMEOUT = 8      /* a bounded tensor-core completion wait gave up   */
 } spl_status;
 
 /* geometry kinds (Eq. 1 lines) */
@@ -68,10 +76,10 @@ enum { SPL_FP_QUAD = 0, SPL_FP_MLP = 1, SPL_FP_DIRECT = 2, SPL_FP_TABLE = 3 };
  * (i - M) h e1 + (j - M) h e2, i, j = 0..2M, M = ceil(sqrt(3)(n+1)/(2h)) + 1,
  * and a pair's footprint is the bilinear interpolation of the table at the
  * pair's offset (second-order accurate in h), over the exact pair set.  The
- * tables (4 (2M+1)^2 bytes per view, 198 KB for cubic) are built on the
- * first call per degree (device allocation and kernels, then a
- * synchronisation).  Forward and adjoint use the same table values; other
- * geometry kinds return SPL_ERR_UNSUPPORTED.  spl_footprint with this mode,
+ * tables (4 (2M+1)^2 bytes per view, 198 KB for cubic) are built by
+ * spl_prepare (device allocation and kernels, then a synchronisation).
+ * Forward and adjoint use the same table values; other geometry kinds
+ * return SPL_ERR_UNSUPPORTED.  spl_footprint with this mode,
  * or with SPL_FP_DIRECT, evaluates the exact footprint. */
 /* adjoint forms for view geometries: SPL_ADJ_AUTO picks the faster one on
  * this GPU (the scatter form); SPL_ADJ_GATHER walks coefficient bricks and
@@ -100,7 +108,11 @@ typedef struct spl_mlp spl_mlp;           /* opaque, library-owned */
  *   or the line through the source and q (cone); ray index
  *   r = (k*nv + iv)*nu + iu.  All arrays are host FP64, read during the call
  *   and copied to the device; the caller keeps ownership.
- *   Grid: coefficient (i, j, l) sits at origin + (i, j, l), lattice step 1. */
+ *   Grid: coefficient (i, j, l) sits at origin + (i, j, l), lattice step 1
+ *   (Sec. 2.1 places the bases on the unit lattice).  A grid of step h is
+ *   the same transform in units of h: divide every position (origin,
+ *   sources, detector centres and axes, ray points) by h and multiply the
+ *   forward projection (and the adjoint) by h. */
 typedef struct {
     int kind;
     int nx, ny, nz;
@@ -161,8 +173,10 @@ long long spl_geometry_rays(const spl_geometry *g);
 long long spl_geometry_coeffs(const spl_geometry *g);
 
 /* Synchronise `stream`, then read and clear the geometry's device error flag.
- * Returns SPL_ERR_STEPCAP if a kernel that ran on `g` reached a loop bound
- * since the last call, SPL_ERR_CUDA on a CUDA error, else SPL_OK. */
+ * Returns SPL_ERR_TIMEOUT if a tensor-core wait of the learned-footprint
+ * projector gave up, else SPL_ERR_STEPCAP if a kernel that ran on `g`
+ * reached a loop bound since the last call, SPL_ERR_CUDA on a CUDA error,
+ * else SPL_OK. */
 spl_status spl_geometry_status(const spl_geometry *g, void *stream);
 
 /* Slice-separable views.  A parallel view is slice-separable along axis b
@@ -183,16 +197,22 @@ spl_status spl_geometry_status(const spl_geometry *g, void *stream);
  * a forward then resamples c along b into S and gathers the rows of G;
  * an adjoint gathers the columns of G and resamples back along b, with no
  * atomics.
- * spl_prepare builds the plane matrices for basis->degree (one-time device
- * allocation and kernels on `stream`, then a synchronisation).
- * spl_forward / spl_adjoint call it on first use.  Geometries without
- * separable views, basis->separable == SPL_SEP_OFF and the MLP footprint do
- * not use it.  The plane buffers include the scratch of S and of its
- * adjoint, so calls on one geometry must not overlap on the GPU.
- * Returns SPL_OK also when the geometry has no separable views or the basis
- * does not use the path.  Errors: SPL_ERR_ARG; SPL_ERR_OOM (the path stays
- * off for this geometry and degree: spl_forward / spl_adjoint then walk
- * those views like the others and succeed); SPL_ERR_CUDA. */
+ * spl_prepare builds what spl_forward / spl_adjoint need for `basis` on
+ * this geometry, which they never allocate themselves: the plane matrices
+ * for basis->degree (exact footprint, SPL_SEP_AUTO, geometries with a
+ * separable group), or the footprint tables of SPL_FP_TABLE (see there).
+ * One-time device allocation and kernels on `stream`, then a
+ * synchronisation; later calls for the same degree return at once.  Until
+ * it has run, spl_forward / spl_adjoint refuse such a basis with
+ * SPL_ERR_STATE.  Geometries without separable views,
+ * basis->separable == SPL_SEP_OFF and the MLP footprint need nothing.  The
+ * plane buffers include the scratch of S and of its adjoint, so calls on
+ * one geometry must not overlap on the GPU.
+ * Errors: SPL_ERR_ARG; SPL_ERR_OOM (plane matrices: the path stays off for
+ * this geometry and degree, and spl_forward / spl_adjoint then walk those
+ * views like the others and succeed; tables: SPL_FP_TABLE stays
+ * unavailable); SPL_ERR_UNSUPPORTED (SPL_FP_TABLE on a cone or ray
+ * geometry); SPL_ERR_CUDA. */
 spl_status spl_prepare(spl_geometry *g, const spl_basis_desc *basis, void *stream);
 
 /* ---------------------------------------------------------------- operators */
@@ -204,9 +224,12 @@ spl_status spl_prepare(spl_geometry *g, const spl_basis_desc *basis, void *strea
  * construction), and each basis the ray crosses adds c_k * Pphi(w, s - X(k))
  * once.  Slice-separable views of a parallel geometry go through the plane
  * matrices instead (see spl_prepare), with the same footprint values.
+ *   Cone views: every ray is walked with the general (three-factor) form
+ *   of the march, so a ray's values do not depend on its direction class.
  *   c_dev: [nz][ny][nx] float32 (read only);  y_dev: n_rays float32,
  *   overwritten.  Errors: SPL_ERR_ARG (null pointer, degree, mode, missing or
- *   mismatched MLP), SPL_ERR_CUDA (launch failure). */
+ *   mismatched MLP), SPL_ERR_STATE (the basis needs spl_prepare first),
+ *   SPL_ERR_CUDA (launch failure). */
 spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *basis, const float *c_dev, float *y_dev,
                        void *stream);
 
@@ -240,6 +263,18 @@ spl_status spl_count_pairs(const spl_geometry *g, int degree, unsigned long long
  *   canonical features, multiplied by the exact support indicator. */
 spl_status spl_footprint(const spl_basis_desc *basis, long long count, const float *omega_dev, const float *p_dev,
                          float *out_dev, void *stream);
+
+/* The frame of H_w in which spl_features measures offsets, for `count`
+ * directions (host arrays, FP64 [count][3]; any nonzero length, normalised
+ * here).  Algorithm 2 fixes only u perpendicular to w and v = u x w; the
+ * library's frame is continuous over the chamber 0 <= w1 <= w2 <= w3 of
+ * the direction's signed permutation G (phi is invariant under G): there
+ * u_c = normalize(e1 x Gw), v_c = u_c x Gw, and the outputs are
+ * u = G^T u_c, v = G^T v_c (orthonormal, perpendicular to w,
+ * v = det(G) u x w).  spl_features' last two values are <p, u> sqrt(3)/W
+ * and <p, v> sqrt(3)/W.  Synchronous host call, no device work.
+ * Errors: SPL_ERR_ARG, SPL_ERR_NONFINITE (zero or non-finite direction). */
+spl_status spl_frame(long long count, const double *omega, double *u, double *v);
 
 /* MLP input features of (w, p) (float32 [count][5]): the signed permutation
  * G that maps w into the chamber 0 <= w1 <= w2 <= w3 (phi is invariant under
@@ -288,8 +323,30 @@ spl_status spl_mlp_get_params(const spl_mlp *m, float *host_params);
  * on the tcgen05 tensor cores (128-row tiles, BF16 operands, FP32
  * accumulation in tensor memory; layer 1 and the biases at FP32 accuracy).
  * A tensor-core completion wait that exceeds its bound (not expected)
- * leaves NaN in the rows of the affected tile. */
+ * leaves NaN in the rows of the affected tile and sets the network's error
+ * flag (spl_mlp_status). */
 spl_status spl_mlp_eval(const spl_mlp *m, long long count, const float *feat_dev, float *out_dev, void *stream);
+
+/* Synchronise `stream`, then read and clear the network's device error
+ * flag: SPL_ERR_TIMEOUT if a tensor-core wait of spl_footprint
+ * (SPL_FP_MLP), spl_mlp_eval, spl_mlp_grad or spl_mlp_train_step on this
+ * network gave up since the last call, else SPL_OK (SPL_ERR_CUDA on a CUDA
+ * error). */
+spl_status spl_mlp_status(const spl_mlp *m, void *stream);
+
+/* Checkpoint of the training state (Algorithm 1), a little-endian binary
+ * file: the 8 bytes "SPLMLP2\0"; int32 version (2), degree, parameter count
+ * (SPL_MLP_PARAMS), input width (5), hidden width (64), hidden layers (3),
+ * dtype (0 = float32), Adam step count; uint64 initialisation seed; then
+ * the float32 master parameters, Adam first moments and Adam second
+ * moments (SPL_MLP_PARAMS values each).  spl_mlp_load restores all of it
+ * (and refreshes the BF16 copies), so training resumes exactly where the
+ * saved network stopped.  Both synchronise the device.  spl_mlp_load
+ * refuses a file of another degree or shape (SPL_ERR_ARG) and non-finite
+ * values (SPL_ERR_NONFINITE); I/O failures return SPL_ERR_ARG with the
+ * reason in spl_last_error(). */
+spl_status spl_mlp_save(const spl_mlp *m, const char *path);
+spl_status spl_mlp_load(spl_mlp *m, const char *path);
 
 /* Gradient of L = (1/B) sum_b (f_theta(x_b) - y_b)^2 (Algorithm 1's loss)
  * with respect to the master parameters, float32 [SPL_MLP_PARAMS] into
@@ -327,7 +384,10 @@ spl_status spl_dot_f64(long long n, const float *a_dev, const float *b_dev, doub
  * GPU that loads the library until the process exits) instead of a caller
  * workspace.  The first call on a device looks up that array's device
  * address (with the device current) and caches it; make that first call
- * before any stream capture.  Every call shares the array, which keeps the
+ * before any stream capture.  The cached address belongs to the device's
+ * primary context (the one the CUDA runtime uses): calls under another
+ * context, or after cudaDeviceReset, are not supported.  Every call shares
+ * the array, which keeps the
  * last call's partials (each call overwrites all of them, nothing needs
  * clearing); calls that overlap on the GPU race on it.
  * n: 0 .. SPL_DOT_NOALLOC_MAX_N elements (the partial count does not depend
@@ -346,6 +406,20 @@ spl_status spl_cg_step_p(long long n, float *p_dev, const float *s_dev, const do
                          const double *den_dev, void *stream);
 
 /* ---------------------------------------------------------------- misc */
+
+/* FP32 throughput probe (measurement support, no counterpart in the paper):
+ * launches blocks_per_sm x (SM count) blocks of 256 threads, each thread
+ * running `iters` x 4 x 16 fused multiply-adds on 16 independent chains,
+ * as scalar FMAs (packed = 0) or as packed FP32x2 FMAs (packed != 0,
+ * __ffma2_rn: two per instruction).  *flop receives the FP32 operation
+ * count of the launch (2 per multiply-add), to be divided by the launch's
+ * duration measured on `stream`.  out_dev: one float32 of device memory
+ * (written only in a case that never happens; it keeps the chains live).
+ * Errors: SPL_ERR_ARG, SPL_ERR_CUDA. */
+spl_status spl_fp32_probe(int packed, int blocks_per_sm, int iters, float *out_dev, double *flop, void *stream);
+/* Number of SMs of the current device. */
+int spl_sm_count(void);
+
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *spl_last_error(void);

@@ -88,6 +88,7 @@ def _load():
             lib.orc_adjoint.argtypes = [C.c_int, _ip, _dp, _dp, G, _dp]
             lib.orc_adjoint_at.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_longlong, _llp, _dp, _llp, C.c_int]
             lib.orc_adjoint_subset.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_longlong, _llp, _dp, _llp, C.c_int]
+            lib.orc_adjoint_at_views.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_longlong, _llp, _dp, _llp, C.c_int]
             lib.orc_forward_segmented.argtypes = [C.c_int, _ip, _dp, _dp, G, C.c_longlong, _llp, _dp, C.c_int]
             lib.orc_eval_spline.restype = C.c_double
             lib.orc_eval_spline.argtypes = [C.c_int, _ip, _dp, _dp, _dp]
@@ -273,6 +274,22 @@ def adjoint_at(n, dims, origin, y, geom: Geometry, kidx, nthreads: int = 0):
     pairs = np.zeros(k.shape[0], dtype=np.int64)
     _load().orc_adjoint_at(int(n), dp, op, yp, geom.ptr, k.shape[0], kp, out.ctypes.data_as(_dp),
                            pairs.ctypes.data_as(_llp), int(nthreads))
+    return out, pairs
+
+
+def adjoint_at_views(n, dims, origin, y, geom: Geometry, kidx, nthreads: int = 0):
+    """Entries `kidx` of A^T y for a view geometry, visiting per view only
+    the detector window of each coefficient's support (the same sum as
+    adjoint_at, fast enough for full-size detectors)."""
+    if geom.kind == "rays":
+        raise ValueError("adjoint_at_views needs a view geometry")
+    keep, dp, op = _grid(dims, origin)
+    yy, yp = _d(np.asarray(y).reshape(-1))
+    k, kp = _ll(kidx)
+    out = np.zeros(k.shape[0])
+    pairs = np.zeros(k.shape[0], dtype=np.int64)
+    _load().orc_adjoint_at_views(int(n), dp, op, yp, geom.ptr, k.shape[0], kp, out.ctypes.data_as(_dp),
+                                 pairs.ctypes.data_as(_llp), int(nthreads))
     return out, pairs
 
 

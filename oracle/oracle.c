@@ -406,14 +406,27 @@ void orc_adjoint(int n, const int *dims, const double *org, const double *y, con
 
 /* Adjoint restricted to a subset of rays: c_k = sum_{i} y_i Pphi(w_{r_i},
  * s_{r_i} - k) over the listed rays (the rows of Eq. 6 they index); same
- * definition as orc_adjoint, parallel over rays with one private
- * accumulation buffer per thread.  Overwrites c; pairs[0] = pair count. */
+ * definition as orc_adjoint, parallel over rays.  Grids of up to 2^24
+ * coefficients use one private accumulation buffer per thread; larger ones
+ * add into c directly with atomic adds (a private copy of a 512^3 grid per
+ * thread would not fit in host memory).  Overwrites c; pairs[0] = pair
+ * count. */
+static void adj_visit_atomic(void *vctx, long long kidx, const int *k, const double *p)
+{
+    (void)k;
+    adj_ctx *x = (adj_ctx *)vctx;
+    const double v = x->yr * orc_footprint(x->n, x->w, p);
+#pragma omp atomic
+    x->c[kidx] += v;
+}
+
 void orc_adjoint_subset(int n, const int *dims, const double *org, const double *y, const orc_geom *g,
                         long long count, const long long *rays, double *c, long long *pairs, int nthreads)
 {
     long long nk = (long long)dims[0] * dims[1] * dims[2];
     memset(c, 0, sizeof(double) * nk);
     long long np = 0;
+    const int shared = nk > (1LL << 24);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -421,21 +434,23 @@ void orc_adjoint_subset(int n, const int *dims, const double *org, const double 
 #endif
 #pragma omp parallel reduction(+ : np)
     {
-        double *priv = (double *)calloc(nk, sizeof(double));
+        double *priv = shared ? c : (double *)calloc(nk, sizeof(double));
         fwd_ctx cnt = {n, NULL, NULL, 0.0, 0};
 #pragma omp for schedule(dynamic, 4)
         for (long long i = 0; i < count; ++i) {
             double s[3], w[3];
             orc_geom_ray(g, rays[i], s, w);
             adj_ctx x = {n, w, y[i], priv};
-            for_each_pair(n, dims, org, s, w, adj_visit, &x);
+            for_each_pair(n, dims, org, s, w, shared ? adj_visit_atomic : adj_visit, &x);
             cnt.w = w;
             for_each_pair(n, dims, org, s, w, count_visit, &cnt);
         }
         np += cnt.count;
+        if (!shared) {
 #pragma omp critical
-        for (long long k = 0; k < nk; ++k) c[k] += priv[k];
-        free(priv);
+            for (long long k = 0; k < nk; ++k) c[k] += priv[k];
+            free(priv);
+        }
     }
     if (pairs) pairs[0] = np;
 }
@@ -473,6 +488,121 @@ void orc_adjoint_at(int n, const int *dims, const double *org, const double *y, 
             if (!ok || !(hi > lo)) continue;
             sum += y[r] * orc_footprint(n, w, p);
             np += 1;
+        }
+        out[i] = sum;
+        if (pairs) pairs[i] = np;
+    }
+}
+
+/* Adjoint at selected coefficients of a view geometry, visiting for each
+ * coefficient and view only the detector pixels whose ray can meet the
+ * coefficient's support cube: the pixel bounding box (one pixel of margin)
+ * of the 8 cube corners projected onto the detector plane along the view's
+ * direction (parallel) or through its source (cone).  The support is
+ * convex, so every ray that meets it passes through the hull of the
+ * projected corners; a corner at or behind the source plane keeps the whole
+ * detector.  Each candidate ray then gets the same exact pair test and
+ * footprint as orc_adjoint_at, so the result is the same sum (for full-size
+ * sampled checks where looping over every ray per coefficient is too slow).
+ */
+static int view_pixel_window(const orc_geom *g, int v, const double *lo, const double *hi, int *u0, int *u1,
+                             int *v0, int *v1)
+{
+    const double *dc = g->det_c + 3 * v, *du = g->det_u + 3 * v, *dv = g->det_v + 3 * v;
+    const double *src = g->dir_or_src + 3 * v;
+    double nrm[3] = {du[1] * dv[2] - du[2] * dv[1], du[2] * dv[0] - du[0] * dv[2], du[0] * dv[1] - du[1] * dv[0]};
+    /* (a, b) of a point P on the plane: solve the 2x2 normal equations of
+       P - dc = a du + b dv */
+    const double guu = du[0] * du[0] + du[1] * du[1] + du[2] * du[2];
+    const double gvv = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+    const double guv = du[0] * dv[0] + du[1] * dv[1] + du[2] * dv[2];
+    const double det = guu * gvv - guv * guv;
+    if (!(det > 0.0)) return 0;
+    double amin = INFINITY, amax = -INFINITY, bmin = INFINITY, bmax = -INFINITY;
+    for (int corner = 0; corner < 8; ++corner) {
+        const double x[3] = {(corner & 1) ? hi[0] : lo[0], (corner & 2) ? hi[1] : lo[1], (corner & 4) ? hi[2] : lo[2]};
+        double P[3];
+        if (g->kind == 1) {
+            const double den = src[0] * nrm[0] + src[1] * nrm[1] + src[2] * nrm[2];
+            if (den == 0.0) return 0;
+            const double t = ((x[0] - dc[0]) * nrm[0] + (x[1] - dc[1]) * nrm[1] + (x[2] - dc[2]) * nrm[2]) / den;
+            for (int d = 0; d < 3; ++d) P[d] = x[d] - t * src[d];
+        } else {
+            const double num = (dc[0] - src[0]) * nrm[0] + (dc[1] - src[1]) * nrm[1] + (dc[2] - src[2]) * nrm[2];
+            const double den = (x[0] - src[0]) * nrm[0] + (x[1] - src[1]) * nrm[1] + (x[2] - src[2]) * nrm[2];
+            if (!(num * den > 0.0)) return 0; /* corner on or behind the source plane */
+            const double lam = num / den;
+            for (int d = 0; d < 3; ++d) P[d] = src[d] + lam * (x[d] - src[d]);
+        }
+        const double r[3] = {P[0] - dc[0], P[1] - dc[1], P[2] - dc[2]};
+        const double ru = r[0] * du[0] + r[1] * du[1] + r[2] * du[2];
+        const double rv = r[0] * dv[0] + r[1] * dv[1] + r[2] * dv[2];
+        const double a = (gvv * ru - guv * rv) / det, b = (guu * rv - guv * ru) / det;
+        if (a < amin) amin = a;
+        if (a > amax) amax = a;
+        if (b < bmin) bmin = b;
+        if (b > bmax) bmax = b;
+    }
+    const double cu = 0.5 * (g->nu - 1), cv = 0.5 * (g->nv - 1);
+    double fu0 = floor(amin + cu) - 1.0, fu1 = ceil(amax + cu) + 1.0;
+    double fv0 = floor(bmin + cv) - 1.0, fv1 = ceil(bmax + cv) + 1.0;
+    if (fu0 < 0.0) fu0 = 0.0;
+    if (fv0 < 0.0) fv0 = 0.0;
+    if (fu1 > g->nu - 1) fu1 = g->nu - 1;
+    if (fv1 > g->nv - 1) fv1 = g->nv - 1;
+    *u0 = (int)fu0;
+    *u1 = (int)fu1;
+    *v0 = (int)fv0;
+    *v1 = (int)fv1;
+    return 1;
+}
+
+void orc_adjoint_at_views(int n, const int *dims, const double *org, const double *y, const orc_geom *g,
+                          long long count, const long long *kidx, double *out, long long *pairs, int nthreads)
+{
+    const double W = 0.5 * (n + 1);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long long i = 0; i < count; ++i) {
+        long long kk = kidx[i];
+        int kx = (int)(kk % dims[0]), ky = (int)((kk / dims[0]) % dims[1]), kz = (int)(kk / ((long long)dims[0] * dims[1]));
+        double ctr[3] = {org[0] + kx, org[1] + ky, org[2] + kz};
+        double lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = ctr[d] - W;
+            hi[d] = ctr[d] + W;
+        }
+        double sum = 0.0;
+        long long np = 0;
+        for (int v = 0; v < g->n_views; ++v) {
+            int u0 = 0, u1 = g->nu - 1, v0 = 0, v1 = g->nv - 1;
+            if (!view_pixel_window(g, v, lo, hi, &u0, &u1, &v0, &v1)) {
+                u0 = 0;
+                u1 = g->nu - 1;
+                v0 = 0;
+                v1 = g->nv - 1;
+            }
+            for (int iv = v0; iv <= v1; ++iv)
+                for (int iu = u0; iu <= u1; ++iu) {
+                    const long long r = ((long long)v * g->nv + iv) * g->nu + iu;
+                    double s[3], w[3], p[3], tlo = -INFINITY, thi = INFINITY;
+                    orc_geom_ray(g, r, s, w);
+                    int ok = 1;
+                    for (int d = 0; d < 3 && ok; ++d) {
+                        double a, b;
+                        p[d] = s[d] - ctr[d];
+                        if (!axis_interval(n, p[d], w[d], &a, &b)) { ok = 0; break; }
+                        if (a > tlo) tlo = a;
+                        if (b < thi) thi = b;
+                    }
+                    if (!ok || !(thi > tlo)) continue;
+                    sum += y[r] * orc_footprint(n, w, p);
+                    np += 1;
+                }
         }
         out[i] = sum;
         if (pairs) pairs[i] = np;

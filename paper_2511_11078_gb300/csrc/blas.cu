@@ -85,8 +85,49 @@ __global__ void k_cg_step_p(long long n, float *__restrict__ p, const float *__r
 
 static int stream_blocks(long long n)
 {
-    const long long b = (n + 255) / 256;
-    return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+    const long long b = (n + 255) / 256, cap = 8LL * sm_count();
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+// FP32 throughput probe: kProbeChains independent FMA chains per thread,
+// x <- x a + b (contracting to b / (1 - a): no overflow, no subnormals), as
+// scalar FMAs or as packed FP32x2 FMAs (__ffma2_rn, two per instruction).
+constexpr int kProbeChains = 16;
+constexpr int kProbeThreads = 256;
+__global__ void __launch_bounds__(kProbeThreads) k_fp32_probe(int iters, int packed, float *out)
+{
+    const float a = 0.9999f, b = 1e-4f;
+    const float x0 = 0.5f + 1e-6f * (float)(threadIdx.x + blockIdx.x);
+    float sum = 0.0f;
+    if (packed) {
+        float2 x[kProbeChains / 2];
+#pragma unroll
+        for (int i = 0; i < kProbeChains / 2; ++i) x[i] = make_float2(x0 + 0.01f * i, x0 - 0.01f * i);
+        const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll 1
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < kProbeChains / 2; ++i) x[i] = __ffma2_rn(x[i], a2, b2);
+        }
+#pragma unroll
+        for (int i = 0; i < kProbeChains / 2; ++i) sum += x[i].x + x[i].y;
+    } else {
+        float x[kProbeChains];
+#pragma unroll
+        for (int i = 0; i < kProbeChains; ++i) x[i] = x0 + 0.01f * i;
+#pragma unroll 1
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < kProbeChains; ++i) x[i] = fmaf(x[i], a, b);
+        }
+#pragma unroll
+        for (int i = 0; i < kProbeChains; ++i) sum += x[i];
+    }
+    if (sum == -1.0f) out[0] = sum;  // never true; keeps the chains live
 }
 
 }  // namespace spl
@@ -94,6 +135,20 @@ static int stream_blocks(long long n)
 using namespace spl;
 
 extern "C" long long spl_dot_f64_workspace_bytes(void) { return (long long)kDotBlocks * sizeof(double); }
+
+extern "C" spl_status spl_fp32_probe(int packed, int blocks_per_sm, int iters, float *out_dev, double *flop,
+                                     void *stream)
+{
+    clear_error();
+    if (blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || !out_dev || !flop)
+        return fail(SPL_ERR_ARG, "bad argument");
+    const int blocks = blocks_per_sm * sm_count();
+    *flop = 2.0 * 4.0 * kProbeChains * (double)iters * blocks * kProbeThreads;
+    k_fp32_probe<<<blocks, kProbeThreads, 0, (cudaStream_t)stream>>>(iters, packed ? 1 : 0, out_dev);
+    return cuda_check(cudaGetLastError(), "probe launch");
+}
+
+extern "C" int spl_sm_count(void) { return sm_count(); }
 
 extern "C" spl_status spl_dot_f64(long long n, const float *a_dev, const float *b_dev, double *out_dev, void *work_dev,
                                   long long work_bytes, void *stream)

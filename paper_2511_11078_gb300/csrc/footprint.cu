@@ -143,6 +143,32 @@ extern "C" spl_status spl_features(int degree, long long count, const float *ome
     return cuda_check(cudaGetLastError(), "features launch");
 }
 
+extern "C" spl_status spl_frame(long long count, const double *omega, double *u, double *v)
+{
+    clear_error();
+    if (count < 0) return fail(SPL_ERR_ARG, "bad count");
+    if (count == 0) return SPL_OK;
+    if (!omega || !u || !v) return fail(SPL_ERR_ARG, "NULL array");
+    for (long long i = 0; i < count; ++i) {
+        double w[3];
+        double nrm = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            w[e] = omega[3 * i + e];
+            nrm += w[e] * w[e];
+        }
+        nrm = sqrt(nrm);
+        if (!(nrm > 0.0) || !isfinite(nrm)) return fail(SPL_ERR_NONFINITE, "direction %lld is zero or not finite", i);
+        for (int e = 0; e < 3; ++e) w[e] /= nrm;
+        double uu[3], vv[3];
+        canonical_frame(w, uu, vv);
+        for (int e = 0; e < 3; ++e) {
+            u[3 * i + e] = uu[e];
+            v[3 * i + e] = vv[e];
+        }
+    }
+    return SPL_OK;
+}
+
 extern "C" spl_status spl_footprint_samples(int degree, long long count, const float *normals_dev,
                                             const float *uniforms_dev, float *omega_dev, float *p_dev, void *stream)
 {

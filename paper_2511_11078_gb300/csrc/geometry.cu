@@ -31,6 +31,52 @@ spl_status cuda_check(cudaError_t e, const char *what)
     return fail(SPL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// ---------------------------------------------------------------- per-device state
+namespace {
+constexpr int kMaxDev = 64;
+std::mutex g_dev_mutex;
+int g_sm_count[kMaxDev];             // 0: not queried yet
+struct AttrDone {
+    const void *func;
+    int device;
+};
+AttrDone g_attr_done[256];
+int g_attr_n = 0;
+}  // namespace
+
+int sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return 1;
+    }
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if (g_sm_count[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 1;
+        }
+        g_sm_count[dev] = n;
+    }
+    return g_sm_count[dev];
+}
+
+spl_status smem_attr_once(const void *func, int bytes, const char *what)
+{
+    int dev = 0;
+    spl_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != SPL_OK) return s;
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    for (int i = 0; i < g_attr_n; ++i)
+        if (g_attr_done[i].func == func && g_attr_done[i].device == dev) return SPL_OK;
+    s = cuda_check(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes), what);
+    if (s != SPL_OK) return s;
+    if (g_attr_n < (int)(sizeof(g_attr_done) / sizeof(g_attr_done[0]))) g_attr_done[g_attr_n++] = {func, dev};
+    return SPL_OK;
+}
+
 // ---------------------------------------------------------------- quadrature
 // Roots of the Legendre polynomial P_m by Newton's method from Tricomi's
 // asymptotic initial guess, in long double; weights 2/((1-x^2) P_m'(x)^2).
@@ -432,6 +478,7 @@ extern "C" spl_status spl_geometry_status(const spl_geometry *g, void *stream)
         s = cuda_check(cudaMemsetAsync(g->dev.err, 0, sizeof(int), st), "status clear");
         if (s != SPL_OK) return s;
         cudaStreamSynchronize(st);
+        if (flag & 2) return fail(SPL_ERR_TIMEOUT, "a bounded tensor-core wait gave up (flag 0x%x)", flag);
         return fail(SPL_ERR_STEPCAP, "a kernel reached a loop bound (flag 0x%x)", flag);
     }
     return SPL_OK;

@@ -16,6 +16,7 @@
 //   k_adam           -- Adam on the FP32 master copy, then k_prep refreshes
 //                       the BF16 evaluation copy.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -34,6 +35,7 @@ struct spl_mlp {
     int max_batch;
     int device;
     int step;
+    unsigned long long seed;  // seed of the initial parameters
     float *master;    // [kParams] FP32 master parameters
     float *adam_m;    // [kParams]
     float *adam_v;    // [kParams]
@@ -47,6 +49,7 @@ struct spl_mlp {
     float *dz4;       // [max_batch]
     float *part;      // [chunks][kParams + 1] weight-gradient (and loss) partials
     double *loss_part;  // [max_batch / 128 + 1] per-block loss partials
+    int *err;         // device error flag (kErrTimeout: a tensor-core wait gave up)
     void *block;      // single device allocation holding all of the above
 };
 
@@ -58,6 +61,7 @@ MlpDev mlp_dev(const spl_mlp *m)
     d.w23 = m->w23;
     d.f32 = m->f32;
     d.tc_img = m->tc_img;
+    d.err = m->err;
     return d;
 }
 
@@ -154,10 +158,14 @@ __global__ void __launch_bounds__(2 * kTcRows, 2) k_mlp_rows(MlpDev w, int degre
         float o;
         const bool ok = tc_mlp_tile<2>(S, x, o, phase, part);
         // a tensor-core wait that gave up (not expected) leaves NaN in the
-        // rows of the tile and stops the CTA
+        // rows of the tile, sets the network's error flag and stops the CTA
         const bool bad = __syncthreads_or(!ok);
         if (r < count && tc_half<2>() == 0) out[r] = bad ? __int_as_float(0x7FC00000) : o * mask;
-        if (bad) break;
+        if (bad) {
+            if (threadIdx.x == 0) atomicOr(w.err, kErrTimeout);
+            tc_mlp_teardown(S, phase, true);
+            return;
+        }
     }
     tc_mlp_teardown(S);
 }
@@ -165,19 +173,14 @@ __global__ void __launch_bounds__(2 * kTcRows, 2) k_mlp_rows(MlpDev w, int degre
 static unsigned eval_blocks(long long count)
 {
     const long long tiles = (count + kTcRows - 1) / kTcRows;
-    return (unsigned)(tiles < 152 * 4 ? (tiles > 0 ? tiles : 1) : 152 * 4);
+    const long long cap = 4LL * sm_count();
+    return (unsigned)(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
 }
 
 // dynamic shared memory of the tcgen05 row kernels (set once per process)
 template <bool FROM_WP> static spl_status rows_smem_attr()
 {
-    static bool done = false;
-    if (done) return SPL_OK;
-    spl_status s = cuda_check(cudaFuncSetAttribute(k_mlp_rows<FROM_WP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)sizeof(TcMlpSmem)),
-                              "mlp rows smem attribute");
-    if (s == SPL_OK) done = true;
-    return s;
+    return smem_attr_once((const void *)k_mlp_rows<FROM_WP>, (int)sizeof(TcMlpSmem), "mlp rows smem attribute");
 }
 
 spl_status footprint_mlp(const spl_basis_desc *b, long long count, const float *w, const float *p, float *out,
@@ -210,10 +213,15 @@ __global__ void __launch_bounds__(2 * kTcRows, 2) k_train_forward(MlpDev w, int 
         float o;
         const bool ok = tc_mlp_tile<2, true>(S, x, o, phase, part, &sv);
         // a tensor-core wait that gave up (not expected) leaves NaN outputs,
-        // so the loss and the gradient come out NaN
+        // so the loss and the gradient come out NaN, and sets the network's
+        // error flag
         const bool bad = __syncthreads_or(!ok);
         if (r < B && tc_half<2>() == 0) out[r] = bad ? __int_as_float(0x7FC00000) : o;
-        if (bad) break;
+        if (bad) {
+            if (threadIdx.x == 0) atomicOr(w.err, kErrTimeout);
+            tc_mlp_teardown(S, phase, true);
+            return;
+        }
     }
     tc_mlp_teardown(S);
 }
@@ -450,13 +458,10 @@ static spl_status grad_impl(spl_mlp *m, int B, const float *X, const float *Y, f
                             cudaStream_t st)
 {
     const MlpDev w = mlp_dev(m);
-    static bool attr_done = false;
-    if (!attr_done) {
-        spl_status s = cuda_check(cudaFuncSetAttribute(k_train_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)sizeof(TcMlpSmem)),
-                                  "train forward smem attribute");
+    {
+        spl_status s = smem_attr_once((const void *)k_train_forward, (int)sizeof(TcMlpSmem),
+                                      "train forward smem attribute");
         if (s != SPL_OK) return s;
-        attr_done = true;
     }
     k_train_forward<<<eval_blocks(B), 2 * kTcRows, sizeof(TcMlpSmem), st>>>(w, B, X, m->act, m->out, m->max_batch);
     const int bblocks = (B + kBwdRows - 1) / kBwdRows;
@@ -494,6 +499,7 @@ extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long lo
     if (!m) return fail(SPL_ERR_OOM, "host allocation failed");
     m->degree = degree;
     m->max_batch = max_batch;
+    m->seed = seed;
     cudaGetDevice(&m->device);
     const int chunks = (max_batch + kChunkRows - 1) / kChunkRows;
     const int nloss = (max_batch + kBwdRows - 1) / kBwdRows;
@@ -508,7 +514,8 @@ extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long lo
                  o_img = take(sizeof(TcMlpImage)),
                  o_act = take((size_t)6 * max_batch * 64 * 4), o_out = take((size_t)max_batch * 4),
                  o_dz = take((size_t)3 * max_batch * 64 * 4), o_dz4 = take((size_t)max_batch * 4),
-                 o_part = take((size_t)chunks * (kParams + 1) * 4), o_loss = take((size_t)nloss * 8);
+                 o_part = take((size_t)chunks * (kParams + 1) * 4), o_loss = take((size_t)nloss * 8),
+                 o_err = take(sizeof(int));
     void *blk = nullptr;
     cudaError_t ce = cudaMalloc(&blk, off);
     if (ce != cudaSuccess) {
@@ -531,6 +538,13 @@ extern "C" spl_status spl_mlp_create(int degree, int max_batch, unsigned long lo
     m->dz4 = (float *)(base + o_dz4);
     m->part = (float *)(base + o_part);
     m->loss_part = (double *)(base + o_loss);
+    m->err = (int *)(base + o_err);
+    if (cudaMemset(m->err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(blk);
+        free(m);
+        return fail(SPL_ERR_CUDA, "error flag clear failed");
+    }
     // seeded uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for weights and biases
     float *h = (float *)malloc(kParams * sizeof(float));
     if (!h) { cudaFree(blk); free(m); return fail(SPL_ERR_OOM, "host allocation failed"); }
@@ -578,6 +592,148 @@ extern "C" spl_status spl_mlp_set_params(spl_mlp *m, const float *host_params)
     s = prep(m, 0);
     if (s != SPL_OK) return s;
     return cuda_check(cudaDeviceSynchronize(), "params prep");
+}
+
+extern "C" spl_status spl_mlp_status(const spl_mlp *m, void *stream)
+{
+    clear_error();
+    if (!m) return fail(SPL_ERR_ARG, "mlp is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int flag = 0;
+    spl_status s = cuda_check(cudaMemcpyAsync(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost, st), "status read");
+    if (s == SPL_OK) s = cuda_check(cudaStreamSynchronize(st), "status sync");
+    if (s != SPL_OK) return s;
+    if (flag) {
+        s = cuda_check(cudaMemsetAsync(m->err, 0, sizeof(int), st), "status clear");
+        if (s == SPL_OK) s = cuda_check(cudaStreamSynchronize(st), "status sync");
+        if (s != SPL_OK) return s;
+        return fail(SPL_ERR_TIMEOUT, "a bounded tensor-core wait gave up (flag 0x%x)", flag);
+    }
+    return SPL_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+namespace {
+const char kCkptMagic[8] = {'S', 'P', 'L', 'M', 'L', 'P', '2', '\0'};
+constexpr int kCkptVersion = 2;
+constexpr int kCkptHeader = 8;  // int32 fields after the magic
+
+void put_le32(unsigned char *b, uint32_t v)
+{
+    for (int i = 0; i < 4; ++i) b[i] = (unsigned char)(v >> (8 * i));
+}
+uint32_t get_le32(const unsigned char *b)
+{
+    uint32_t v = 0;
+    for (int i = 0; i < 4; ++i) v |= (uint32_t)b[i] << (8 * i);
+    return v;
+}
+}  // namespace
+
+extern "C" spl_status spl_mlp_save(const spl_mlp *m, const char *path)
+{
+    clear_error();
+    if (!m || !path) return fail(SPL_ERR_ARG, "NULL argument");
+    const size_t nbytes = 8 + 4 * kCkptHeader + 8 + 3 * (size_t)kParams * 4;
+    unsigned char *buf = (unsigned char *)malloc(nbytes);
+    if (!buf) return fail(SPL_ERR_OOM, "host allocation failed");
+    memcpy(buf, kCkptMagic, 8);
+    const int32_t head[kCkptHeader] = {kCkptVersion, m->degree, kParams, kIn, kHid, 3, 0, m->step};
+    for (int i = 0; i < kCkptHeader; ++i) put_le32(buf + 8 + 4 * i, (uint32_t)head[i]);
+    unsigned char *p = buf + 8 + 4 * kCkptHeader;
+    put_le32(p, (uint32_t)(m->seed & 0xffffffffu));
+    put_le32(p + 4, (uint32_t)(m->seed >> 32));
+    p += 8;
+    float *tmp = (float *)malloc((size_t)kParams * 4);
+    if (!tmp) {
+        free(buf);
+        return fail(SPL_ERR_OOM, "host allocation failed");
+    }
+    const float *src[3] = {m->master, m->adam_m, m->adam_v};
+    spl_status s = cuda_check(cudaDeviceSynchronize(), "checkpoint sync");
+    for (int a = 0; a < 3 && s == SPL_OK; ++a) {
+        s = cuda_check(cudaMemcpy(tmp, src[a], (size_t)kParams * 4, cudaMemcpyDeviceToHost), "checkpoint download");
+        for (int i = 0; i < kParams && s == SPL_OK; ++i) {
+            uint32_t bits;
+            memcpy(&bits, tmp + i, 4);
+            put_le32(p + 4 * ((size_t)a * kParams + i), bits);
+        }
+    }
+    free(tmp);
+    if (s == SPL_OK) {
+        FILE *f = fopen(path, "wb");
+        if (!f) s = fail(SPL_ERR_ARG, "cannot open %s for writing", path);
+        else {
+            const size_t w = fwrite(buf, 1, nbytes, f);
+            const int c = fclose(f);
+            if (w != nbytes || c != 0) s = fail(SPL_ERR_ARG, "write to %s failed", path);
+        }
+    }
+    free(buf);
+    return s;
+}
+
+extern "C" spl_status spl_mlp_load(spl_mlp *m, const char *path)
+{
+    clear_error();
+    if (!m || !path) return fail(SPL_ERR_ARG, "NULL argument");
+    const size_t nbytes = 8 + 4 * kCkptHeader + 8 + 3 * (size_t)kParams * 4;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(SPL_ERR_ARG, "cannot open %s", path);
+    unsigned char *buf = (unsigned char *)malloc(nbytes + 1);
+    if (!buf) {
+        fclose(f);
+        return fail(SPL_ERR_OOM, "host allocation failed");
+    }
+    const size_t got = fread(buf, 1, nbytes + 1, f);
+    fclose(f);
+    spl_status s = SPL_OK;
+    int32_t head[kCkptHeader];
+    if (got != nbytes) s = fail(SPL_ERR_ARG, "%s: %zu bytes, expected %zu", path, got, nbytes);
+    else if (memcmp(buf, kCkptMagic, 8) != 0) s = fail(SPL_ERR_ARG, "%s is not an f_theta checkpoint", path);
+    if (s == SPL_OK) {
+        for (int i = 0; i < kCkptHeader; ++i) head[i] = (int32_t)get_le32(buf + 8 + 4 * i);
+        if (head[0] != kCkptVersion || head[2] != kParams || head[3] != kIn || head[4] != kHid || head[5] != 3 ||
+            head[6] != 0)
+            s = fail(SPL_ERR_ARG, "%s: unsupported version or network shape", path);
+        else if (head[1] != m->degree)
+            s = fail(SPL_ERR_ARG, "%s holds a network for degree %d, not %d", path, head[1], m->degree);
+        else if (head[7] < 0)
+            s = fail(SPL_ERR_ARG, "%s: negative step count", path);
+    }
+    float *vals = nullptr;
+    if (s == SPL_OK) {
+        vals = (float *)malloc(3 * (size_t)kParams * 4);
+        if (!vals) s = fail(SPL_ERR_OOM, "host allocation failed");
+    }
+    if (s == SPL_OK) {
+        const unsigned char *p = buf + 8 + 4 * kCkptHeader + 8;
+        for (size_t i = 0; i < 3 * (size_t)kParams; ++i) {
+            const uint32_t bits = get_le32(p + 4 * i);
+            memcpy(vals + i, &bits, 4);
+            if (!isfinite(vals[i])) {
+                s = fail(SPL_ERR_NONFINITE, "%s: value %zu is not finite", path, i);
+                break;
+            }
+        }
+    }
+    if (s == SPL_OK) {
+        const unsigned char *p = buf + 8 + 4 * kCkptHeader;
+        float *dst[3] = {m->master, m->adam_m, m->adam_v};
+        s = cuda_check(cudaDeviceSynchronize(), "checkpoint sync");
+        for (int a = 0; a < 3 && s == SPL_OK; ++a)
+            s = cuda_check(cudaMemcpy(dst[a], vals + (size_t)a * kParams, (size_t)kParams * 4, cudaMemcpyHostToDevice),
+                           "checkpoint upload");
+        if (s == SPL_OK) {
+            m->step = head[7];
+            m->seed = (unsigned long long)get_le32(p) | ((unsigned long long)get_le32(p + 4) << 32);
+            s = prep(m, 0);
+        }
+        if (s == SPL_OK) s = cuda_check(cudaDeviceSynchronize(), "checkpoint prep");
+    }
+    free(vals);
+    free(buf);
+    return s;
 }
 
 extern "C" spl_status spl_mlp_get_params(const spl_mlp *m, float *host_params)

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_views(DevGeom g, MlpDev 
     __syncthreads();
     const int rounds = T.rounds;
     unsigned phase = 0;
-    bool ok = true, stop = false;
+    bool ok = true, stop = false, timeout = false;
     for (int round = 0; round < rounds && !stop; ++round) {
         if (round < nslab) {
             MlpSinkN<N> sk;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_views(DevGeom g, MlpDev 
             float o;
             const bool tok = tc_mlp_tile<1>(S, x, o, phase);
             if (__syncthreads_or(!tok)) {  // a tensor-core wait gave up (not expected)
-                ok = false;
+                timeout = true;
                 stop = true;
                 break;
             }
@@ -215,9 +215,10 @@ __global__ void __launch_bounds__(kMlpThreads, 3) k_mlp_views(DevGeom g, MlpDev 
         if (tid == 0) T.count = 0;
         __syncthreads();
     }
-    if (!ok) atomicOr(g.err, 1);
-    if (!ADJ && valid) yout[ray] = T.acc[tid];
-    tc_mlp_teardown(S);
+    if (!ok) atomicOr(g.err, kErrStepCap);
+    if (timeout && tid == 0) atomicOr(g.err, kErrTimeout);
+    if (!ADJ && valid) yout[ray] = timeout ? __int_as_float(0x7FC00000) : T.acc[tid];
+    tc_mlp_teardown(S, phase, timeout);
 }
 
 template <int N, bool ADJ>
@@ -227,13 +228,9 @@ static spl_status launch_mlp_views(const spl_geometry *g, const spl_mlp *m, cons
     const DevGeom &dg = g->dev;
     if (dg.n_rays == 0) return SPL_OK;
     const size_t sm = mlp_views_smem<N>();
-    static bool attr_done = false;
-    if (!attr_done) {
-        spl_status s = cuda_check(cudaFuncSetAttribute(k_mlp_views<N, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)sm),
-                                  "mlp smem attribute");
+    {
+        spl_status s = smem_attr_once((const void *)k_mlp_views<N, ADJ>, (int)sm, "mlp smem attribute");
         if (s != SPL_OK) return s;
-        attr_done = true;
     }
     dim3 grid((dg.nu + 7) / 8, (dg.nv + 15) / 16, dg.n_views);
     k_mlp_views<N, ADJ><<<grid, kMlpThreads, sm, st>>>(dg, mlp_dev(m), cin, yout, yin, cout, quad_rule(N));

@@ -483,6 +483,13 @@ bool plane_ready(spl_geometry *g, int degree, cudaStream_t st, spl_status *err)
     return pk.state == 1;
 }
 
+int plane_state(const spl_geometry *g, int degree)
+{
+    if (!g->plane || degree < 0 || degree > 3) return -1;
+    std::lock_guard<std::mutex> lock(g_plane_mu);
+    return g->plane->pack[degree].state;
+}
+
 void plane_free(PlaneGroup *pg)
 {
     if (!pg) return;
@@ -596,7 +603,9 @@ extern "C" spl_status spl_prepare(spl_geometry *g, const spl_basis_desc *basis, 
     if (!g) return spl::fail(SPL_ERR_ARG, "geometry is NULL");
     spl_status s = spl::check_basis(basis);
     if (s != SPL_OK) return s;
-    if (basis->mode == SPL_FP_MLP || basis->mode == SPL_FP_TABLE || basis->separable == SPL_SEP_OFF) return SPL_OK;
+    if (basis->mode == SPL_FP_MLP) return SPL_OK;
+    if (basis->mode == SPL_FP_TABLE) return spl::table_build(g, basis->degree, (cudaStream_t)stream);
+    if (basis->separable == SPL_SEP_OFF) return SPL_OK;
     spl_status err;
     spl::plane_ready(g, basis->degree, (cudaStream_t)stream, &err);
     return err;

@@ -43,7 +43,10 @@ struct FwdSink {
     SinkBox bx;
     float inv_wd;
     bool kahan;
-    float acc, sum, comp;
+    // the cell's partial sum c_l * F_l, spread over four independent
+    // accumulators (a face's 16 gathers and FMAs then form four chains of
+    // four instead of one chain of sixteen)
+    float acc[4], sum, comp;
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
@@ -51,16 +54,16 @@ struct FwdSink {
     }
     __device__ __forceinline__ void flush(int ld, int la, int lb, float v)
     {
-        if (bx.holds(ld, la, lb)) acc = fmaf(__ldg(c + (ld * S0 + la * S1 + lb * S2)), v, acc);
+        if (bx.holds(ld, la, lb)) acc[0] = fmaf(__ldg(c + (ld * S0 + la * S1 + lb * S2)), v, acc[0]);
     }
-    __device__ __forceinline__ void put(unsigned o, bool in, float v)
+    __device__ __forceinline__ void put(unsigned o, bool in, float v, int slot)
     {
-        if (in) acc = fmaf(__ldg(c + o), v, acc);
+        if (in) acc[slot & 3] = fmaf(__ldg(c + o), v, acc[slot & 3]);
     }
     __device__ __forceinline__ void cell_end()
     {
-        const float v = acc * inv_wd;
-        acc = 0.0f;
+        const float v = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * inv_wd;
+        acc[0] = acc[1] = acc[2] = acc[3] = 0.0f;
         if (kahan) kahan_add(sum, comp, v);
         else sum += v;
     }
@@ -82,7 +85,7 @@ struct CountSink {
     {
         n += (bx.holds(ld, la, lb) && v > 0.0f) ? 1u : 0u;
     }
-    __device__ __forceinline__ void put(unsigned, bool in, float v) { n += (in && v > 0.0f) ? 1u : 0u; }
+    __device__ __forceinline__ void put(unsigned, bool in, float v, int) { n += (in && v > 0.0f) ? 1u : 0u; }
     __device__ __forceinline__ void cell_end() {}
 };
 
@@ -103,7 +106,7 @@ struct AtomicSink {
     {
         if (bx.holds(ld, la, lb)) atomicAdd(c + (ld * S0 + la * S1 + lb * S2), yv * v);
     }
-    __device__ __forceinline__ void put(unsigned o, bool in, float v)
+    __device__ __forceinline__ void put(unsigned o, bool in, float v, int)
     {
         if (in) atomicAdd(c + o, yv * v);
     }
@@ -128,7 +131,7 @@ struct BrickSink {
     {
         if (bx.holds(ld, la, lb)) atomicAdd(part + (unsigned)(ld * S0 + la * S1 + lb * S2 + (int)off), yv * v);
     }
-    __device__ __forceinline__ void put(unsigned o, bool in, float v)
+    __device__ __forceinline__ void put(unsigned o, bool in, float v, int)
     {
         if (in) atomicAdd(part + o, yv * v);
     }
@@ -137,19 +140,33 @@ struct BrickSink {
 
 // ---------------------------------------------------------------- forward
 
-// View classes of a view-kernel launch.  VM_MIXED: cone views, the march
-// form (flat or general) is chosen per ray.  VM_FLAT / VM_GENERAL: parallel
+// View classes of a view-kernel launch.  VM_FLAT / VM_GENERAL: parallel
 // views of one class, taken from the geometry's view order; the form is
 // fixed at compile time, so each kernel carries the registers of one form
 // only (a parallel view's rays share their direction, hence their form).
-enum { VM_MIXED = 0, VM_FLAT = 1, VM_GENERAL = 2, VM_RAYS = 3 };
+// VM_CONE: cone views, every ray with the piece march (a cone ray with a
+// zero direction component, rare, is integrated by the general form too:
+// its constant factor is then evaluated at every node, which is exact but
+// slower; the kernel keeps the registers and code of one form).  VM_RAYS:
+// explicit rays, the form chosen per ray.
+enum { VM_CONE = 0, VM_FLAT = 1, VM_GENERAL = 2, VM_RAYS = 3 };
 
 template <int N, int VM, class Sink>
 __device__ __forceinline__ bool march_vm(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sk)
 {
     if constexpr (VM == VM_FLAT) return cell_march<N, Sink, true>(rs, cf, cl, qr, sk);
-    else if constexpr (VM == VM_GENERAL) return piece_march<N, Sink>(rs, cf, cl, qr, sk);
+    else if constexpr (VM == VM_GENERAL || VM == VM_CONE) return piece_march<N, Sink>(rs, cf, cl, qr, sk);
     else return march<N>(rs, cf, cl, qr, sk);
+}
+
+// The march form of a ray of geometry kind `kind` (used where one kernel
+// serves every view kind: the pair count and the brick adjoint), the same
+// as the projection kernels': cone rays always take the piece march.
+template <int N, class Sink>
+__device__ __forceinline__ bool march_kind(int kind, const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sk)
+{
+    if (kind == SPL_CONE) return piece_march<N, Sink>(rs, cf, cl, qr, sk);
+    return march<N>(rs, cf, cl, qr, sk);
 }
 
 // blocks per SM the register budget is sized for (measured): the flat form
@@ -167,7 +184,7 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
                                                bool kahan, int *err)
 {
     if constexpr (DIRECT && VM != VM_FLAT) {
-        if (VM == VM_GENERAL || rs.rb != 0.0f) {
+        if (VM == VM_GENERAL || VM == VM_CONE || rs.rb != 0.0f) {
             float out;
             if (!direct_march<N>(rs, c, rs.S[0], rs.S[1], rs.S[2], make_box(rs.lo, rs.hi), qr, kahan, out))
                 atomicOr(err, 1);
@@ -183,14 +200,14 @@ __device__ __forceinline__ float march_forward(const RaySetup &rs, const float *
     sk.bx = make_box(rs.lo, rs.hi);
     sk.inv_wd = rs.inv_wd;
     sk.kahan = kahan;
-    sk.acc = sk.sum = sk.comp = 0.0f;
+    sk.acc[0] = sk.acc[1] = sk.acc[2] = sk.acc[3] = sk.sum = sk.comp = 0.0f;
     if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
     return sk.sum;
 }
 
-// cone views (the march form is chosen per ray)
+// cone views (every ray with the piece march)
 template <int N, bool DIRECT>
-__global__ void __launch_bounds__(128, (ViewBlocks<VM_MIXED, DIRECT>::value))
+__global__ void __launch_bounds__(128, (ViewBlocks<VM_CONE, DIRECT>::value))
     k_forward_views(DevGeom g, const float *__restrict__ c, float *__restrict__ y, QuadRule qr, int kahan)
 {
     int iu, iv;
@@ -200,7 +217,7 @@ __global__ void __launch_bounds__(128, (ViewBlocks<VM_MIXED, DIRECT>::value))
     RaySetup rs;
     float v = 0.0f;
     if (view_setup<N>(g, grid_of(g), k, iu, iv, rs))
-        v = march_forward<N, VM_MIXED, DIRECT>(rs, c, qr, kahan != 0, g.err);
+        v = march_forward<N, VM_CONE, DIRECT>(rs, c, qr, kahan != 0, g.err);
     y[((long long)k * g.nv + iv) * g.nu + iu] = v;
 }
 
@@ -241,8 +258,8 @@ __global__ void __launch_bounds__(128) k_forward_rays(DevGeom g, const float *__
 
 // ---------------------------------------------------------------- pair count
 template <int N>
-__device__ __forceinline__ void march_count(const RaySetup &rs, const QuadRule &qr, int *err, unsigned int &pairs,
-                                            unsigned int &pieces, unsigned int &flat_pieces)
+__device__ __forceinline__ void march_count(int kind, const RaySetup &rs, const QuadRule &qr, int *err,
+                                            unsigned int &pairs, unsigned int &pieces, unsigned int &flat_pieces)
 {
     CountSink sk;
     sk.S0 = sk.S1 = sk.S2 = 0;
@@ -250,10 +267,11 @@ __device__ __forceinline__ void march_count(const RaySetup &rs, const QuadRule &
     sk.bx = make_box(rs.lo, rs.hi);
     sk.n = 0u;
     sk.pieces = 0u;
-    if (!march<N>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
+    if (!march_kind<N>(kind, rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
+    const bool flat = rs.rb == 0.0f && kind != SPL_CONE;
     pairs = sk.n;
-    pieces = rs.rb == 0.0f ? 0u : sk.pieces;
-    flat_pieces = rs.rb == 0.0f ? sk.pieces : 0u;
+    pieces = flat ? 0u : sk.pieces;
+    flat_pieces = flat ? sk.pieces : 0u;
 }
 
 __device__ __forceinline__ void add_count(unsigned long long *count, unsigned int v)
@@ -273,7 +291,7 @@ __global__ void __launch_bounds__(128) k_count_views(DevGeom g, unsigned long lo
     unsigned int v = 0, pc = 0, pf = 0;
     RaySetup rs;
     if (iu < g.nu && iv < g.nv && view_setup<N>(g, grid_of(g), k, iu, iv, rs))
-        march_count<N>(rs, qr, g.err, v, pc, pf);
+        march_count<N>(g.kind, rs, qr, g.err, v, pc, pf);
     add_count(count, v);
     add_count(count + 1, pc);
     add_count(count + 2, pf);
@@ -288,7 +306,7 @@ __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long lon
         double s[3], w[3];
         explicit_ray(g, r, s, w);
         RaySetup rs;
-        if (ray_setup<N>(grid_of(g), s, w, rs)) march_count<N>(rs, qr, g.err, v, pc, pf);
+        if (ray_setup<N>(grid_of(g), s, w, rs)) march_count<N>(SPL_RAYS, rs, qr, g.err, v, pc, pf);
     }
     add_count(count, v);
     add_count(count + 1, pc);
@@ -337,7 +355,7 @@ __global__ void __launch_bounds__(128, 3)
     const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
     if (yr == 0.0f) return;
     RaySetup rs;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM_MIXED>(rs, yr, c, qr, g.err);
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM_CONE>(rs, yr, c, qr, g.err);
 }
 
 template <int N, int VM>
@@ -529,7 +547,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
             sk.off = (unsigned)Loff;
             sk.bx = make_box(blo, bhi);
             sk.yv = yr * rs.inv_wd;
-            ok &= march<N>(rs, cf, cl, qr, sk);
+            ok &= march_kind<N>(g.kind, rs, cf, cl, qr, sk);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < kBrickVol; i += kAdjThreads) {
@@ -575,15 +593,18 @@ static void for_view_chunks(const spl_geometry *g, int v0, int count, F launch)
 // Parallel geometries: the separable group through the plane matrices
 // (when used), the other flat views with the flat kernel, the rest with the
 // general one.  Returns the first view_order index the flat kernel takes.
-static int plane_views(const spl_geometry *g, const spl_basis_desc *b, cudaStream_t st, spl_status *err)
+// The plane matrices are built by spl_prepare only: unbuilt is an error
+// (SPL_ERR_STATE), unavailable (their allocation failed) walks the views.
+static int plane_views(const spl_geometry *g, const spl_basis_desc *b, spl_status *err)
 {
     *err = SPL_OK;
     if (b->separable == SPL_SEP_OFF || b->mode == SPL_FP_MLP || b->mode == SPL_FP_TABLE || !g->plane) return 0;
-    spl_status e;
-    const bool ok = plane_ready(const_cast<spl_geometry *>(g), b->degree, st, &e);
-    if (!ok && e != SPL_OK && e != SPL_ERR_OOM) *err = e;  // out of memory: walk the views instead
-    clear_error();
-    return ok ? g->dev.n_sep : 0;
+    const int state = plane_state(g, b->degree);
+    if (state == 0) {
+        *err = fail(SPL_ERR_STATE, "plane matrices of degree %d not built: call spl_prepare first", b->degree);
+        return 0;
+    }
+    return state == 1 ? g->dev.n_sep : 0;
 }
 
 template <int N, bool DIRECT>
@@ -599,7 +620,7 @@ static spl_status forward_quad_t(const spl_geometry *g, const spl_basis_desc *b,
         k_forward_rays<N, DIRECT><<<(unsigned)blocks, 128, 0, st>>>(dg, c, y, qr, kahan);
     } else if (dg.kind == SPL_PARALLEL) {
         spl_status s;
-        const int v0 = plane_views(g, b, st, &s);
+        const int v0 = plane_views(g, b, &s);
         if (s != SPL_OK) return s;
         // the plane path (memory-latency bound) runs beside the march of the
         // other views (arithmetic bound) when both have work: the two write
@@ -614,11 +635,17 @@ static spl_status forward_quad_t(const spl_geometry *g, const spl_basis_desc *b,
                 ps = g->plane->side;
             }
             s = plane_forward(g, N, kahan, c, y, ps);
-            if (s != SPL_OK) return s;
             if (overlap) {
-                s = cuda_check(cudaEventRecord(g->plane->join, ps), "join record");
-                if (s != SPL_OK) return s;
+                const spl_status sj = cuda_check(cudaEventRecord(g->plane->join, ps), "join record");
+                if (s != SPL_OK || sj != SPL_OK) {
+                    // join the side stream before returning the error, so the
+                    // caller's stream (or its graph capture) never leaves it
+                    // unjoined
+                    if (sj == SPL_OK) cudaStreamWaitEvent(st, g->plane->join, 0);
+                    return s != SPL_OK ? s : sj;
+                }
             }
+            if (s != SPL_OK) return s;
         }
         const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
         for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
@@ -654,7 +681,7 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
     spl_status s;
     int v0 = 0;
     if (dg.kind == SPL_PARALLEL) {
-        v0 = plane_views(g, b, st, &s);
+        v0 = plane_views(g, b, &s);
         if (s != SPL_OK) return s;
     }
     // With the scatter form the plane path's gather (T, memory-latency
@@ -667,10 +694,16 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
     if (overlap) {
         s = cuda_check(cudaEventRecord(g->plane->fork, st), "fork record");
         if (s == SPL_OK) s = cuda_check(cudaStreamWaitEvent(g->plane->side, g->plane->fork, 0), "fork wait");
-        if (s == SPL_OK) s = plane_adjoint_t(g, N, y, g->plane->side);
-        if (s == SPL_OK) s = cuda_check(cudaEventRecord(g->plane->join, g->plane->side), "join record");
-        if (s == SPL_OK) s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
         if (s != SPL_OK) return s;
+        s = plane_adjoint_t(g, N, y, g->plane->side);
+        spl_status sj = cuda_check(cudaEventRecord(g->plane->join, g->plane->side), "join record");
+        if (s == SPL_OK) s = sj;
+        if (s == SPL_OK) s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
+        if (s != SPL_OK) {
+            // join the side stream before returning the error
+            if (sj == SPL_OK) cudaStreamWaitEvent(st, g->plane->join, 0);
+            return s;
+        }
     } else if (v0 > 0) {
         s = plane_adjoint(g, N, y, c, st);
         if (s != SPL_OK) return s;
@@ -703,14 +736,8 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
         }
         return launch_status("adjoint launch");
     }
-    static bool attr_set[4] = {false, false, false, false};
-    if (!attr_set[N]) {
-        s = cuda_check(cudaFuncSetAttribute(k_adjoint_bricks<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kAdjSmem),
-                       "adjoint smem attribute");
-        if (s != SPL_OK) return s;
-        attr_set[N] = true;
-    }
+    s = smem_attr_once((const void *)k_adjoint_bricks<N>, (int)kAdjSmem, "adjoint smem attribute");
+    if (s != SPL_OK) return s;
     const int bx = (dg.n[0] + kBrick - 1) / kBrick, by = (dg.n[1] + kBrick - 1) / kBrick,
               bz = (dg.n[2] + kBrick - 1) / kBrick;
     // bricks over the views the plane path did not take (all of them

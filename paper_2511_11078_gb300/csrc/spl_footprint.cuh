@@ -20,7 +20,7 @@ struct PointSink {
         __device__ __forceinline__ bool in1(int a) const { return a == 0; }
         __device__ __forceinline__ bool in2(int b) const { return b == 0; }
     } bx;
-    __device__ __forceinline__ void put(unsigned, bool in, float val)
+    __device__ __forceinline__ void put(unsigned, bool in, float val, int)
     {
         if (in) v = val;
     }

@@ -68,6 +68,11 @@ spl_status fail(spl_status st, const char *fmt, ...);
 spl_status cuda_check(cudaError_t e, const char *what);
 // Clear the thread's last error.
 void clear_error();
+// Number of SMs of the current device (queried once per device).
+int sm_count();
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per kernel and device (thread-safe).
+spl_status smem_attr_once(const void *func, int bytes, const char *what);
 
 // Gauss-Legendre rule that integrates degree-3n polynomials exactly
 // (m = ceil((3n+1)/2) nodes), computed once per process in FP64.
@@ -85,6 +90,9 @@ spl_status check_basis(const spl_basis_desc *b);
 // builds the degree's pack on first use; false when the geometry has no
 // group or the pack is unavailable.
 bool plane_ready(spl_geometry *g, int degree, cudaStream_t st, spl_status *err);
+// State of the degree's pack without building it: 0 not built, 1 built, -1
+// unavailable (allocation failed, or no separable group).
+int plane_state(const spl_geometry *g, int degree);
 spl_status plane_forward(const spl_geometry *g, int degree, int kahan, const float *c, float *y, cudaStream_t st);
 // writes every coefficient (the other views' scatter adds after it)
 spl_status plane_adjoint(const spl_geometry *g, int degree, const float *y, float *c, cudaStream_t st);
@@ -95,8 +103,10 @@ spl_status plane_adjoint_t(const spl_geometry *g, int degree, const float *y, cu
 spl_status plane_adjoint_add(const spl_geometry *g, int degree, float *c, cudaStream_t st);
 void plane_free(PlaneGroup *pg);
 
-// Footprint tables of the views of a parallel geometry (table.cu), built on
-// first use per degree.
+// Footprint tables of the views of a parallel geometry (table.cu): built
+// by table_build (spl_prepare); the projector returns SPL_ERR_STATE when
+// they are missing.
+spl_status table_build(spl_geometry *g, int degree, cudaStream_t st);
 spl_status table_forward(const spl_geometry *g, const spl_basis_desc *b, const float *c, float *y, cudaStream_t st);
 spl_status table_adjoint(const spl_geometry *g, const spl_basis_desc *b, const float *y, float *c, cudaStream_t st);
 void table_free(TableSet *ts);

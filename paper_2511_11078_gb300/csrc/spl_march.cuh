@@ -795,8 +795,10 @@ __device__ __forceinline__ bool cell_march(const RaySetup &rs, int cf, int cl, c
 // integrates one piece per iteration whatever cell it is in, and the event
 // that ends the piece (an a- or b-crossing, or the end of the cell) is
 // handled without branches: the leaving face is picked with selects,
-// flushed through sink.put(offset, in_region, F) at offsets in the sink's
-// layout (sink.S0..S2, sink.off, region sink.bx), and the window shifted
+// flushed through sink.put(offset, in_region, F, slot) at offsets in the
+// sink's layout (sink.S0..S2, sink.off, region sink.bx; slot in 0..N is the
+// face entry's second index, so a sink may spread the face over N+1
+// independent partial sums), and the window shifted
 // with selects along the event's axis.  Only the set-up of the next cell
 // is a branch.
 template <int N, class Sink>
@@ -869,7 +871,7 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
 #pragma unroll
                 for (int y = 0; y <= N; ++y) {
                     const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
-                    sink.put(base + (unsigned)x * SX + (unsigned)y * SY, vx[x] && vy[y], v);
+                    sink.put(base + (unsigned)x * SX + (unsigned)y * SY, vx[x] && vy[y], v, y);
                 }
         }
         // shift along the event's axis (in place: reads only higher indices)
@@ -930,7 +932,7 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
                 const int ld = cl + 1 - N + d, la = QA - N + i, lb = QB - N + k;
                 const unsigned off = sink.off + (unsigned)ld * (unsigned)sink.S0 + (unsigned)la * (unsigned)sink.S1 +
                                      (unsigned)lb * (unsigned)sink.S2;
-                sink.put(off, sink.bx.in0(ld) && sink.bx.in1(la) && sink.bx.in2(lb), acc[d][i][k]);
+                sink.put(off, sink.bx.in0(ld) && sink.bx.in1(la) && sink.bx.in2(lb), acc[d][i][k], k);
             }
     sink.cell_end();
     return true;

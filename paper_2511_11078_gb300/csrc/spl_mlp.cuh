@@ -56,6 +56,43 @@ __host__ __device__ inline void canonical_features(int degree, const double (&w_
     f[4] = (p[0] * v[0] + p[1] * v[1] + p[2] * v[2]) * sc;
 }
 
+// The frame of the features in the caller's coordinates: with G the
+// signed permutation above (chamber direction Gw) and the chamber frame
+// u_c = normalize(e1 x Gw), v_c = u_c x Gw, returns u = G^T u_c and
+// v = G^T v_c, so that <Gp, u_c> = <p, u> and <Gp, v_c> = <p, v>: the last
+// two features are <p, u> sqrt3/W and <p, v> sqrt3/W.  u and v are an
+// orthonormal basis of the plane perpendicular to w, and
+// v = det(G) (u x w).  FP64.
+__host__ __device__ inline void canonical_frame(const double (&w_in)[3], double (&u_out)[3], double (&v_out)[3])
+{
+    double w[3];
+    int idx[3], sg[3];
+    for (int e = 0; e < 3; ++e) {
+        sg[e] = w_in[e] < 0.0 ? -1 : 1;
+        w[e] = w_in[e] < 0.0 ? -w_in[e] : w_in[e];
+        idx[e] = e;
+    }
+    // the same stable ascending sort as canonical_features, tracking which
+    // axis lands in each chamber position
+    for (int i = 1; i < 3; ++i)
+        for (int j = i; j > 0 && w[j - 1] > w[j]; --j) {
+            const double t = w[j];
+            w[j] = w[j - 1];
+            w[j - 1] = t;
+            const int k = idx[j];
+            idx[j] = idx[j - 1];
+            idx[j - 1] = k;
+        }
+    const double nr = sqrt(w[1] * w[1] + w[2] * w[2]);
+    const double u[3] = {0.0, -w[2] / nr, w[1] / nr};
+    const double v[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+    // chamber component j is sg[idx[j]] times the caller's component idx[j]
+    for (int j = 0; j < 3; ++j) {
+        u_out[idx[j]] = sg[idx[j]] * u[j];
+        v_out[idx[j]] = sg[idx[j]] * v[j];
+    }
+}
+
 // The same features in FP32 (the library's FP64 units are scarce on GB300;
 // the features are FP32 values either way).  Same flip, stable sort and frame.
 __device__ __forceinline__ void canonical_features_f32(int degree, const float (&w_in)[3], const float (&p_in)[3],
@@ -101,7 +138,11 @@ struct MlpDev {
     const uint32_t *w23;  // [2][64][36] BF16 pairs: W2 then W3, row = output unit
     const float *f32;     // W1 [64][5], b1 [64], b2 [64], b3 [64], W4 [64], b4 [1]
     const void *tc_img;   // the same network in the tcgen05 tile's operand layout
+    int *err;             // device error flag of the network (bit 1: a tensor-core wait gave up)
 };
+// bits of the device error flags (geometry and MLP): a loop bound was
+// reached / a bounded tensor-core completion wait gave up
+constexpr int kErrStepCap = 1, kErrTimeout = 2;
 constexpr int kF32W1 = 0, kF32B1 = 320, kF32B2 = 384, kF32B3 = 448, kF32W4 = 512, kF32B4 = 576, kF32Size = 577;
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)

@@ -250,9 +250,13 @@ __device__ __forceinline__ void tc_mlp_setup(const MlpDev &w, TcMlpSmem &S)
     tc::fence_after();
 }
 
-// Release the TMEM accumulator (after a CTA barrier; every MMA has completed).
-__device__ __forceinline__ void tc_mlp_teardown(TcMlpSmem &S)
+// Release the TMEM accumulator (after a CTA barrier).  When a completion
+// wait gave up (`pending`), the last committed MMAs may still be running:
+// wait once more, bounded, for the phase of the last commit (`phase` is the
+// parity the next wait would use) before the columns are freed.
+__device__ __forceinline__ void tc_mlp_teardown(TcMlpSmem &S, unsigned phase = 0u, bool pending = false)
 {
+    if (pending) tc::mbar_wait(&S.mbar, phase ^ 1u);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();

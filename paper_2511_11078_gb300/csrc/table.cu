@@ -279,22 +279,17 @@ spl_status build_table(spl_geometry *g, cudaStream_t st)
     return SPL_OK;
 }
 
-spl_status table_ready(const spl_geometry *gc, int degree, cudaStream_t st)
+// The tables of `degree` exist (the projector allocates nothing: spl_prepare
+// builds them).
+spl_status table_ready(const spl_geometry *g, int degree)
 {
-    spl_geometry *g = const_cast<spl_geometry *>(gc);
     if (g->dev.kind != SPL_PARALLEL)
         return fail(SPL_ERR_UNSUPPORTED, "SPL_FP_TABLE needs a parallel-beam geometry (one footprint per view)");
     std::lock_guard<std::mutex> lock(g_table_mu);
-    if (!g->table) g->table = new TableSet();
-    TablePack &pk = g->table->pack[degree];
-    if (pk.state == 1) return SPL_OK;
-    if (pk.state == -1) return fail(SPL_ERR_OOM, "footprint tables unavailable for this geometry and degree");
-    switch (degree) {
-    case 0: return build_table<0>(g, st);
-    case 1: return build_table<1>(g, st);
-    case 2: return build_table<2>(g, st);
-    default: return build_table<3>(g, st);
-    }
+    const int state = g->table ? g->table->pack[degree].state : 0;
+    if (state == 1) return SPL_OK;
+    if (state == -1) return fail(SPL_ERR_OOM, "footprint tables unavailable for this geometry and degree");
+    return fail(SPL_ERR_STATE, "footprint tables of degree %d not built: call spl_prepare first", degree);
 }
 
 template <int N, bool ADJ>
@@ -318,7 +313,7 @@ spl_status table_launch(const spl_geometry *g, const spl_basis_desc *b, const fl
 
 spl_status table_forward(const spl_geometry *g, const spl_basis_desc *b, const float *c, float *y, cudaStream_t st)
 {
-    spl_status s = table_ready(g, b->degree, st);
+    spl_status s = table_ready(g, b->degree);
     if (s != SPL_OK || g->dev.n_rays == 0) return s;
     switch (b->degree) {
     case 0: return table_launch<0, false>(g, b, c, y, nullptr, nullptr, st);
@@ -330,7 +325,7 @@ spl_status table_forward(const spl_geometry *g, const spl_basis_desc *b, const f
 
 spl_status table_adjoint(const spl_geometry *g, const spl_basis_desc *b, const float *y, float *c, cudaStream_t st)
 {
-    spl_status s = table_ready(g, b->degree, st);
+    spl_status s = table_ready(g, b->degree);
     if (s != SPL_OK) return s;
     const long long nc = (long long)g->dev.n[0] * g->dev.n[1] * g->dev.n[2];
     s = cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint clear");
@@ -340,6 +335,23 @@ spl_status table_adjoint(const spl_geometry *g, const spl_basis_desc *b, const f
     case 1: return table_launch<1, true>(g, b, nullptr, nullptr, y, c, st);
     case 2: return table_launch<2, true>(g, b, nullptr, nullptr, y, c, st);
     default: return table_launch<3, true>(g, b, nullptr, nullptr, y, c, st);
+    }
+}
+
+spl_status table_build(spl_geometry *g, int degree, cudaStream_t st)
+{
+    if (g->dev.kind != SPL_PARALLEL)
+        return fail(SPL_ERR_UNSUPPORTED, "SPL_FP_TABLE needs a parallel-beam geometry (one footprint per view)");
+    std::lock_guard<std::mutex> lock(g_table_mu);
+    if (!g->table) g->table = new TableSet();
+    TablePack &pk = g->table->pack[degree];
+    if (pk.state == 1) return SPL_OK;
+    if (pk.state == -1) return fail(SPL_ERR_OOM, "footprint tables unavailable for this geometry and degree");
+    switch (degree) {
+    case 0: return build_table<0>(g, st);
+    case 1: return build_table<1>(g, st);
+    case 2: return build_table<2>(g, st);
+    default: return build_table<3>(g, st);
     }
 }
 

@@ -11,15 +11,10 @@ to measure max-abs and RMS error against the exact footprint.
 from __future__ import annotations
 
 import math
-import struct
 
-import numpy as np
 import torch
 
 from . import spl
-
-MAGIC = b"SPLMLP1\0"
-
 
 class FootprintSet:
     """`count` exact-footprint samples of Algorithm 1 resident on the GPU."""
@@ -86,18 +81,13 @@ def train(mlp: "spl.Mlp", data: FootprintSet, steps: int, batch: int = 8192, lr0
 
 
 def save(mlp: "spl.Mlp", path: str):
-    """Raw little-endian checkpoint: magic, degree, count, float32 params."""
-    p = mlp.get_params().astype("<f4")
-    with open(path, "wb") as f:
-        f.write(MAGIC + struct.pack("<ii", mlp.degree, p.size) + p.tobytes())
+    """Checkpoint of the training state (spl_mlp_save: header with the
+    network's shape, degree, dtype, seed and Adam step; master parameters and
+    Adam moments)."""
+    mlp.save(path)
 
 
 def load(mlp: "spl.Mlp", path: str):
-    with open(path, "rb") as f:
-        head = f.read(16)
-        if head[:8] != MAGIC:
-            raise ValueError("not an f_theta checkpoint")
-        degree, n = struct.unpack("<ii", head[8:])
-        if degree != mlp.degree or n != spl.MLP_PARAMS:
-            raise ValueError("checkpoint for degree %d with %d params" % (degree, n))
-        mlp.set_params(np.frombuffer(f.read(4 * n), dtype="<f4").astype(np.float32))
+    """Restore a checkpoint written by save (spl_mlp_load); training resumes
+    where it stopped."""
+    mlp.load(path)

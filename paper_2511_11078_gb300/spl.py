@@ -21,7 +21,7 @@ SPL_ADJ_AUTO, SPL_ADJ_GATHER, SPL_ADJ_SCATTER = 0, 1, 2
 SPL_SEP_AUTO, SPL_SEP_OFF = 0, 1
 MLP_PARAMS = 8769
 STATUS_NAMES = {0: "SPL_OK", 1: "SPL_ERR_ARG", 2: "SPL_ERR_NONFINITE", 3: "SPL_ERR_CUDA", 4: "SPL_ERR_STEPCAP",
-                5: "SPL_ERR_OOM", 6: "SPL_ERR_STATE", 7: "SPL_ERR_UNSUPPORTED"}
+                5: "SPL_ERR_OOM", 6: "SPL_ERR_STATE", 7: "SPL_ERR_UNSUPPORTED", 8: "SPL_ERR_TIMEOUT"}
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -80,6 +80,12 @@ _SIGS = {
     "spl_cg_step_x": (C.c_int, [C.c_longlong, _vp, _vp, C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
     "spl_cg_step_p": (C.c_int, [C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
     "spl_debug_set_iter_cap": (C.c_int, [C.c_int]),
+    "spl_frame": (C.c_int, [C.c_longlong, _dp, _dp, _dp]),
+    "spl_mlp_status": (C.c_int, [_vp, _vp]),
+    "spl_mlp_save": (C.c_int, [_vp, C.c_char_p]),
+    "spl_mlp_load": (C.c_int, [_vp, C.c_char_p]),
+    "spl_fp32_probe": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, _dp]),
+    "spl_sm_count": (C.c_int, []),
     "spl_last_error": (C.c_char_p, []),
     "spl_version": (C.c_char_p, []),
 }
@@ -171,6 +177,7 @@ class Geometry:
             d.nu, d.nv = int(geometry.nu), int(geometry.nv)
             self.shape = (d.n_views, d.nv, d.nu)
         self.kind = geometry.kind
+        self._prepared = set()
         h = _vp()
         check(lib().spl_make_geometry(C.byref(d), C.byref(h)))
         self._h = h
@@ -209,21 +216,37 @@ def basis(degree: int, mode: int = SPL_FP_QUAD, mlp=None, kahan: bool = True, ad
     return b
 
 
+def _basis_key(bas: BasisDesc):
+    return (int(bas.degree), int(bas.mode), int(bas.separable))
+
+
 def prepare(geom: Geometry, bas: BasisDesc, stream=None):
-    """Build the plane matrices of the geometry's slice-separable views for
-    this basis (done by the first forward/adjoint otherwise)."""
+    """spl_prepare: build what the projector needs for this basis (the plane
+    matrices of slice-separable views, the footprint tables of
+    SPL_FP_TABLE); one-time allocation, then a synchronisation."""
     check(lib().spl_prepare(geom.handle, C.byref(bas), _stream(stream)))
+    geom._prepared.add(_basis_key(bas))
+
+
+def _ensure_prepared(geom: Geometry, bas: BasisDesc, stream):
+    # spl_forward / spl_adjoint never allocate and refuse a basis whose
+    # structures are not built (SPL_ERR_STATE); the binding prepares each
+    # (degree, mode, separable) once, before its first use
+    if _basis_key(bas) not in geom._prepared:
+        prepare(geom, bas, stream)
 
 
 def forward(geom: Geometry, c, y, bas: BasisDesc, stream=None):
     """y = A c (Algorithm 2).  c: float32 CUDA [nz,ny,nx]; y: float32 CUDA (n_rays)."""
     _check_sizes(geom, c, y)
+    _ensure_prepared(geom, bas, stream)
     check(lib().spl_forward(geom.handle, C.byref(bas), _ptr(c), _ptr(y), _stream(stream)))
 
 
 def adjoint(geom: Geometry, y, c, bas: BasisDesc, stream=None):
     """c = A^T y (matched adjoint)."""
     _check_sizes(geom, c, y)
+    _ensure_prepared(geom, bas, stream)
     check(lib().spl_adjoint(geom.handle, C.byref(bas), _ptr(y), _ptr(c), _stream(stream)))
 
 
@@ -293,6 +316,18 @@ class Mlp:
             raise ValueError("need %d parameters" % MLP_PARAMS)
         check(lib().spl_mlp_set_params(self._h, p.ctypes.data_as(_fp)))
 
+    def status(self, stream=None):
+        """Synchronise and raise if a tensor-core wait of this network gave up."""
+        check(lib().spl_mlp_status(self._h, _stream(stream)))
+
+    def save(self, path: str):
+        """spl_mlp_save: parameters, Adam moments and step count to `path`."""
+        check(lib().spl_mlp_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """spl_mlp_load: restore a checkpoint written by save()."""
+        check(lib().spl_mlp_load(self._h, os.fsencode(path)))
+
     def eval(self, feat, out, stream=None):
         check(lib().spl_mlp_eval(self._h, feat.shape[0], _ptr(feat), _ptr(out), _stream(stream)))
 
@@ -303,6 +338,28 @@ class Mlp:
     def train_step(self, feat, target, lr: float, loss=None, stream=None):
         check(lib().spl_mlp_train_step(self._h, feat.shape[0], _ptr(feat), _ptr(target), C.c_float(lr), _ptr(loss),
                                        _stream(stream)))
+
+
+def frame(omega):
+    """spl_frame: the (u, v) frame of H_w in which the MLP features measure
+    offsets, for directions omega [N,3] (host FP64); returns (u, v) [N,3]."""
+    w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1, 3))
+    u = np.zeros_like(w)
+    v = np.zeros_like(w)
+    check(lib().spl_frame(w.shape[0], _dptr(w), _dptr(u), _dptr(v)))
+    return u, v
+
+
+def fp32_probe(out, packed: bool, blocks_per_sm: int = 4, iters: int = 4096, stream=None) -> float:
+    """Launch the FP32 FMA throughput probe; returns its FLOP count."""
+    flop = C.c_double(0.0)
+    check(lib().spl_fp32_probe(1 if packed else 0, int(blocks_per_sm), int(iters), _ptr(out), C.byref(flop),
+                               _stream(stream)))
+    return float(flop.value)
+
+
+def sm_count() -> int:
+    return int(lib().spl_sm_count())
 
 
 def dot_workspace(device=None):

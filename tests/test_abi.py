@@ -130,3 +130,41 @@ def test_basis_modes_are_validated_on_the_host(spl):
     assert L.spl_footprint(C.byref(bad), 0, None, None, None, None) == 1
     mlp_without_net = spl.basis(3, spl.SPL_FP_MLP)
     assert L.spl_footprint(C.byref(mlp_without_net), 0, None, None, None, None) == 1
+
+
+def test_frame_is_the_feature_frame(spl, orc):
+    """spl_frame (a host call) returns the frame of H_w in which the MLP
+    features measure offsets: orthonormal, perpendicular to w, and the
+    oracle's features 4 and 5 of (w, p) are <p, u> sqrt(3)/W and
+    <p, v> sqrt(3)/W (the oracle computes them from the chamber frame of its
+    own, independently written canonicalisation)."""
+    rng = np.random.default_rng(404)
+    w = rng.normal(size=(300, 3))
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    # directions on chamber walls and ties, axis-aligned, negative zeros
+    extra = np.array([[0, 0, 1.0], [0, 1.0, 0], [-1.0, 0, 0], [1, 1, 0], [1, 1, 1], [-1, 1, -1], [0, -1, 1],
+                      [1e-12, 0.3, -0.9], [0.5, 0.5, -0.70710678118654757]])
+    extra /= np.linalg.norm(extra, axis=1, keepdims=True)
+    w = np.concatenate([w, extra])
+    u, v = spl.frame(w)
+    np.testing.assert_allclose(np.sum(u * u, axis=1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(np.sum(v * v, axis=1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(np.sum(u * v, axis=1), 0.0, atol=1e-14)
+    np.testing.assert_allclose(np.sum(u * w, axis=1), 0.0, atol=1e-14)
+    np.testing.assert_allclose(np.sum(v * w, axis=1), 0.0, atol=1e-14)
+    # v = +-(u x w): the sign is the determinant of the direction's signed permutation
+    np.testing.assert_allclose(np.abs(np.sum(v * np.cross(u, w), axis=1)), 1.0, atol=1e-14)
+    for n in (1, 3):
+        sc = np.sqrt(3.0) / (0.5 * (n + 1))
+        for i in range(0, w.shape[0], 7):
+            p = rng.normal(size=3) * 2.0
+            f = orc.features(n, w[i], p)
+            assert abs(f[3] - np.dot(p, u[i]) * sc) <= 1e-12
+            assert abs(f[4] - np.dot(p, v[i]) * sc) <= 1e-12
+    # the frame does not depend on the length of w; zero directions are refused
+    u2, v2 = spl.frame(3.5 * w[:5])
+    np.testing.assert_allclose(u2, u[:5], atol=1e-15)
+    np.testing.assert_allclose(v2, v[:5], atol=1e-15)
+    z = np.zeros((1, 3))
+    st = spl.lib().spl_frame(1, spl._dptr(z), spl._dptr(np.zeros((1, 3))), spl._dptr(np.zeros((1, 3))))
+    assert st == 2

@@ -289,6 +289,93 @@ def test_adjointness(orc, n):
     np.testing.assert_allclose(vals, ATy.reshape(-1)[k], rtol=1e-12, atol=1e-13)
 
 
+def _pin_geometries(orc, rng):
+    par = I.parallel_views(I.random_directions(rng, 4), 9, 7, 1.0, center=(0.31, -0.2, 0.17))
+    cone = I.helical_cone(3, 20.0, 34.0, 11, 8, 1.4, turns=0.7, table_feed=3.0)
+    out = []
+    for geo in (par, cone):
+        kw = dict(det_center=geo.det_center, det_u=geo.det_u, det_v=geo.det_v, nu=geo.nu, nv=geo.nv)
+        if geo.kind == "parallel":
+            out.append(orc.Geometry("parallel", direction=geo.src, **kw))
+        else:
+            out.append(orc.Geometry("cone", source=geo.src, **kw))
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_subset_operators_match_full_operators(orc, n):
+    """forward_subset / adjoint_subset (the checkers of the full-size GPU
+    tests and of the timed CPU baseline) equal the full operators restricted
+    to the same rays: rows of A c, and A^T of a y that is zero off the
+    listed rays; pair counts equal count_pairs per ray."""
+    rng = np.random.default_rng(140 + n)
+    dims = (11, 9, 10)
+    origin = I.centred_origin(dims)
+    c = rng.normal(size=dims[::-1])
+    for g in _pin_geometries(orc, rng):
+        rays = np.sort(rng.choice(g.n_rays, 37, replace=False))
+        full = orc.forward(n, dims, origin, c, g)
+        sub, pairs = orc.forward_subset(n, dims, origin, c, g, rays)
+        np.testing.assert_allclose(sub, full[rays], rtol=1e-13, atol=1e-13 * np.abs(full).max())
+        _, per = orc.count_pairs(n, dims, origin, g, per_ray=True)
+        np.testing.assert_array_equal(pairs, per[rays])
+        ys = rng.normal(size=rays.size)
+        yfull = np.zeros(g.n_rays)
+        yfull[rays] = ys
+        ref = orc.adjoint(n, dims, origin, yfull, g)
+        got, npair = orc.adjoint_subset(n, dims, origin, ys, g, rays)
+        np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+        assert npair == per[rays].sum()
+
+
+def test_adjoint_subset_on_a_large_grid(orc):
+    """Above 2^24 coefficients adjoint_subset adds into one shared buffer
+    with atomic adds instead of per-thread buffers: same sums as the plain
+    serial scatter of orc_adjoint (here on a few rays through a 260 x 255 x
+    256 grid), and the same as the private-buffer mode on a smaller grid."""
+    rng = np.random.default_rng(150)
+    dims = (260, 255, 256)
+    assert dims[0] * dims[1] * dims[2] > (1 << 24)
+    origin = I.centred_origin(dims)
+    geo = I.parallel_views(I.random_directions(rng, 2), 3, 2, 37.0)
+    g = orc.Geometry("parallel", direction=geo.src, det_center=geo.det_center, det_u=geo.det_u, det_v=geo.det_v,
+                     nu=geo.nu, nv=geo.nv)
+    rays = np.arange(g.n_rays)
+    y = rng.uniform(0.5, 1.5, g.n_rays)
+    ref = orc.adjoint(3, dims, origin, y, g)
+    got, npair = orc.adjoint_subset(3, dims, origin, y, g, rays, nthreads=4)
+    nz = np.abs(ref) > 0
+    assert nz.sum() > 10000 and npair == orc.count_pairs(3, dims, origin, g)
+    assert np.array_equal(np.abs(got) > 0, nz)
+    np.testing.assert_allclose(got[nz], ref[nz], rtol=1e-13)
+
+
+def test_windowed_adjoint_at_matches_adjoint_at(orc):
+    """adjoint_at_views (pixel windows of each coefficient's support) gives
+    the same values and pair counts as adjoint_at (every ray tested), for
+    parallel and cone views, coefficients at corners, faces and inside, and a
+    cone whose source sits close enough that some support corners are behind
+    its plane (the whole detector is then kept)."""
+    rng = np.random.default_rng(160)
+    dims = (13, 11, 12)
+    origin = I.centred_origin(dims)
+    close = I.helical_cone(3, 7.0, 16.0, 15, 13, 1.0, turns=0.5, table_feed=2.0)
+    geoms = _pin_geometries(orc, rng) + [orc.Geometry("cone", source=close.src, det_center=close.det_center,
+                                                      det_u=close.det_u, det_v=close.det_v, nu=close.nu,
+                                                      nv=close.nv)]
+    nk = dims[0] * dims[1] * dims[2]
+    k = np.unique(np.concatenate([rng.choice(nk, 40, replace=False),
+                                  [0, dims[0] - 1, nk - 1, nk // 2, dims[0] * dims[1] * 5 + 6]]))
+    for n in (0, 3):
+        for g in geoms:
+            y = rng.normal(size=g.n_rays)
+            ref, pr = orc.adjoint_at(n, dims, origin, y, g, k)
+            got, pg = orc.adjoint_at_views(n, dims, origin, y, g, k)
+            np.testing.assert_array_equal(pg, pr)
+            assert pr.sum() > 0
+            np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
 def test_cone_geometry_rays(orc):
     geo = I.helical_cone(3, 100.0, 150.0, 5, 4, 1.5, turns=1.0, table_feed=6.0)
     g = orc.Geometry("cone", source=geo.src, det_center=geo.det_center, det_u=geo.det_u, det_v=geo.det_v,
