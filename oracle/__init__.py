@@ -100,6 +100,8 @@ def _load():
             lib.orc_mlp_param_count.restype = C.c_longlong
             lib.orc_mlp_param_count.argtypes = [C.c_int, _ip]
             lib.orc_mlp_forward.argtypes = [C.c_int, _ip, _dp, C.c_longlong, _dp, _dp, C.c_int]
+            lib.orc_mlp_flip_variants.restype = C.c_longlong
+            lib.orc_mlp_flip_variants.argtypes = [C.c_int, _ip, _dp, _dp, C.c_double, _dp, C.c_longlong]
             lib.orc_mlp_loss_grad.restype = C.c_double
             lib.orc_mlp_loss_grad.argtypes = [C.c_int, _ip, _dp, C.c_longlong, _dp, _dp, _dp]
             lib.orc_mlp_loss_grad_mode.restype = C.c_double
@@ -371,6 +373,18 @@ def mlp_forward(sizes, params, X, mode: int = 0):
     out = np.zeros(x.shape[0])
     _load().orc_mlp_forward(len(sizes) - 1, sp, pp, x.shape[0], xp, out.ctypes.data_as(_dp), int(mode))
     return out
+
+
+def mlp_flip_variants(sizes, params, x, rel_eps: float, cap: int = 4096):
+    """Outputs of the BF16 contract for one feature row x with a single
+    hidden activation that lies within rel_eps of a BF16 rounding boundary
+    rounded the other way (one value per such activation and direction)."""
+    s, sp = _i(sizes)
+    p, pp = _d(params)
+    xx, xp = _d(np.asarray(x).reshape(-1))
+    out = np.zeros(cap)
+    n = _load().orc_mlp_flip_variants(len(sizes) - 1, sp, pp, xp, float(rel_eps), out.ctypes.data_as(_dp), cap)
+    return out[:min(n, cap)].copy()
 
 
 def mlp_loss_grad(sizes, params, X, Y, mode: int = 0):

@@ -924,8 +924,19 @@ long long orc_mlp_param_count(int nl, const int *sizes)
  * tensor cores in BF16; the first (features -> hidden) and last
  * (hidden -> scalar) layers are FP32 CUDA-core work in the kernel.  The
  * emulation rounds exactly the operands of the hidden-to-hidden layers. */
+/* ov_layer >= 0: in layer ov_layer (a hidden-to-hidden layer) the input
+ * activation ov_unit takes the value ov_value instead of its rounding. */
+static void mlp_forward_ov(int nl, const int *sizes, const double *prm, const double *x, int mode, double *zs,
+                           double *hs, double *out, int ov_layer, int ov_unit, double ov_value);
+
 static void mlp_forward_one(int nl, const int *sizes, const double *prm, const double *x, int mode,
                             double *zs, double *hs, double *out)
+{
+    mlp_forward_ov(nl, sizes, prm, x, mode, zs, hs, out, -1, -1, 0.0);
+}
+
+static void mlp_forward_ov(int nl, const int *sizes, const double *prm, const double *x, int mode, double *zs,
+                           double *hs, double *out, int ov_layer, int ov_unit, double ov_value)
 {
     /* zs, hs: scratch of size sum(sizes[1..nl]) each; hs[0..] hidden outputs */
     const double *in = x;
@@ -944,7 +955,7 @@ static void mlp_forward_one(int nl, const int *sizes, const double *prm, const d
                 double wv = Wl[(long long)o * ni + i], hv = inbuf[i];
                 if (mode != 0) {
                     wv = bf16_round(wv);
-                    if (tensor) hv = act_round(hv, mode);
+                    if (tensor) hv = (li == ov_layer && i == ov_unit) ? ov_value : act_round(hv, mode);
                 }
                 acc += wv * hv;
             }
@@ -957,6 +968,45 @@ static void mlp_forward_one(int nl, const int *sizes, const double *prm, const d
         P += (long long)no * ni + no;
     }
     *out = hs[off - 1];
+}
+
+/* The outputs of the BF16 contract (act_mode 1) with one hidden activation
+ * rounded to its other BF16 neighbour: for every activation h entering a
+ * hidden-to-hidden layer whose rounding changes when h moves by rel_eps |h|
+ * (h lies that close to a BF16 rounding boundary), the network's output
+ * with that single activation rounded the other way.  An evaluation whose
+ * FP32 arithmetic puts such an activation on the other side of the
+ * boundary returns one of these outputs.  Writes at most max_alts values
+ * to alts and returns how many there are (possibly more than max_alts). */
+long long orc_mlp_flip_variants(int nl, const int *sizes, const double *prm, const double *x, double rel_eps,
+                                double *alts, long long max_alts)
+{
+    int tot = 0;
+    for (int i = 1; i <= nl; ++i) tot += sizes[i];
+    double *zs = (double *)malloc(sizeof(double) * tot), *hs = (double *)malloc(sizeof(double) * tot);
+    double *zs2 = (double *)malloc(sizeof(double) * tot), *hs2 = (double *)malloc(sizeof(double) * tot);
+    double base;
+    mlp_forward_ov(nl, sizes, prm, x, 1, zs, hs, &base, -1, -1, 0.0);
+    long long n = 0;
+    int off = 0;
+    for (int li = 0; li + 1 < nl; ++li) {
+        const int no = sizes[li + 1];
+        const int next_tensor = (li + 1 > 0 && li + 1 < nl - 1);
+        for (int o = 0; o < no && next_tensor; ++o) {
+            const double h = hs[off + o], r = bf16_round(h);
+            const double cand[2] = {bf16_round(h - rel_eps * fabs(h)), bf16_round(h + rel_eps * fabs(h))};
+            for (int c = 0; c < 2; ++c) {
+                if (cand[c] == r || (c == 1 && cand[1] == cand[0])) continue;
+                double v;
+                mlp_forward_ov(nl, sizes, prm, x, 1, zs2, hs2, &v, li + 1, o, cand[c]);
+                if (n < max_alts) alts[n] = v;
+                n++;
+            }
+        }
+        off += no;
+    }
+    free(zs); free(hs); free(zs2); free(hs2);
+    return n;
 }
 
 void orc_mlp_forward(int nl, const int *sizes, const double *prm, long long B, const double *X, double *out, int mode)

@@ -211,25 +211,29 @@ def rasterize(ell: Ellipsoids, dims, dtype=np.float64) -> np.ndarray:
     """Additive ellipsoid indicators sampled at the lattice points -> [z][y][x]."""
     nx, ny, nz = (int(v) for v in dims)
     org = centred_origin(dims)
-    xs = org[0] + np.arange(nx)
-    ys = org[1] + np.arange(ny)
     out = np.zeros((nz, ny, nx), dtype=dtype)
+    n = (nx, ny, nz)
     for e in range(ell.centers.shape[0]):
         R = ell.rotations[e]
         a = ell.semi_axes[e]
         c = ell.centers[e]
         rad = float(a.max())
-        z0 = max(0, int(np.floor(c[2] - rad - org[2])))
-        z1 = min(nz - 1, int(np.ceil(c[2] + rad - org[2])))
+        # lattice points within the bounding cube of the ellipsoid
+        lo = [max(0, int(np.floor(c[d] - rad - org[d]))) for d in range(3)]
+        hi = [min(n[d] - 1, int(np.ceil(c[d] + rad - org[d]))) for d in range(3)]
+        if any(hi[d] < lo[d] for d in range(3)):
+            continue
+        xs = org[0] + np.arange(lo[0], hi[0] + 1)
+        ys = org[1] + np.arange(lo[1], hi[1] + 1)
         X, Y = np.meshgrid(xs - c[0], ys - c[1], indexing="xy")
-        for kz in range(z0, z1 + 1):
+        for kz in range(lo[2], hi[2] + 1):
             Z = org[2] + kz - c[2]
             # body coordinates = R^T (x - c)
             bx = R[0, 0] * X + R[1, 0] * Y + R[2, 0] * Z
             by = R[0, 1] * X + R[1, 1] * Y + R[2, 1] * Z
             bz = R[0, 2] * X + R[1, 2] * Y + R[2, 2] * Z
             inside = (bx / a[0]) ** 2 + (by / a[1]) ** 2 + (bz / a[2]) ** 2 <= 1.0
-            out[kz][inside] += ell.densities[e]
+            out[kz, lo[1]:hi[1] + 1, lo[0]:hi[0] + 1][inside] += ell.densities[e]
     return out
 
 
@@ -258,14 +262,17 @@ def ellipsoid_line_integrals(ell: Ellipsoids, s: np.ndarray, w: np.ndarray) -> n
 def bandlimited_noise(rng: np.random.Generator, dims, sigma: float, amplitude: float) -> np.ndarray:
     """White Gaussian noise low-passed by a Gaussian of std `sigma` voxels,
     scaled to standard deviation `amplitude`; float32 [z][y][x]."""
+    import scipy.fft as sfft
+
     nx, ny, nz = (int(v) for v in dims)
     wn = rng.standard_normal((nz, ny, nx)).astype(np.float32)
-    F = np.fft.rfftn(wn)
+    F = sfft.rfftn(wn, workers=-1)
     fz = np.fft.fftfreq(nz)[:, None, None]
     fy = np.fft.fftfreq(ny)[None, :, None]
     fx = np.fft.rfftfreq(nx)[None, None, :]
     H = np.exp(-2.0 * (np.pi * sigma) ** 2 * (fx * fx + fy * fy + fz * fz)).astype(np.float32)
-    out = np.fft.irfftn(F * H, s=(nz, ny, nx), axes=(0, 1, 2)).astype(np.float32)
+    F *= H
+    out = sfft.irfftn(F, s=(nz, ny, nx), axes=(0, 1, 2), workers=-1).astype(np.float32)
     out *= amplitude / max(float(out.std()), 1e-30)
     return out
 
@@ -282,21 +289,29 @@ _INTERP_TAPS = {2: (3.0 / 4.0, 1.0 / 8.0), 3: (2.0 / 3.0, 1.0 / 6.0)}
 def _solve_tridiagonal_axis(x: np.ndarray, diag: float, off: float, axis: int) -> np.ndarray:
     """Solve T c = x along `axis` with T = tridiag(off, diag, off) of the axis
     length (Thomas algorithm, vectorised over the other axes)."""
-    x = np.moveaxis(np.array(x, dtype=np.float64, copy=True), axis, 0)
+    # a contiguous copy with the solve axis first: each step of the sweeps
+    # is then one contiguous slab operation, done in place
+    x = np.ascontiguousarray(np.moveaxis(np.asarray(x, dtype=np.float64), axis, 0))
+    if x.base is not None or not x.flags.writeable:
+        x = x.copy()
     N = x.shape[0]
     cp = np.zeros(N)
-    dp = np.empty_like(x)
+    m = np.zeros(N)
+    m[0] = diag
     cp[0] = off / diag
-    dp[0] = x[0] / diag
     for k in range(1, N):
-        m = diag - off * cp[k - 1]
-        cp[k] = off / m
-        dp[k] = (x[k] - off * dp[k - 1]) / m
-    c = np.empty_like(x)
-    c[N - 1] = dp[N - 1]
+        m[k] = diag - off * cp[k - 1]
+        cp[k] = off / m[k]
+    tmp = np.empty_like(x[0])
+    x[0] /= m[0]
+    for k in range(1, N):
+        np.multiply(x[k - 1], off, out=tmp)
+        x[k] -= tmp
+        x[k] /= m[k]
     for k in range(N - 2, -1, -1):
-        c[k] = dp[k] - cp[k] * c[k + 1]
-    return np.moveaxis(c, 0, axis)
+        np.multiply(x[k + 1], cp[k], out=tmp)
+        x[k] -= tmp
+    return np.moveaxis(x, 0, axis)
 
 
 def prefilter(samples: np.ndarray, degree: int) -> np.ndarray:
@@ -309,7 +324,7 @@ def prefilter(samples: np.ndarray, degree: int) -> np.ndarray:
     diag, off = _INTERP_TAPS[int(degree)]
     for ax in range(out.ndim):
         out = _solve_tridiagonal_axis(out, diag, off, ax)
-    return out
+    return np.ascontiguousarray(out)
 
 
 # --------------------------------------------------------------------------

@@ -7,6 +7,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -66,3 +67,42 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "1"], env=env, capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_stratified_ray_sample_covers_the_classes():
+    """The oracle leg's ray sample: seeded, unique, in range, at least the
+    requested size, and holding detector edge rows and columns, the first
+    and last views."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2511_11078_gb300 import inputs as I
+
+    geo = I.helical_cone(720, 1000.0, 1500.0, 768, 768, 0.8, turns=2.0, table_feed=204.8)
+    r = bench.stratified_rays(geo, 4096, seed=2026)
+    assert np.array_equal(r, bench.stratified_rays(geo, 4096, seed=2026))
+    assert r.size >= 4096 * 0.98 and np.unique(r).size == r.size
+    assert r.min() >= 0 and r.max() < geo.n_rays
+    view, rem = np.divmod(r, geo.nu * geo.nv)
+    iv, iu = np.divmod(rem, geo.nu)
+    assert np.any(view == 0) and np.any(view == geo.n_views - 1)
+    for edge in (iu == 0, iu == geo.nu - 1, iv == 0, iv == geo.nv - 1):
+        assert np.count_nonzero(edge) >= 50
+
+
+def test_ncu_traffic_only_for_current_sources(tmp_path, monkeypatch):
+    """A kernel's DRAM traffic is taken from a committed ncu summary only
+    while the CUDA sources hash to the value the summary names."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    sha = bench.csrc_sha16()
+    (prof / "k.md").write_text("x\ntraffic_bytes_per_launch k_foo wl-a 1.5e9 csrc %s\n"
+                               "traffic_bytes_per_launch k_bar wl-a 2.5e9 csrc 0123456789abcdef\n" % sha)
+    real_glob = bench.glob.glob
+    monkeypatch.setattr(bench.glob, "glob", lambda pat: real_glob(str(prof / "*.md")) if "profiles" in pat
+                        else real_glob(pat))
+    assert bench.ncu_traffic("k_foo", "wl-a") == 1.5e9
+    assert bench.ncu_traffic("k_foo", "wl-b") is None
+    assert bench.ncu_traffic("k_bar", "wl-a") is None  # stale: another source hash

@@ -452,84 +452,142 @@ def test_dot_f64_and_cg_steps(env):
 
 
 # ---------------------------------------------------------------- full size, sampled
-@pytest.fixture(scope="module")
-def tilt128():
-    return I.workload_tilt(3)
+# At the benchmark's sizes and launch configuration (the whole geometry in
+# one call), against the oracle on dense seeded samples: >= 4096 rays per
+# view class (slice-separable tilt views, general parallel views, circular
+# cone, helical cone), stratified to include detector edge rows and columns,
+# the detector centre and the first and last views (ray ends, rays through
+# the truncated volume corners of the cone workloads), and >= 512
+# coefficients of A^T, stratified to include the grid's corners, edges and
+# faces.
+N_RAYS = 4096
+N_COEFFS = 512
 
 
-def test_full_size_forward_sampled(env, orc, tilt128):
-    """128^3 cubic, 244 parallel views of 192x192 (the benchmark's launch
-    configuration): sampled rays against the oracle."""
+def stratified_rays(geo, views, count, seed):
+    """`count` rays of the listed views: 7/8 uniform, the rest on detector
+    edges, the centre and the first and last of the views."""
+    rng = np.random.default_rng(seed)
+    views = np.asarray(views)
+    per = geo.nu * geo.nv
+    k_extra = count // 8
+    v = views[rng.integers(0, views.size, count)]
+    iu = rng.integers(0, geo.nu, count)
+    iv = rng.integers(0, geo.nv, count)
+    which = rng.integers(0, 6, k_extra)
+    e = slice(count - k_extra, count)
+    iu[e] = np.where(which == 0, 0, np.where(which == 1, geo.nu - 1, iu[e]))
+    iv[e] = np.where(which == 2, 0, np.where(which == 3, geo.nv - 1, iv[e]))
+    iu[e] = np.where(which == 4, geo.nu // 2, iu[e])
+    iv[e] = np.where(which == 4, geo.nv // 2, iv[e])
+    v[e] = np.where(which == 5, views[0], v[e])
+    v[count - k_extra:count - k_extra + k_extra // 6] = views[-1]
+    return np.unique((v.astype(np.int64) * geo.nv + iv) * geo.nu + iu)
+
+
+def stratified_coeffs(dims, count, seed):
+    """`count` coefficients: 3/4 uniform, the rest on the grid's corners,
+    edges and faces."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    k = rng.integers(0, [nx, ny, nz], size=(count, 3))
+    m = count // 4
+    for r in range(count - m, count):
+        for d, nd in enumerate((nx, ny, nz)):
+            if rng.uniform() < 0.6:
+                k[r, d] = rng.choice([0, 1, nd - 2, nd - 1])
+    return np.unique((k[:, 2].astype(np.int64) * ny + k[:, 1]) * nx + k[:, 0])
+
+
+def full_size_check(env, orc, wl, class_views, seed):
+    """Forward and adjoint of the whole workload geometry on the GPU; the
+    rays of each view class and the sampled coefficients against the
+    oracle."""
     torch, spl = env
-    wl = tilt128
-    g = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    geo = wl.geometry
+    g = spl.Geometry(wl.dims, wl.origin, geo)
+    og = oracle_geom(orc, geo)
+    c64 = wl.coeffs.astype(np.float64)
     ct = torch.tensor(wl.coeffs, device="cuda")
     y = torch.empty(g.n_rays, dtype=torch.float32, device="cuda")
     spl.forward(g, ct, y, spl.basis(3))
     g.status()
-    rng = np.random.default_rng(2400)
-    rays = np.sort(rng.choice(g.n_rays, 48, replace=False))
-    # include a few rays of the axis-aligned first view
-    rays = np.unique(np.concatenate([rays, [96 * 192 + 96, 100 * 192 + 7]]))
-    yref, pairs = orc.forward_subset(3, wl.dims, wl.origin, wl.coeffs.astype(np.float64),
-                                     oracle_geom(orc, wl.geometry), rays)
-    got = y.cpu().numpy()[rays].astype(np.float64)
-    assert rel_l2(got, yref) <= TOL, rel_l2(got, yref)
-    assert pairs.sum() > 0
-
-
-def test_full_size_adjoint_sampled(env, orc, tilt128):
-    torch, spl = env
-    wl = tilt128
-    g = spl.Geometry(wl.dims, wl.origin, wl.geometry)
-    rng = np.random.default_rng(2500)
-    y = rng.uniform(0, 1, size=g.n_rays).astype(np.float32)
-    c = torch.empty(g.coeff_shape, dtype=torch.float32, device="cuda")
-    spl.adjoint(g, torch.tensor(y, device="cuda"), c, spl.basis(3))
-    g.status()
-    k = np.sort(rng.choice(g.n_coeffs, 24, replace=False))
-    k = np.unique(np.concatenate([k, [0, g.n_coeffs - 1, 64 * 128 * 128 + 64 * 128 + 64]]))
-    ref, _ = orc.adjoint_at(3, wl.dims, wl.origin, y.astype(np.float64), oracle_geom(orc, wl.geometry), k)
-    got = c.cpu().numpy().reshape(-1)[k].astype(np.float64)
-    assert rel_l2(got, ref) <= TOL, rel_l2(got, ref)
-
-
-@pytest.mark.parametrize("which", ["cone256", "helical512"])
-def test_full_size_cone_and_helical_sampled(env, orc, which):
-    """The 256^3 circular cone-beam and 512^3 helical workloads at full
-    volume and detector size, on a subset of their views: sampled rays of A
-    and sampled coefficients of A^T against the oracle."""
-    torch, spl = env
-    if which == "cone256":
-        wl = I.workload_cone()
-        views = [0, 45, 90, 200]
-    else:
-        wl = I.workload_helical()
-        views = [0, 181, 360, 719]
-    geo = wl.geometry.subset_views(views)
-    g = spl.Geometry(wl.dims, wl.origin, geo)
-    c = torch.tensor(wl.coeffs, device="cuda")
-    y = torch.empty(g.n_rays, dtype=torch.float32, device="cuda")
-    spl.forward(g, c, y, spl.basis(3))
-    g.status()
-    rng = np.random.default_rng(2600)
-    rays = np.sort(rng.choice(g.n_rays, 40, replace=False))
-    og = oracle_geom(orc, geo)
-    yref, pairs = orc.forward_subset(3, wl.dims, wl.origin, wl.coeffs.astype(np.float64), og, rays)
-    got = y.cpu().numpy()[rays].astype(np.float64)
-    assert pairs.sum() > 0
-    assert rel_l2(got, yref) <= TOL, rel_l2(got, yref)
+    yh = y.cpu().numpy().astype(np.float64)
+    for name, views in class_views.items():
+        rays = stratified_rays(geo, views, N_RAYS, seed)
+        assert rays.size >= N_RAYS * 0.97
+        yref, pairs = orc.forward_subset(3, wl.dims, wl.origin, c64, og, rays)
+        assert pairs.sum() > 0, name
+        err = rel_l2(yh[rays], yref)
+        assert err <= TOL, (name, err)
+    rng = np.random.default_rng(seed + 1)
     yv = rng.uniform(0, 1, size=g.n_rays).astype(np.float32)
-    cb = torch.empty(g.coeff_shape, dtype=torch.float32, device="cuda")
+    cb = torch.full(g.coeff_shape, float("nan"), dtype=torch.float32, device="cuda")
     spl.adjoint(g, torch.tensor(yv, device="cuda"), cb, spl.basis(3))
     g.status()
-    n = int(np.prod(wl.dims))
-    ctr = ((np.array(wl.dims[::-1]) // 2) * np.array([wl.dims[0] * wl.dims[1], wl.dims[0], 1])).sum()
-    k = np.unique(np.concatenate([rng.choice(n, 12, replace=False), [ctr, ctr + 7, ctr + 3 * wl.dims[0]]]))
-    ref, npair = orc.adjoint_at(3, wl.dims, wl.origin, yv.astype(np.float64), og, k)
-    gotc = cb.cpu().numpy().reshape(-1)[k].astype(np.float64)
-    assert npair.sum() > 0
-    assert rel_l2(gotc, ref) <= TOL, rel_l2(gotc, ref)
+    k = stratified_coeffs(wl.dims, N_COEFFS + 40, seed + 2)
+    assert k.size >= N_COEFFS
+    ref, npair = orc.adjoint_at_views(3, wl.dims, wl.origin, yv.astype(np.float64), og, k)
+    got = cb.cpu().numpy().reshape(-1)[k].astype(np.float64)
+    assert np.isfinite(got).all() and npair.sum() > 0
+    err = rel_l2(got, ref)
+    assert err <= TOL, err
+
+
+def test_full_size_tilt128(env, orc):
+    """128^3 cubic, 244 parallel views of 192x192: the 180 slice-separable
+    tilt views (plane matrices) and the 64 general views (piece march)."""
+    wl = I.workload_tilt(3)
+    src = np.asarray(wl.geometry.src)
+    flat = np.nonzero(np.any(src == 0.0, axis=1))[0]
+    gen = np.nonzero(~np.any(src == 0.0, axis=1))[0]
+    full_size_check(env, orc, wl, {"separable": flat, "general": gen}, 2400)
+
+
+def test_full_size_cone256(env, orc):
+    """256^3 cubic, circular cone beam, 360 views of 384x384 (the detector
+    truncates the volume corners)."""
+    wl = I.workload_cone()
+    full_size_check(env, orc, wl, {"cone": np.arange(wl.geometry.n_views)}, 2600)
+
+
+def test_full_size_helical512(env, orc):
+    """512^3 cubic, helical cone beam, 720 views of 768x768: the benchmark's
+    headline workload in its launch configuration."""
+    wl = I.workload_helical()
+    full_size_check(env, orc, wl, {"helical": np.arange(wl.geometry.n_views)}, 2700)
+
+
+def test_unprepared_basis_is_refused(env):
+    """spl_forward / spl_adjoint allocate nothing: through the C ABI, a basis
+    whose plane matrices (or footprint tables) the geometry has not built is
+    refused with SPL_ERR_STATE until spl_prepare has run; a geometry that
+    needs nothing (cone views) runs without it."""
+    import ctypes as C
+
+    torch, spl = env
+    L = spl.lib()
+    origin = I.centred_origin(DIMS)
+    st = torch.cuda.current_stream().cuda_stream
+    g = spl.Geometry(DIMS, origin, tilt_geometry(2))
+    c = torch.ones(g.coeff_shape, dtype=torch.float32, device="cuda")
+    y = torch.zeros(g.n_rays, dtype=torch.float32, device="cuda")
+    for mode in (spl.SPL_FP_QUAD, spl.SPL_FP_TABLE):
+        b = spl.basis(3, mode)
+        assert L.spl_forward(g.handle, C.byref(b), spl._ptr(c), spl._ptr(y), C.c_void_p(st)) == 6
+        assert L.spl_adjoint(g.handle, C.byref(b), spl._ptr(y), spl._ptr(c), C.c_void_p(st)) == 6
+        assert b"spl_prepare" in L.spl_last_error()
+        assert L.spl_prepare(g.handle, C.byref(b), C.c_void_p(st)) == 0
+        assert L.spl_forward(g.handle, C.byref(b), spl._ptr(c), spl._ptr(y), C.c_void_p(st)) == 0
+    torch.cuda.synchronize()
+    g.status()
+    assert float(y.abs().max()) > 0
+    gc = spl.Geometry(DIMS, origin, cone_geometry())
+    yc = torch.zeros(gc.n_rays, dtype=torch.float32, device="cuda")
+    b = spl.basis(3)
+    assert L.spl_forward(gc.handle, C.byref(b), spl._ptr(c), spl._ptr(yc), C.c_void_p(st)) == 0
+    torch.cuda.synchronize()
+    gc.status()
 
 
 def test_cuda_graph_capture_of_mixed_geometry(env):

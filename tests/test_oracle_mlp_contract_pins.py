@@ -177,3 +177,39 @@ def test_contract_gradient_passes_roundings_straight_through(orc):
     for j in range(5):
         ref = 2 * np.mean(res * np.array(d1) * X[:, j])
         assert abs(g[OFF_W1 + 5 * k + j] - ref) <= 1e-13 * max(1.0, abs(ref))
+
+
+def test_flip_variants_round_the_near_boundary_activation_the_other_way(orc):
+    """mlp_flip_variants returns, for an activation within rel_eps of a BF16
+    rounding boundary, the output with that activation rounded to its other
+    BF16 neighbour; on the chain network the expected value is computed by
+    hand with the independent rounding above."""
+    k = 5
+    rng = np.random.default_rng(950)
+    w1 = np.array([bf16_nearest(v) for v in rng.uniform(-1.0, 1.0, 5)])
+    w4, b2, b3, b4 = bf16_nearest(1.25), -0.2718281828459045, 0.1234567890123, 0.0987654321
+    x = rng.uniform(-1.0, 1.0, 5)
+    # first activation just below the midpoint of the BF16 pair (lo, lo + 2^-7) near 1.3
+    lo = bf16_nearest(1.3)
+    mid = lo + 2.0 ** -8
+    h_target = mid * (1.0 - 1e-7)
+    z1 = 1.3
+    for _ in range(60):  # Newton on silu(z) = h_target
+        z1 -= (silu(z1) - h_target) / dsilu(z1)
+    b1 = z1 - float(np.dot(w1, x))
+    prm = chain_network(k, w1, b1, b2, b3, w4, b4)
+    _, (z1c, _, _) = chain_out(x, w1, b1, b2, b3, w4, b4, rounded=True)
+    h1 = silu(z1c)
+    assert bf16_nearest(h1) == lo and abs(h1 - mid) < 1e-6 * mid
+    # the same chain with the first activation rounded up instead of down
+    z2 = (lo + 2.0 ** -7) + b2
+    z3 = bf16_nearest(silu(z2)) + b3
+    flipped = w4 * silu(z3) + b4
+    alts = orc.mlp_flip_variants(SIZES, prm, x, 1e-6)
+    assert np.min(np.abs(alts - flipped)) <= 1e-15 * max(1.0, abs(flipped)), (alts, flipped)
+    base = orc.mlp_forward(SIZES, prm, x[None, :], mode=1)[0]
+    assert abs(flipped - base) > 1e-4
+    # a tolerance below the activation's distance to the boundary gives no
+    # variant of it
+    alts_tight = orc.mlp_flip_variants(SIZES, prm, x, 1e-9)
+    assert alts_tight.size == 0 or np.min(np.abs(alts_tight - flipped)) > 1e-9
