@@ -442,6 +442,25 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
         if (d.kind == SPL_PARALLEL) dg.view_order = (const int *)((const char *)blk + order_off);
     }
     dg.err = (int *)((char *)blk + flag_off);
+    // The scatter adjoint of a geometry with more than one batch of views
+    // (rays) adds the batches in an FP64 accumulator of the grid's size
+    // (scratch sized here, so the adjoint itself allocates nothing).
+    const long long nk = (long long)dg.n[0] * dg.n[1] * dg.n[2];
+    const bool batched = d.kind == SPL_RAYS ? dg.n_rays > kAdjBatchRays : d.n_views > kAdjBatchViews;
+    g->acc64 = nullptr;
+    if (batched && dg.n_rays > 0) {
+        ce = cudaMalloc((void **)&g->acc64, (size_t)nk * sizeof(double));
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            g->acc64 = nullptr;
+            cudaFree(blk);
+            plane_free(g->plane);
+            free(g->vconst);
+            free(g->views_host);
+            free(g);
+            return fail(SPL_ERR_OOM, "cudaMalloc of the adjoint accumulator (%lld doubles) failed", nk);
+        }
+    }
     *out = g;
     return SPL_OK;
 }
@@ -452,6 +471,7 @@ extern "C" void spl_destroy_geometry(spl_geometry *g)
     plane_free(g->plane);
     table_free(g->table);
     free(g->vconst);
+    if (g->acc64) cudaFree(g->acc64);
     if (g->dev_block) cudaFree(g->dev_block);
     free(g->views_host);
     free(g);

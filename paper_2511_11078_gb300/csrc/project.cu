@@ -329,12 +329,13 @@ __device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float 
     if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
 }
 
+// rays r0 .. r1-1
 template <int N>
 __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__restrict__ y, float *__restrict__ c,
-                                                      QuadRule qr)
+                                                      QuadRule qr, long long r0, long long r1)
 {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= g.n_rays) return;
+    const long long r = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= r1) return;
     const float yr = y[r];
     if (yr == 0.0f) return;
     double s[3], w[3];
@@ -343,14 +344,15 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
     if (ray_setup<N>(grid_of(g), s, w, rs)) scatter_ray<N, VM_RAYS>(rs, yr, c, qr, g.err);
 }
 
-// view geometries, scatter form: the forward's thread mapping, float atomics
+// view geometries, scatter form: the forward's thread mapping, float
+// atomics; views v0 + blockIdx.z
 template <int N>
 __global__ void __launch_bounds__(128, 3)
-    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr)
+    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr, int v0)
 {
     int iu, iv;
     tile_pixel(iu, iv);
-    const int k = blockIdx.z;
+    const int k = v0 + blockIdx.z;
     if (iu >= g.nu || iv >= g.nv) return;
     const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
     if (yr == 0.0f) return;
@@ -568,6 +570,20 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_bricks(DevGeom g, const
 
 constexpr size_t kAdjSmem = kBrickVol * (sizeof(double) + sizeof(float));
 
+// Batched scatter: acc += c (FP64 total of the batches), and c = acc at the
+// end.  Grid-strided, coalesced.
+__global__ void k_acc_add(long long n, double *__restrict__ acc, const float *__restrict__ c)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) acc[i] += (double)c[i];
+}
+
+__global__ void k_acc_store(long long n, const double *__restrict__ acc, float *__restrict__ c)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) c[i] = (float)acc[i];
+}
+
 }  // namespace spl
 
 using namespace spl;
@@ -578,16 +594,23 @@ static spl_status launch_status(const char *what)
 }
 
 // Launch `launch(chunk, n)` for the parallel views view_order[v0 .. v0+count)
-// in chunks of at most kViewChunk, each with its views' constants.
+// in chunks of at most `per` (<= kViewChunk) views, each with its views'
+// constants.
 template <class F>
-static void for_view_chunks(const spl_geometry *g, int v0, int count, F launch)
+static void for_view_chunks(const spl_geometry *g, int v0, int count, F launch, int per = kViewChunk)
 {
     static thread_local ViewChunk ch;
-    for (int s = 0; s < count; s += kViewChunk) {
-        const int n = count - s < kViewChunk ? count - s : kViewChunk;
+    for (int s = 0; s < count; s += per) {
+        const int n = count - s < per ? count - s : per;
         memcpy(ch.v, g->vconst + v0 + s, (size_t)n * sizeof(ViewConst));
         launch(ch, n);
     }
+}
+
+static unsigned stream_grid(long long n)
+{
+    const long long b = (n + 255) / 256, cap = 8LL * sm_count();
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 // Parallel geometries: the separable group through the plane matrices
@@ -678,7 +701,7 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
     const QuadRule qr = quad_rule(N);
     const int form = b->adjoint;
     const long long nc = (long long)dg.n[0] * dg.n[1] * dg.n[2];
-    spl_status s;
+    spl_status s = SPL_OK;
     int v0 = 0;
     if (dg.kind == SPL_PARALLEL) {
         v0 = plane_views(g, b, &s);
@@ -712,27 +735,69 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
         if (s != SPL_OK) return s;
     }
     if (dg.n_rays == 0) return SPL_OK;
+    // The scatter adds y_r * F_l with FP32 atomics.  A coefficient of a
+    // large geometry receives tens of thousands of them (512^3 helical:
+    // ~4e4), and an FP32 running sum of that many terms loses ~1e-5 of its
+    // value; so a geometry with more than one batch of views (rays) scatters
+    // each batch into the cleared c and adds the batch to an FP64 total
+    // (its scratch, acc64, is allocated with the geometry), which is
+    // rounded to c at the end.  Each batch's FP32 sum has ~1/B of the terms
+    // and of the magnitude, so its rounding error is ~1/B of the whole.
+    const bool batched = g->acc64 != nullptr;
+    auto begin_batch = [&]() -> spl_status {
+        if (!batched) return SPL_OK;
+        return cuda_check(cudaMemsetAsync(c, 0, nc * sizeof(float), st), "adjoint batch clear");
+    };
+    auto end_batch = [&]() {
+        if (batched) k_acc_add<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);
+    };
+    if (batched && form != SPL_ADJ_GATHER) {
+        s = cuda_check(cudaMemsetAsync(g->acc64, 0, nc * sizeof(double), st), "adjoint accumulator clear");
+        if (s != SPL_OK) return s;
+        // the plane path already wrote its part into c (no side stream):
+        // it enters the total first
+        if (v0 > 0 && !overlap) end_batch();
+    }
     if (dg.kind == SPL_RAYS) {
-        const long long blocks = (dg.n_rays + 127) / 128;
-        k_adjoint_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, y, c, qr);
+        for (long long r0 = 0; r0 < dg.n_rays; r0 += kAdjBatchRays) {
+            const long long r1 = r0 + kAdjBatchRays < dg.n_rays ? r0 + kAdjBatchRays : dg.n_rays;
+            if ((s = begin_batch()) != SPL_OK) return s;
+            k_adjoint_rays<N><<<(unsigned)((r1 - r0 + 127) / 128), 128, 0, st>>>(dg, y, c, qr, r0, r1);
+            end_batch();
+        }
+        if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);
         return launch_status("adjoint launch");
     }
     if (form != SPL_ADJ_GATHER) {
         const unsigned gx = (dg.nu + 15) / 16, gy = (dg.nv + 7) / 8;
+        const int per = batched ? kAdjBatchViews : kViewChunk;
         if (dg.kind == SPL_PARALLEL) {
             for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
+                if (s == SPL_OK) s = begin_batch();
                 k_adjoint_pviews_scatter<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
-            });
+                end_batch();
+            }, per);
             for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
+                if (s == SPL_OK) s = begin_batch();
                 k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
-            });
+                end_batch();
+            }, per);
+            if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);
             if (overlap) {
-                s = cuda_check(cudaStreamWaitEvent(st, g->plane->join, 0), "join wait");
+                const spl_status sj = cuda_check(cudaStreamWaitEvent(st, g->plane->join, 0), "join wait");
+                if (s == SPL_OK) s = sj;
                 if (s == SPL_OK) s = plane_adjoint_add(g, N, c, st);
-                if (s != SPL_OK) return s;
             }
+            if (s != SPL_OK) return s;
         } else {
-            k_adjoint_views_scatter<N><<<dim3(gx, gy, dg.n_views), 128, 0, st>>>(dg, y, c, qr);
+            const int per_launch = batched ? kAdjBatchViews : dg.n_views;
+            for (int k0 = 0; k0 < dg.n_views; k0 += per_launch) {
+                const int nview = dg.n_views - k0 < per_launch ? dg.n_views - k0 : per_launch;
+                if ((s = begin_batch()) != SPL_OK) return s;
+                k_adjoint_views_scatter<N><<<dim3(gx, gy, nview), 128, 0, st>>>(dg, y, c, qr, k0);
+                end_batch();
+            }
+            if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);
         }
         return launch_status("adjoint launch");
     }

@@ -20,8 +20,16 @@ struct spl_geometry {
     int device;
     spl::PlaneGroup *plane;       // slice-separable view group (parallel geometries), or NULL
     spl::ViewConst *vconst;       // parallel geometries: per-view constants in view_order order (host)
-    spl::TableSet *table;         // footprint tables (SPL_FP_TABLE), built on first use per degree, or NULL
+    spl::TableSet *table;         // footprint tables (SPL_FP_TABLE), built by spl_prepare, or NULL
+    double *acc64;                // FP64 accumulator of the scatter adjoint's batches (nx*ny*nz), or NULL
 };
+
+namespace spl {
+// The scatter adjoint adds each batch of at most this many views (rays) in
+// FP32 atomics and the batches in FP64 (see adjoint_quad).
+constexpr int kAdjBatchViews = 48;
+constexpr long long kAdjBatchRays = 1LL << 22;
+}
 
 namespace spl {
 

@@ -558,6 +558,32 @@ def test_full_size_helical512(env, orc):
     full_size_check(env, orc, wl, {"helical": np.arange(wl.geometry.n_views)}, 2700)
 
 
+@pytest.mark.parametrize("kind", ["cone", "parallel"])
+def test_adjoint_batched_over_views(env, orc, kind):
+    """Geometries with more than 48 views scatter the adjoint in batches of
+    views (FP32 atomics) added in an FP64 total: the result matches the
+    oracle, for cone views and for parallel views with separable,
+    flat and general classes (the plane path's part joins the total)."""
+    torch, spl = env
+    rng = np.random.default_rng(1200)
+    dims = (14, 13, 12)
+    origin = I.centred_origin(dims)
+    if kind == "cone":
+        geo = I.helical_cone(101, 40.0, 70.0, 9, 8, 2.2, turns=1.3, table_feed=4.0)
+    else:
+        t = tilt_geometry(2, n_views=40, nu=13, nv=11)
+        extra = I.parallel_views(I.random_directions(rng, 70), 13, 11, 1.0, center=(0.2, 0.1, -0.3))
+        geo = I.ViewGeometry("parallel", np.concatenate([t.src, extra.src]),
+                             np.concatenate([t.det_center, extra.det_center]), np.concatenate([t.det_u, extra.det_u]),
+                             np.concatenate([t.det_v, extra.det_v]), 13, 11)
+    assert geo.n_views > 48
+    y = rng.uniform(0, 1, geo.n_rays)
+    got = gpu_adjoint(env, dims, origin, geo, y, 3, form=2)
+    ref = orc.adjoint(3, dims, origin, y.astype(np.float32).astype(np.float64), oracle_geom(orc, geo))
+    assert np.isfinite(got).all()
+    assert rel_l2(got, ref) <= TOL, rel_l2(got, ref)
+
+
 def test_unprepared_basis_is_refused(env):
     """spl_forward / spl_adjoint allocate nothing: through the C ABI, a basis
     whose plane matrices (or footprint tables) the geometry has not built is
