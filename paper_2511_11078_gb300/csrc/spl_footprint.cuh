@@ -19,6 +19,10 @@ struct PointSink {
         __device__ __forceinline__ bool in0(int d) const { return d == 0; }
         __device__ __forceinline__ bool in1(int a) const { return a == 0; }
         __device__ __forceinline__ bool in2(int b) const { return b == 0; }
+        __device__ __forceinline__ bool cube_in(int d0, int a0, int b0, int n) const
+        {
+            return n == 0 && d0 == 0 && a0 == 0 && b0 == 0;
+        }
     } bx;
     __device__ __forceinline__ void put(unsigned, bool in, float val, int)
     {

@@ -225,6 +225,10 @@ template <int N> struct GL { static constexpr int M = (3 * N + 2) / 2 > 0 ? (3 *
 // inner ones use the mirror symmetry B_{N,i}(g) = B_{N,N-i}(1 - g):
 //   cubic:     w1 = 2/3 - g^2 (1 - g/2),  w2 = 2/3 - t^2 (1 - t/2)
 //   quadratic: w1 = 1/2 + g t
+// The mirror pairs (w_i, w_{N-i}) are evaluated as one packed FP32x2 pair
+// (g, t): each component rounds like the scalar operation in the same
+// order, so the weights are those of the scalar formulas in fewer
+// instructions.
 template <int N>
 __device__ __forceinline__ void bweights(float g, float (&w)[N + 1])
 {
@@ -235,15 +239,22 @@ __device__ __forceinline__ void bweights(float g, float (&w)[N + 1])
         w[0] = t;
         w[1] = g;
     } else if constexpr (N == 2) {
-        w[0] = 0.5f * t * t;
+        // (0.5 g) g and (0.5 t) t
+        const float2 gt = make_float2(g, t);
+        const float2 e = __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), gt), gt);
+        w[0] = e.y;
         w[1] = fmaf(g, t, 0.5f);
-        w[2] = 0.5f * g * g;
+        w[2] = e.x;
     } else {
-        const float g2 = g * g, t2 = t * t;
-        w[0] = t2 * t * (1.0f / 6.0f);
-        w[1] = fmaf(-g2, fmaf(-0.5f, g, 1.0f), 2.0f / 3.0f);
-        w[2] = fmaf(-t2, fmaf(-0.5f, t, 1.0f), 2.0f / 3.0f);
-        w[3] = g2 * g * (1.0f / 6.0f);
+        const float2 gt = make_float2(g, t);
+        const float2 sq = __fmul2_rn(gt, gt);                                           // g^2, t^2
+        const float2 cu = __fmul2_rn(__fmul2_rn(sq, gt), make_float2(1.0f / 6.0f, 1.0f / 6.0f));  // w3, w0
+        const float2 in = __ffma2_rn(make_float2(-0.5f, -0.5f), gt, make_float2(1.0f, 1.0f));
+        const float2 md = __ffma2_rn(make_float2(-sq.x, -sq.y), in, make_float2(2.0f / 3.0f, 2.0f / 3.0f));  // w1, w2
+        w[0] = cu.y;
+        w[1] = md.x;
+        w[2] = md.y;
+        w[3] = cu.x;
     }
 }
 
@@ -491,6 +502,13 @@ struct SinkBox {
     __device__ __forceinline__ bool in0(int d) const { return (unsigned)(d - lo0) <= ext0; }
     __device__ __forceinline__ bool in1(int a) const { return (unsigned)(a - lo1) <= ext1; }
     __device__ __forceinline__ bool in2(int b) const { return (unsigned)(b - lo2) <= ext2; }
+    // whether the cube [d0, d0+n] x [a0, a0+n] x [b0, b0+n] lies inside the region
+    __device__ __forceinline__ bool cube_in(int d0, int a0, int b0, int n) const
+    {
+        return (unsigned)(d0 - lo0) + (unsigned)n <= ext0 && (unsigned)(d0 - lo0) <= ext0 &&
+               (unsigned)(a0 - lo1) + (unsigned)n <= ext1 && (unsigned)(a0 - lo1) <= ext1 &&
+               (unsigned)(b0 - lo2) + (unsigned)n <= ext2 && (unsigned)(b0 - lo2) <= ext2;
+    }
     // whether the window [d0, d1] x [a0, a1] x [b0, b1] meets the region
     __device__ __forceinline__ bool meets(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
@@ -859,20 +877,32 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
             const unsigned base = sink.off + (unsigned)bd * (unsigned)sink.S0 + (unsigned)ba * (unsigned)sink.S1 +
                                   (unsigned)bb * (unsigned)sink.S2;
             const unsigned SX = (unsigned)(evD ? sink.S1 : sink.S0), SY = (unsigned)(evB ? sink.S1 : sink.S2);
-            const bool vf = evA ? sink.bx.in1(ba) : (evB ? sink.bx.in2(bb) : sink.bx.in0(bd));
-            bool vx[N + 1], vy[N + 1];
+            if (sink.bx.cube_in(bd, ba, bb, N)) {
+                // the whole window lies in the region (most pieces): every
+                // face entry is in, no per-entry tests
 #pragma unroll
-            for (int x = 0; x <= N; ++x) {
-                vx[x] = vf && (evD ? sink.bx.in1(ba + x) : sink.bx.in0(bd + x));
-                vy[x] = evB ? sink.bx.in1(ba + x) : sink.bx.in2(bb + x);
-            }
+                for (int x = 0; x <= N; ++x)
 #pragma unroll
-            for (int x = 0; x <= N; ++x)
+                    for (int y = 0; y <= N; ++y) {
+                        const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
+                        sink.put(base + (unsigned)x * SX + (unsigned)y * SY, true, v, y);
+                    }
+            } else {
+                const bool vf = evA ? sink.bx.in1(ba) : (evB ? sink.bx.in2(bb) : sink.bx.in0(bd));
+                bool vx[N + 1], vy[N + 1];
 #pragma unroll
-                for (int y = 0; y <= N; ++y) {
-                    const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
-                    sink.put(base + (unsigned)x * SX + (unsigned)y * SY, vx[x] && vy[y], v, y);
+                for (int x = 0; x <= N; ++x) {
+                    vx[x] = vf && (evD ? sink.bx.in1(ba + x) : sink.bx.in0(bd + x));
+                    vy[x] = evB ? sink.bx.in1(ba + x) : sink.bx.in2(bb + x);
                 }
+#pragma unroll
+                for (int x = 0; x <= N; ++x)
+#pragma unroll
+                    for (int y = 0; y <= N; ++y) {
+                        const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
+                        sink.put(base + (unsigned)x * SX + (unsigned)y * SY, vx[x] && vy[y], v, y);
+                    }
+            }
         }
         // shift along the event's axis (in place: reads only higher indices)
 #pragma unroll

@@ -584,6 +584,26 @@ def test_adjoint_batched_over_views(env, orc, kind):
     assert rel_l2(got, ref) <= TOL, rel_l2(got, ref)
 
 
+def test_adjoint_staged_fallbacks(env, orc):
+    """The staged scatter's two fallbacks to direct global atomics: a coarse
+    detector whose 16 x 8 pixel tiles reach a region larger than the
+    staging buffer, and a cone whose rays within one tile have different
+    dominant axes or mirror signs (source close to the grid, 45-degree
+    views)."""
+    torch, spl = env
+    rng = np.random.default_rng(1300)
+    dims = (48, 46, 44)
+    origin = I.centred_origin(dims)
+    coarse = I.parallel_views(np.array([[0.3, 0.5, 0.8], [0.9, -0.1, 0.4]]), 16, 8, 4.3)
+    close = I.helical_cone(3, 30.0, 60.0, 19, 17, 3.0, turns=0.375, table_feed=2.0)
+    for geo in (coarse, close):
+        y = rng.uniform(0, 1, geo.n_rays)
+        got = gpu_adjoint(env, dims, origin, geo, y, 3, form=2)
+        ref = orc.adjoint(3, dims, origin, y.astype(np.float32).astype(np.float64), oracle_geom(orc, geo))
+        assert np.isfinite(got).all()
+        assert rel_l2(got, ref) <= TOL, rel_l2(got, ref)
+
+
 def test_unprepared_basis_is_refused(env):
     """spl_forward / spl_adjoint allocate nothing: through the C ABI, a basis
     whose plane matrices (or footprint tables) the geometry has not built is
