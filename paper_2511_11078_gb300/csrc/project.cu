@@ -396,18 +396,33 @@ __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
 // rays do not share the mirrored frame (dominant axis and signs), and
 // segments whose region exceeds the staging buffer, add to global memory
 // directly.
+//
+// The staging buffer holds 32-bit fixed-point sums (integer shared-memory
+// atomics are single instructions; float ones are not).  Scale: a flushed
+// footprint F_l of a segment is a partial integral of the basis's d-factor
+// times two weights <= 1, so F_l <= 1, and 1/|w_d| <= sqrt(3); every
+// contribution y_r F_l / |w_d| is then at most 2 Ymax in magnitude, Ymax the
+// largest |y_r| of the block, and is rounded to the quantum
+// q = 2 Ymax / 2^21 (a single rounding of at most q/2 ~ 5e-7 Ymax).  A basis
+// receives at most one contribution per ray of the block in a segment, so
+// its sum stays below 128 x 2^21 = 2^28 (no overflow); integer sums are
+// exact, and the flush converts them back to float.
 constexpr int kSegCells = 8;
-constexpr int kStageFloats = 12288;  // 48 KB per block
-constexpr size_t kStageSmem = kStageFloats * sizeof(float);
+constexpr int kStageWords = 12288;  // 48 KB per block
+constexpr size_t kStageSmem = kStageWords * sizeof(int);
+
+// x rounded to the nearest integer, for |x| < 2^22: adding 1.5 2^23 puts the
+// integer part in the float's mantissa (unit last place = 1)
+__device__ __forceinline__ int fixed_round(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
 
 struct StageSink {
     static constexpr bool plane = false;
-    float *buf;
+    int *buf;
     int S0, S1, S2;  // buffer strides of (d, a, b)
     unsigned off;
     SinkBox bx;      // the grid (mirrored frame)
     unsigned size;
-    float yv;
+    float yv;        // y_r / |w_d| / q
     bool over;       // a basis fell outside the buffer (the region bounds rule it out)
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
@@ -421,7 +436,7 @@ struct StageSink {
     __device__ __forceinline__ void put(unsigned o, bool in, float v, int)
     {
         if (in) {
-            if (o < size) atomicAdd(buf + o, yv * v);
+            if (o < size) atomicAdd(buf + o, fixed_round(yv * v));
             else over = true;
         }
     }
@@ -438,8 +453,9 @@ __device__ __forceinline__ int frame_key(const RaySetup &rs)
 // Add the staging buffer (region origin R0 in the mirrored frame, extents
 // E, buffer strides T; the x axis has stride 1 in the buffer) to c.  Each
 // warp takes whole rows along x, so its atomics are coalesced.
-__device__ __forceinline__ void stage_flush(const float *stage, float *__restrict__ c, int key, const int (&n)[3],
-                                            const int (&R0)[3], const int (&E)[3], const int (&T)[3])
+__device__ __forceinline__ void stage_flush(const int *stage, float q, float *__restrict__ c, int key,
+                                            const int (&n)[3], const int (&R0)[3], const int (&E)[3],
+                                            const int (&T)[3])
 {
     const int ax0 = key & 3, ax1 = (key >> 2) & 3, ax2 = 3 - ax0 - ax1;
     const int st0 = ax0 == 0 ? 1 : (ax0 == 1 ? n[0] : n[0] * n[1]);
@@ -460,11 +476,11 @@ __device__ __forceinline__ void stage_flush(const float *stage, float *__restric
     const int rows = E1 * E2;
     for (int row = warp; row < rows; row += blockDim.x >> 5) {
         const int u1 = row % E1, u2 = row / E1;
-        const float *src = stage + u1 * T1 + u2 * T2;
+        const int *src = stage + u1 * T1 + u2 * T2;
         const int ob = base + u1 * Sg_1 + u2 * Sg_2;
         for (int uf = lane; uf < Ef; uf += 32) {
-            const float v = src[uf];
-            if (v != 0.0f) atomicAdd(c + (ob + uf * Sgf), v);
+            const int v = src[uf];
+            if (v != 0) atomicAdd(c + (ob + uf * Sgf), (float)v * q);
         }
     }
 }
@@ -474,8 +490,8 @@ template <int N, int VM>
 __device__ __forceinline__ void staged_body(const DevGeom &g, const float *__restrict__ y, float *__restrict__ c,
                                             const QuadRule &qr, int k, const ViewConst *V)
 {
-    extern __shared__ __align__(16) float stage[];
-    __shared__ int red[8];  // frame key min/max, then the region's d, a, b ranges
+    extern __shared__ __align__(16) int stage[];
+    __shared__ int red[9];  // frame key min/max, then the region's d, a, b ranges; Ymax
     const int tid = threadIdx.x;
     int iu, iv;
     tile_pixel(iu, iv);
@@ -496,6 +512,7 @@ __device__ __forceinline__ void staged_body(const DevGeom &g, const float *__res
         red[1] = -1;
         red[2] = 0x7fffffff;
         red[3] = -0x7fffffff;
+        red[8] = 0;
     }
     __syncthreads();
     if (active) {
@@ -504,15 +521,20 @@ __device__ __forceinline__ void staged_body(const DevGeom &g, const float *__res
         atomicMax(&red[1], key);
         atomicMin(&red[2], rs.c0);
         atomicMax(&red[3], rs.c1);
+        atomicMax(&red[8], __float_as_int(fabsf(yr)));  // non-negative floats order as integers
     }
     __syncthreads();
     const int key = red[0], kmax = red[1], Cmin = red[2], Cmax = red[3];
+    const float ymax = __int_as_float(red[8]);
     __syncthreads();
     if (kmax < 0) return;  // no ray of the block meets the grid (block-uniform)
     if (key != kmax) {     // rays of the block in different mirrored frames (block-uniform)
         if (active) scatter_ray<N, VM>(rs, yr, c, qr, g.err);
         return;
     }
+    // fixed-point quantum q = 2 Ymax / 2^21 (a power-of-two multiple of Ymax
+    // would do as well; this one is exact to FP32 rounding)
+    const float q = ymax * (2.0f / 2097152.0f), inv_q = 2097152.0f / (2.0f * ymax);
     const float yv = active ? yr * rs.inv_wd : 0.0f;
     bool bad = false;
 #pragma unroll 1
@@ -564,7 +586,7 @@ __device__ __forceinline__ void staged_body(const DevGeom &g, const float *__res
         __syncthreads();
         if (E[0] <= 0) continue;  // no ray reaches the grid in this segment (block-uniform)
         const long long vol = (long long)E[0] * E[1] * E[2];
-        if (vol > kStageFloats) {
+        if (vol > kStageWords || !(ymax < 1e30f)) {
             // region too large for the buffer: add to global memory directly
             if (run) {
                 AtomicSink sk;
@@ -587,7 +609,7 @@ __device__ __forceinline__ void staged_body(const DevGeom &g, const float *__res
         T[0] = qf == 0 ? 1 : (qf == 1 ? E[1] : E[2]);
         T[1] = qf == 1 ? 1 : (qf == 0 ? E[0] : E[2] * E[0]);
         T[2] = qf == 2 ? 1 : (qf == 0 ? E[0] * E[1] : E[1] * E[0]);
-        for (int i = tid; i < (int)vol; i += blockDim.x) stage[i] = 0.0f;
+        for (int i = tid; i < (int)vol; i += blockDim.x) stage[i] = 0;
         __syncthreads();
         if (run) {
             StageSink sk;
@@ -598,13 +620,13 @@ __device__ __forceinline__ void staged_body(const DevGeom &g, const float *__res
             sk.off = (unsigned)(-(R0[0] * T[0] + R0[1] * T[1] + R0[2] * T[2]));
             sk.bx = make_box(rs.lo, rs.hi);
             sk.size = (unsigned)vol;
-            sk.yv = yv;
+            sk.yv = yv * inv_q;
             sk.over = false;
             bad |= !piece_march<N, StageSink>(rs, cf, cl, qr, sk);
             bad |= sk.over;
         }
         __syncthreads();
-        stage_flush(stage, c, key, g.n, R0, E, T);
+        stage_flush(stage, q, c, key, g.n, R0, E, T);
         __syncthreads();
     }
     if (bad) atomicOr(g.err, 1);

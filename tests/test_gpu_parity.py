@@ -520,8 +520,9 @@ def full_size_check(env, orc, wl, class_views, seed):
         assert pairs.sum() > 0, name
         err = rel_l2(yh[rays], yref)
         assert err <= TOL, (name, err)
+    # mixed signs, as a CG residual: the hard case for the adjoint's sums
     rng = np.random.default_rng(seed + 1)
-    yv = rng.uniform(0, 1, size=g.n_rays).astype(np.float32)
+    yv = rng.normal(size=g.n_rays).astype(np.float32)
     cb = torch.full(g.coeff_shape, float("nan"), dtype=torch.float32, device="cuda")
     spl.adjoint(g, torch.tensor(yv, device="cuda"), cb, spl.basis(3))
     g.status()
