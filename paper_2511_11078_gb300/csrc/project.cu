@@ -379,275 +379,6 @@ __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
     }
 }
 
-// ---------------------------------------------------------------- adjoint: staged scatter (view geometries)
-// The ray-driven scatter adds every contribution y_r * F_l with a global
-// float atomic: at 16 scattered addresses per piece the L2's tag lookups
-// become the bound (measured 83 % of their peak on the 512^3 helical
-// views).  The staged form keeps the forward's thread mapping (a block is a
-// 16 x 8 detector tile of one view) but marches the block's rays in
-// lock-step segments of kSegCells cells along their common dominant axis:
-// per segment the block computes the region of bases its rays' windows can
-// reach (the union of each ray's d, a and b index ranges over its cells of
-// the segment, clipped to the grid), the rays add into a shared-memory copy
-// of that region with shared atomics, and the block then adds the region to
-// c with coalesced global atomics along the x axis (zeros skipped).  A
-// basis live across a segment boundary is flushed once per segment (its
-// contributions are additive), so the result is the same sum.  Blocks whose
-// rays do not share the mirrored frame (dominant axis and signs), and
-// segments whose region exceeds the staging buffer, add to global memory
-// directly.
-//
-// The staging buffer holds 32-bit fixed-point sums (integer shared-memory
-// atomics are single instructions; float ones are not).  Scale: a flushed
-// footprint F_l of a segment is a partial integral of the basis's d-factor
-// times two weights <= 1, so F_l <= 1, and 1/|w_d| <= sqrt(3); every
-// contribution y_r F_l / |w_d| is then at most 2 Ymax in magnitude, Ymax the
-// largest |y_r| of the block, and is rounded to the quantum
-// q = 2 Ymax / 2^21 (a single rounding of at most q/2 ~ 5e-7 Ymax).  A basis
-// receives at most one contribution per ray of the block in a segment, so
-// its sum stays below 128 x 2^21 = 2^28 (no overflow); integer sums are
-// exact, and the flush converts them back to float.
-constexpr int kSegCells = 8;
-constexpr int kStageWords = 12288;  // 48 KB per block
-constexpr size_t kStageSmem = kStageWords * sizeof(int);
-
-// x rounded to the nearest integer, for |x| < 2^22: adding 1.5 2^23 puts the
-// integer part in the float's mantissa (unit last place = 1)
-__device__ __forceinline__ int fixed_round(float x) { return __float_as_int(x + 12582912.0f) - 0x4B400000; }
-
-struct StageSink {
-    static constexpr bool plane = false;
-    int *buf;
-    int S0, S1, S2;  // buffer strides of (d, a, b)
-    unsigned off;
-    SinkBox bx;      // the grid (mirrored frame)
-    unsigned size;
-    float yv;        // y_r / |w_d| / q
-    bool over;       // a basis fell outside the buffer (the region bounds rule it out)
-    __device__ __forceinline__ void piece() {}
-    __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
-    {
-        return bx.meets(d0, d1, a0, a1, b0, b1);
-    }
-    __device__ __forceinline__ void flush(int ld, int la, int lb, float v)
-    {
-        if (bx.holds(ld, la, lb)) put(off + (unsigned)(ld * S0 + la * S1 + lb * S2), true, v, 0);
-    }
-    __device__ __forceinline__ void put(unsigned o, bool in, float v, int)
-    {
-        if (in) {
-            if (o < size) atomicAdd(buf + o, fixed_round(yv * v));
-            else over = true;
-        }
-    }
-    __device__ __forceinline__ void cell_end() {}
-};
-
-// The block's mirrored frame, packed into a key: the axis indices of d and a
-// and the three mirror signs.
-__device__ __forceinline__ int frame_key(const RaySetup &rs)
-{
-    return rs.ax[0] | (rs.ax[1] << 2) | ((rs.sg[0] > 0) << 4) | ((rs.sg[1] > 0) << 5) | ((rs.sg[2] > 0) << 6);
-}
-
-// Add the staging buffer (region origin R0 in the mirrored frame, extents
-// E, buffer strides T; the x axis has stride 1 in the buffer) to c.  Each
-// warp takes whole rows along x, so its atomics are coalesced.
-__device__ __forceinline__ void stage_flush(const int *stage, float q, float *__restrict__ c, int key,
-                                            const int (&n)[3], const int (&R0)[3], const int (&E)[3],
-                                            const int (&T)[3])
-{
-    const int ax0 = key & 3, ax1 = (key >> 2) & 3, ax2 = 3 - ax0 - ax1;
-    const int st0 = ax0 == 0 ? 1 : (ax0 == 1 ? n[0] : n[0] * n[1]);
-    const int st1 = ax1 == 0 ? 1 : (ax1 == 1 ? n[0] : n[0] * n[1]);
-    const int st2 = ax2 == 0 ? 1 : (ax2 == 1 ? n[0] : n[0] * n[1]);
-    const int Sg0 = ((key >> 4) & 1) ? st0 : -st0, Sg1 = ((key >> 5) & 1) ? st1 : -st1,
-              Sg2 = ((key >> 6) & 1) ? st2 : -st2;
-    // roles: f (stride 1 in the buffer: the x axis), then r1, r2
-    const int qf = ax0 == 0 ? 0 : (ax1 == 0 ? 1 : 2);
-    const int Ef = qf == 0 ? E[0] : (qf == 1 ? E[1] : E[2]);
-    const int E1 = qf == 0 ? E[1] : E[0];
-    const int E2 = qf == 2 ? E[1] : E[2];
-    const int T1 = qf == 0 ? T[1] : T[0], T2 = qf == 2 ? T[1] : T[2];
-    const int Sgf = qf == 0 ? Sg0 : (qf == 1 ? Sg1 : Sg2);
-    const int Sg_1 = qf == 0 ? Sg1 : Sg0, Sg_2 = qf == 2 ? Sg1 : Sg2;
-    const int base = R0[0] * Sg0 + R0[1] * Sg1 + R0[2] * Sg2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rows = E1 * E2;
-    for (int row = warp; row < rows; row += blockDim.x >> 5) {
-        const int u1 = row % E1, u2 = row / E1;
-        const int *src = stage + u1 * T1 + u2 * T2;
-        const int ob = base + u1 * Sg_1 + u2 * Sg_2;
-        for (int uf = lane; uf < Ef; uf += 32) {
-            const int v = src[uf];
-            if (v != 0) atomicAdd(c + (ob + uf * Sgf), (float)v * q);
-        }
-    }
-}
-
-// V: the view's constants (parallel views), NULL for cone views
-template <int N, int VM>
-__device__ __forceinline__ void staged_body(const DevGeom &g, const float *__restrict__ y, float *__restrict__ c,
-                                            const QuadRule &qr, int k, const ViewConst *V)
-{
-    extern __shared__ __align__(16) int stage[];
-    __shared__ int red[9];  // frame key min/max, then the region's d, a, b ranges; Ymax
-    const int tid = threadIdx.x;
-    int iu, iv;
-    tile_pixel(iu, iv);
-    bool active = iu < g.nu && iv < g.nv;
-    float yr = 0.0f;
-    RaySetup rs;
-    if (active) {
-        yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
-        active = yr != 0.0f;
-    }
-    if (active) {
-        active = view_setup<N>(g, grid_of(g), k, iu, iv, rs);
-        if (active && V) use_view_const(*V, rs);
-        active = active && rs.c0 <= rs.c1;
-    }
-    if (tid == 0) {
-        red[0] = 0x7fffffff;
-        red[1] = -1;
-        red[2] = 0x7fffffff;
-        red[3] = -0x7fffffff;
-        red[8] = 0;
-    }
-    __syncthreads();
-    if (active) {
-        const int key = frame_key(rs);
-        atomicMin(&red[0], key);
-        atomicMax(&red[1], key);
-        atomicMin(&red[2], rs.c0);
-        atomicMax(&red[3], rs.c1);
-        atomicMax(&red[8], __float_as_int(fabsf(yr)));  // non-negative floats order as integers
-    }
-    __syncthreads();
-    const int key = red[0], kmax = red[1], Cmin = red[2], Cmax = red[3];
-    const float ymax = __int_as_float(red[8]);
-    __syncthreads();
-    if (kmax < 0) return;  // no ray of the block meets the grid (block-uniform)
-    if (key != kmax) {     // rays of the block in different mirrored frames (block-uniform)
-        if (active) scatter_ray<N, VM>(rs, yr, c, qr, g.err);
-        return;
-    }
-    // fixed-point quantum q = 2 Ymax / 2^21 (a power-of-two multiple of Ymax
-    // would do as well; this one is exact to FP32 rounding)
-    const float q = ymax * (2.0f / 2097152.0f), inv_q = 2097152.0f / (2.0f * ymax);
-    const float yv = active ? yr * rs.inv_wd : 0.0f;
-    bool bad = false;
-#pragma unroll 1
-    for (int s0 = Cmin; s0 <= Cmax; s0 += kSegCells) {
-        const int s1 = min(s0 + kSegCells - 1, Cmax);
-        int cf = 0, cl = -1;
-        int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
-        if (active) {
-            cf = max(rs.c0, s0);
-            cl = min(rs.c1, s1);
-            if (cf <= cl) {
-                // over cells c of [cf, cl] the window holds l_d in [c - N, c]
-                // and l_a in [QA - N, QA], QA running from floor(v_a(cf)) to
-                // floor(v_a(cl + 1)) (likewise b); clipped to the grid
-                int I0, I1;
-                float f;
-                lo[0] = max(cf - N, rs.lo[0]);
-                hi[0] = min(cl, rs.hi[0]);
-                df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, cf - rs.c0, I0, f);
-                df_coord(rs.Vah, rs.Val, rs.rah, rs.ral, cl + 1 - rs.c0, I1, f);
-                lo[1] = max(I0 - N, rs.lo[1]);
-                hi[1] = min(I1, rs.hi[1]);
-                df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, cf - rs.c0, I0, f);
-                df_coord(rs.Vbh, rs.Vbl, rs.rbh, rs.rbl, cl + 1 - rs.c0, I1, f);
-                lo[2] = max(I0 - N, rs.lo[2]);
-                hi[2] = min(I1, rs.hi[2]);
-            }
-        }
-        const bool run = lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
-        if (tid == 0) {
-            red[2] = red[4] = red[6] = 0x7fffffff;
-            red[3] = red[5] = red[7] = -0x7fffffff;
-        }
-        __syncthreads();
-        if (run) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                atomicMin(&red[2 + 2 * q], lo[q]);
-                atomicMax(&red[3 + 2 * q], hi[q]);
-            }
-        }
-        __syncthreads();
-        int R0[3], E[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            R0[q] = red[2 + 2 * q];
-            E[q] = red[3 + 2 * q] - R0[q] + 1;
-        }
-        __syncthreads();
-        if (E[0] <= 0) continue;  // no ray reaches the grid in this segment (block-uniform)
-        const long long vol = (long long)E[0] * E[1] * E[2];
-        if (vol > kStageWords || !(ymax < 1e30f)) {
-            // region too large for the buffer: add to global memory directly
-            if (run) {
-                AtomicSink sk;
-                sk.c = c;
-                sk.S0 = rs.S[0];
-                sk.S1 = rs.S[1];
-                sk.S2 = rs.S[2];
-                sk.off = 0u;
-                sk.bx = make_box(rs.lo, rs.hi);
-                sk.yv = yv;
-                bad |= !piece_march<N, AtomicSink>(rs, cf, cl, qr, sk);
-            }
-            continue;
-        }
-        // buffer strides: the x axis fastest (the block's frame)
-        const int ax0 = key & 3, ax1 = (key >> 2) & 3;
-        const int qf = ax0 == 0 ? 0 : (ax1 == 0 ? 1 : 2);
-        // orders: qf = 0 (d, a, b), qf = 1 (a, d, b), qf = 2 (b, d, a)
-        int T[3];
-        T[0] = qf == 0 ? 1 : (qf == 1 ? E[1] : E[2]);
-        T[1] = qf == 1 ? 1 : (qf == 0 ? E[0] : E[2] * E[0]);
-        T[2] = qf == 2 ? 1 : (qf == 0 ? E[0] * E[1] : E[1] * E[0]);
-        for (int i = tid; i < (int)vol; i += blockDim.x) stage[i] = 0;
-        __syncthreads();
-        if (run) {
-            StageSink sk;
-            sk.buf = stage;
-            sk.S0 = T[0];
-            sk.S1 = T[1];
-            sk.S2 = T[2];
-            sk.off = (unsigned)(-(R0[0] * T[0] + R0[1] * T[1] + R0[2] * T[2]));
-            sk.bx = make_box(rs.lo, rs.hi);
-            sk.size = (unsigned)vol;
-            sk.yv = yv * inv_q;
-            sk.over = false;
-            bad |= !piece_march<N, StageSink>(rs, cf, cl, qr, sk);
-            bad |= sk.over;
-        }
-        __syncthreads();
-        stage_flush(stage, q, c, key, g.n, R0, E, T);
-        __syncthreads();
-    }
-    if (bad) atomicOr(g.err, 1);
-}
-
-template <int N>
-__global__ void __launch_bounds__(128, 3)
-    k_adjoint_views_staged(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr, int v0)
-{
-    staged_body<N, VM_CONE>(g, y, c, qr, v0 + blockIdx.z, nullptr);
-}
-
-template <int N>
-__global__ void __launch_bounds__(128, 3)
-    k_adjoint_pviews_staged(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr,
-                            const __grid_constant__ ViewChunk vc)
-{
-    const ViewConst &V = vc.v[blockIdx.z];
-    staged_body<N, VM_GENERAL>(g, y, c, qr, V.view, &V);
-}
-
 // ---------------------------------------------------------------- adjoint: brick gather (view geometries)
 constexpr int kBrick = 16;                        // brick edge (coefficients)
 constexpr int kBrickVol = kBrick * kBrick * kBrick;
@@ -1046,11 +777,9 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
                 k_adjoint_pviews_scatter<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
                 end_batch();
             }, per);
-            if (dg.n_views > dg.n_flat && s == SPL_OK)
-                s = smem_attr_once((const void *)k_adjoint_pviews_staged<N>, (int)kStageSmem, "staged adjoint smem");
             for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
                 if (s == SPL_OK) s = begin_batch();
-                k_adjoint_pviews_staged<N><<<dim3(gx, gy, n), 128, kStageSmem, st>>>(dg, y, c, qr, ch);
+                k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
                 end_batch();
             }, per);
             if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);
@@ -1062,12 +791,10 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
             if (s != SPL_OK) return s;
         } else {
             const int per_launch = batched ? kAdjBatchViews : dg.n_views;
-            s = smem_attr_once((const void *)k_adjoint_views_staged<N>, (int)kStageSmem, "staged adjoint smem");
-            if (s != SPL_OK) return s;
             for (int k0 = 0; k0 < dg.n_views; k0 += per_launch) {
                 const int nview = dg.n_views - k0 < per_launch ? dg.n_views - k0 : per_launch;
                 if ((s = begin_batch()) != SPL_OK) return s;
-                k_adjoint_views_staged<N><<<dim3(gx, gy, nview), 128, kStageSmem, st>>>(dg, y, c, qr, k0);
+                k_adjoint_views_scatter<N><<<dim3(gx, gy, nview), 128, 0, st>>>(dg, y, c, qr, k0);
                 end_batch();
             }
             if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);

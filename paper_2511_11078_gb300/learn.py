@@ -17,22 +17,53 @@ import torch
 from . import spl
 
 class FootprintSet:
-    """`count` exact-footprint samples of Algorithm 1 resident on the GPU."""
+    """`count` exact-footprint samples of Algorithm 1 resident on the GPU.
 
-    def __init__(self, degree: int, count: int, seed: int, device="cuda"):
+    The plain set (the defaults) is Algorithm 1's distribution: directions
+    uniform on the sphere, offsets uniform in the disc of radius sqrt(3) W.
+    Training sets may reshape it (the draws stay the caller's random
+    numbers fed to spl_footprint_samples):
+
+    * support_only: keep only samples inside the exact support (nonzero
+      label).  The projector multiplies f_theta by the exact support
+      indicator, so the values outside are never used; without them the
+      loss measures only what the projector sees.
+    * axis_fraction: that fraction of the directions is drawn near the six
+      coordinate axes (a standard normal plus axis_scale times a random
+      signed unit axis, normalised), where the canonical direction sits in
+      the chamber's corner w = e3 and the footprint's peak is sharpest.
+    * center_power: offsets at radius sqrt(3) W u^(center_power / 2)
+      instead of u^(1/2) (u uniform): > 1 draws more samples near the
+      footprint's peak at p = 0.
+    """
+
+    def __init__(self, degree: int, count: int, seed: int, device="cuda", support_only: bool = False,
+                 axis_fraction: float = 0.0, axis_scale: float = 8.0, center_power: float = 1.0):
         self.degree = int(degree)
         gen = torch.Generator(device=device)
         gen.manual_seed(int(seed))
         normals = torch.randn((count, 3), generator=gen, device=device)
         uniforms = torch.rand((count, 2), generator=gen, device=device)
+        if axis_fraction > 0.0:
+            m = int(round(axis_fraction * count))
+            axis = torch.randint(0, 3, (m,), generator=gen, device=device)
+            sign = torch.randint(0, 2, (m,), generator=gen, device=device).float() * 2.0 - 1.0
+            normals[:m].scatter_add_(1, axis[:, None], (axis_scale * sign)[:, None])
+        if center_power != 1.0:
+            uniforms[:, 0] = uniforms[:, 0].pow(center_power)
         self.omega = torch.empty((count, 3), dtype=torch.float32, device=device)
         self.p = torch.empty((count, 3), dtype=torch.float32, device=device)
         spl.footprint_samples(degree, normals, uniforms, self.omega, self.p)
-        self.feat = torch.empty((count, 5), dtype=torch.float32, device=device)
-        spl.features(degree, self.omega, self.p, self.feat)
         self.label = torch.empty(count, dtype=torch.float32, device=device)
         spl.footprint(spl.basis(degree), self.omega, self.p, self.label)
-        self.count = count
+        if support_only:
+            keep = torch.nonzero(self.label > 0.0).flatten()
+            self.omega = self.omega.index_select(0, keep).contiguous()
+            self.p = self.p.index_select(0, keep).contiguous()
+            self.label = self.label.index_select(0, keep).contiguous()
+        self.count = int(self.label.numel())
+        self.feat = torch.empty((self.count, 5), dtype=torch.float32, device=device)
+        spl.features(degree, self.omega, self.p, self.feat)
 
     @property
     def peak(self) -> float:

@@ -585,12 +585,11 @@ def test_adjoint_batched_over_views(env, orc, kind):
     assert rel_l2(got, ref) <= TOL, rel_l2(got, ref)
 
 
-def test_adjoint_staged_fallbacks(env, orc):
-    """The staged scatter's two fallbacks to direct global atomics: a coarse
-    detector whose 16 x 8 pixel tiles reach a region larger than the
-    staging buffer, and a cone whose rays within one tile have different
-    dominant axes or mirror signs (source close to the grid, 45-degree
-    views)."""
+def test_adjoint_coarse_and_close_geometries(env, orc):
+    """The scatter adjoint on a coarse detector (pixels much larger than a
+    cell: one ray per several bases) and on a cone whose rays within one
+    16 x 8 tile have different dominant axes and mirror signs (source close
+    to the grid, 45-degree views)."""
     torch, spl = env
     rng = np.random.default_rng(1300)
     dims = (48, 46, 44)
