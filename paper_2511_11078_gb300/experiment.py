@@ -133,15 +133,71 @@ def run(dims=(180, 180, 50), n_views=200, det=(180, 50), iters=50, degrees=(2, 0
     return out
 
 
+def cylinder_mask(dims):
+    """Grid points inside the cylinder inscribed in the grid about e3 (the
+    cone-beam detectors of the workloads truncate the volume's corners)."""
+    nx, ny, nz = dims
+    org = I.centred_origin(dims)
+    x = org[0] + np.arange(nx)
+    y = org[1] + np.arange(ny)
+    r = 0.5 * (min(nx, ny) - 1)
+    inside = (x[None, :] ** 2 + y[:, None] ** 2) <= r * r
+    return np.broadcast_to(inside[None, :, :], (nz, ny, nx))
+
+
+def mlp_vs_quadrature(mlp, iters=10, views=None, noise=0.01, device="cuda"):
+    """The learned footprint inside least squares (Sec. 2.2 used in Eq. 5)
+    beside the exact quadrature, on the 256^3 circular cone-beam workload:
+    data y = A c_true + Gaussian noise (sigma = `noise` times max A c_true),
+    `iters` CGLS iterations with each footprint form, PSNR of the
+    reconstructed spline sampled at the grid points against the phantom's
+    spline c_true sampled there, inside the inscribed cylinder.  Returns the
+    PSNRs, their difference (the loss from the learned footprint) and the
+    seconds per iteration of each form."""
+    wl = I.workload_cone()
+    geo = wl.geometry if views is None else wl.geometry.subset_views(views)
+    g = spl.Geometry(wl.dims, wl.origin, geo)
+    c_true = torch.tensor(wl.coeffs, device=device)
+    pq = Projector(g, 3)
+    y = pq.forward(c_true)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(I.SEED_BASE + 40)
+    y = y + noise * float(y.max()) * torch.randn(y.shape, generator=gen, device=device)
+    ref = sample_spline(wl.coeffs.astype(np.float64), 3)
+    mask = cylinder_mask(wl.dims)
+    out = {"workload": wl.name + "-cubic", "views": geo.n_views, "iters": iters, "noise_sigma_rel_max": noise}
+    for name, proj in (("quad", pq), ("mlp", Projector(g, 3, spl.SPL_FP_MLP, mlp))):
+        cg = CGLS(proj, y)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        cg.run(iters)
+        t1.record()
+        torch.cuda.synchronize()
+        g.status()
+        f = sample_spline(cg.x.cpu().numpy().astype(np.float64), 3)
+        out[name] = {"psnr_db": psnr(f[mask], ref[mask]), "residual": cg.residual_norm(),
+                     "s_per_iter": t0.elapsed_time(t1) / 1e3 / iters}
+    out["psnr_loss_db"] = out["quad"]["psnr_db"] - out["mlp"]["psnr_db"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--degree", type=int, default=2)
     ap.add_argument("--seeds", type=int, default=1)
+    ap.add_argument("--mlp-checkpoint", default=None,
+                    help="instead: the learned footprint of this checkpoint (spl_mlp_save) against quadrature "
+                         "inside CGLS on the 256^3 cone-beam workload, --iters iterations each")
     args = ap.parse_args()
     from . import build as B
 
     B.build()
+    if args.mlp_checkpoint:
+        mlp = spl.Mlp(3, max_batch=8192)
+        mlp.load(args.mlp_checkpoint)
+        print(json.dumps(mlp_vs_quadrature(mlp, iters=args.iters)), flush=True)
+        return
     for k in range(args.seeds):
         print(json.dumps(run(iters=args.iters, degrees=(args.degree, 0), seed=k)), flush=True)
 
