@@ -37,6 +37,7 @@ namespace spl {
 // piece march).
 struct FwdSink {
     static constexpr bool plane = false;
+    static constexpr bool face = false;
     const float *__restrict__ c;
     int S0, S1, S2;
     unsigned off;
@@ -71,6 +72,7 @@ struct FwdSink {
 
 struct CountSink {
     static constexpr bool plane = false;
+    static constexpr bool face = false;
     int S0, S1, S2;
     unsigned off;
     SinkBox bx;
@@ -89,14 +91,71 @@ struct CountSink {
     __device__ __forceinline__ void cell_end() {}
 };
 
-// adjoint, scatter: y_r / |w_d| * F_l added to c_l with a float atomic
+// adjoint, scatter: y_r / |w_d| * F_l added to c_l with a float atomic.
+// A face whose rows run along the x axis (unit stride) is added with 16-byte
+// vector atomics instead: a row of N+1 = 4 consecutive floats spans at most
+// two aligned groups of 4, each added with one atomic whose other entries
+// are zero (adding +0 leaves them unchanged).  That halves the L2 requests
+// of such faces (the adjoint's bound); vec is false when c is not 16-byte
+// aligned, and a row whose second group would pass the array's end (n
+// floats) is added entry by entry.
 struct AtomicSink {
     static constexpr bool plane = false;
+    static constexpr bool face = true;
     float *__restrict__ c;
     int S0, S1, S2;
     unsigned off;
     SinkBox bx;
     float yv;
+    bool vec;
+    unsigned n;
+    // w0..w3 (already scaled) at p, p + s, p + 2 s, p + 3 s, s = +-1
+    __device__ __forceinline__ void row4(unsigned p, bool up, float w0, float w1, float w2, float w3)
+    {
+        const unsigned lo = up ? p : p - 3u;
+        const float a0 = up ? w0 : w3, a1 = up ? w1 : w2, a2 = up ? w2 : w1, a3 = up ? w3 : w0;
+        const unsigned g = lo & ~3u, k = lo & 3u;
+        if (g + 8u > n) {
+            atomicAdd(c + lo, a0);
+            atomicAdd(c + lo + 1u, a1);
+            atomicAdd(c + lo + 2u, a2);
+            atomicAdd(c + lo + 3u, a3);
+            return;
+        }
+        float4 f, h;
+        f.x = k == 0u ? a0 : 0.0f;
+        f.y = k == 0u ? a1 : (k == 1u ? a0 : 0.0f);
+        f.z = k == 0u ? a2 : (k == 1u ? a1 : (k == 2u ? a0 : 0.0f));
+        f.w = k == 0u ? a3 : (k == 1u ? a2 : (k == 2u ? a1 : a0));
+        h.x = k == 1u ? a3 : (k == 2u ? a2 : a1);
+        h.y = k == 2u ? a3 : (k == 3u ? a2 : 0.0f);
+        h.z = k == 3u ? a3 : 0.0f;
+        h.w = 0.0f;
+        atomicAdd(reinterpret_cast<float4 *>(c + g), f);
+        if (k != 0u) atomicAdd(reinterpret_cast<float4 *>(c + g + 4u), h);
+    }
+    template <int N>
+    __device__ __forceinline__ void put_face(unsigned base, unsigned SX, unsigned SY, const float (&v)[N + 1][N + 1])
+    {
+        if constexpr (N == 3) {
+            if (vec && (SX == 1u || SX == 0xffffffffu)) {
+#pragma unroll
+                for (int y = 0; y <= N; ++y)
+                    row4(base + (unsigned)y * SY, SX == 1u, yv * v[0][y], yv * v[1][y], yv * v[2][y], yv * v[3][y]);
+                return;
+            }
+            if (vec && (SY == 1u || SY == 0xffffffffu)) {
+#pragma unroll
+                for (int x = 0; x <= N; ++x)
+                    row4(base + (unsigned)x * SX, SY == 1u, yv * v[x][0], yv * v[x][1], yv * v[x][2], yv * v[x][3]);
+                return;
+            }
+        }
+#pragma unroll
+        for (int x = 0; x <= N; ++x)
+#pragma unroll
+            for (int y = 0; y <= N; ++y) atomicAdd(c + (base + (unsigned)x * SX + (unsigned)y * SY), yv * v[x][y]);
+    }
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
     {
@@ -117,6 +176,7 @@ struct AtomicSink {
 // shared-memory brick array (mirrored strides S0..S2, offset off)
 struct BrickSink {
     static constexpr bool plane = false;
+    static constexpr bool face = false;
     float *part;
     int S0, S1, S2;
     unsigned off;
@@ -314,9 +374,11 @@ __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long lon
 }
 
 // ---------------------------------------------------------------- adjoint: ray-driven scatter
+__device__ __forceinline__ unsigned ncoef_of(const DevGeom &g) { return (unsigned)(g.n[0] * g.n[1] * g.n[2]); }
+
 template <int N, int VM>
 __device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float *__restrict__ c, const QuadRule &qr,
-                                            int *err)
+                                            int *err, unsigned ncoef)
 {
     AtomicSink sk;
     sk.c = c;
@@ -326,6 +388,8 @@ __device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float 
     sk.off = 0u;
     sk.bx = make_box(rs.lo, rs.hi);
     sk.yv = yr * rs.inv_wd;
+    sk.vec = ((size_t)c & 15u) == 0u;
+    sk.n = ncoef;
     if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
 }
 
@@ -341,7 +405,7 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
     double s[3], w[3];
     explicit_ray(g, r, s, w);
     RaySetup rs;
-    if (ray_setup<N>(grid_of(g), s, w, rs)) scatter_ray<N, VM_RAYS>(rs, yr, c, qr, g.err);
+    if (ray_setup<N>(grid_of(g), s, w, rs)) scatter_ray<N, VM_RAYS>(rs, yr, c, qr, g.err, ncoef_of(g));
 }
 
 // view geometries, scatter form: the forward's thread mapping, float
@@ -357,7 +421,7 @@ __global__ void __launch_bounds__(128, 3)
     const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
     if (yr == 0.0f) return;
     RaySetup rs;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM_CONE>(rs, yr, c, qr, g.err);
+    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM_CONE>(rs, yr, c, qr, g.err, ncoef_of(g));
 }
 
 template <int N, int VM>
@@ -375,7 +439,7 @@ __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
     RaySetup rs;
     if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) {
         use_view_const(V, rs);
-        scatter_ray<N, VM>(rs, yr, c, qr, g.err);
+        scatter_ray<N, VM>(rs, yr, c, qr, g.err, ncoef_of(g));
     }
 }
 

@@ -12,6 +12,7 @@ namespace spl {
 // told is in it, so the strides do not matter
 struct PointSink {
     static constexpr bool plane = false;
+    static constexpr bool face = false;
     float v;
     int S0 = 0, S1 = 0, S2 = 0;
     unsigned off = 0u;

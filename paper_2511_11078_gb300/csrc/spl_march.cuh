@@ -816,7 +816,9 @@ __device__ __forceinline__ bool cell_march(const RaySetup &rs, int cf, int cl, c
 // flushed through sink.put(offset, in_region, F, slot) at offsets in the
 // sink's layout (sink.S0..S2, sink.off, region sink.bx; slot in 0..N is the
 // face entry's second index, so a sink may spread the face over N+1
-// independent partial sums), and the window shifted
+// independent partial sums) -- or, when the whole window lies in the region
+// and the sink has Sink::face, through one sink.put_face(base, SX, SY, F)
+// of the face's (N+1)^2 values at base + x SX + y SY -- and the window shifted
 // with selects along the event's axis.  Only the set-up of the next cell
 // is a branch.
 template <int N, class Sink>
@@ -880,13 +882,23 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
             if (sink.bx.cube_in(bd, ba, bb, N)) {
                 // the whole window lies in the region (most pieces): every
                 // face entry is in, no per-entry tests
+                if constexpr (Sink::face) {
+                    float fv[N + 1][N + 1];
 #pragma unroll
-                for (int x = 0; x <= N; ++x)
+                    for (int x = 0; x <= N; ++x)
 #pragma unroll
-                    for (int y = 0; y <= N; ++y) {
-                        const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
-                        sink.put(base + (unsigned)x * SX + (unsigned)y * SY, true, v, y);
-                    }
+                        for (int y = 0; y <= N; ++y)
+                            fv[x][y] = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
+                    sink.template put_face<N>(base, SX, SY, fv);
+                } else {
+#pragma unroll
+                    for (int x = 0; x <= N; ++x)
+#pragma unroll
+                        for (int y = 0; y <= N; ++y) {
+                            const float v = evA ? acc[x][0][y] : (evB ? acc[x][y][0] : acc[0][x][y]);
+                            sink.put(base + (unsigned)x * SX + (unsigned)y * SY, true, v, y);
+                        }
+                }
             } else {
                 const bool vf = evA ? sink.bx.in1(ba) : (evB ? sink.bx.in2(bb) : sink.bx.in0(bd));
                 bool vx[N + 1], vy[N + 1];
