@@ -90,9 +90,12 @@ def parse():
                     help="Adam steps of the learned footprint trained before the MLP measurement (0: skip it)")
     ap.add_argument("--mlp-views", type=int, default=36,
                     help="views of the 256^3 cone workload (evenly spaced) the MLP projector is timed on")
-    ap.add_argument("--profile-views", default=None, metavar="START:STOP",
-                    help="only run A and A^T once each on views START..STOP-1 of the headline workload (a small "
-                         "case for ncu) and print their times")
+    ap.add_argument("--mlp-recon-iters", type=int, default=10,
+                    help="CGLS iterations of the learned-footprint vs quadrature reconstruction on those views "
+                         "(0: skip it)")
+    ap.add_argument("--profile-views", default=None, metavar="START:STOP[:STEP]",
+                    help="only run A and A^T once each on views START..STOP-1 (every STEP-th) of the headline "
+                         "workload (a small case for ncu) and print their times")
     ap.add_argument("--mlp-profile", default=None, metavar="START:STOP",
                     help="only run the learned-footprint projector (f_theta seeded 5, trained for --mlp-steps "
                          "steps first) once forward and once adjoint on views START..STOP-1 of the 256^3 cone "
@@ -523,16 +526,21 @@ def mlp_block(args, dev, with_oracle: bool):
 
     n = 3
     t0 = time.perf_counter()
-    data = learn.FootprintSet(n, 1 << 22, seed=31, device=dev)
-    val = learn.FootprintSet(n, 1 << 16, seed=32, device=dev)
+    val = learn.FootprintSet(n, 1 << 18, seed=32, device=dev)
     mlp = spl.Mlp(n, max_batch=8192, seed=5)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    learn.train(mlp, data, steps=args.mlp_steps, batch=8192, lr0=3e-3, lr_min=1e-6)
+    data = learn.train_recipe(mlp, n, scale=args.mlp_steps / learn.RECIPE["steps"], device=dev)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     mlp.status()
     acc = learn.evaluate(mlp, val)
+    recon = None
+    if args.mlp_recon_iters > 0:
+        from paper_2511_11078_gb300 import experiment
+
+        rviews = np.linspace(0, 360, args.mlp_views, endpoint=False).astype(int)
+        recon = experiment.mlp_vs_quadrature(mlp, iters=args.mlp_recon_iters, views=rviews, device=dev)
     wl = I.workload_cone()
     views = np.linspace(0, wl.geometry.n_views, args.mlp_views, endpoint=False).astype(int)
     geo = wl.geometry.subset_views(views)
@@ -561,7 +569,7 @@ def mlp_block(args, dev, with_oracle: bool):
     m_at = timed(lambda: pm.adjoint(yq, out=cm))
     geom.status()
     out = {"footprint": "f_theta 5-64-64-64-1 SiLU, BF16 weights/activations, FP32 accumulation (tcgen05, "
-                        "accumulator in TMEM)",
+                        "accumulator in TMEM)", "dataset_s": t1 - t0,
            "workload": "%s-cubic, %d of %d views (evenly spaced)" % (wl.name, len(views), wl.geometry.n_views),
            "contributions_per_A": pairs,
            "quad": {"A_ms": q_a, "AT_ms": q_at, "A_gcontrib_s": pairs / q_a / 1e6, "AT_gcontrib_s": pairs / q_at / 1e6},
@@ -569,11 +577,16 @@ def mlp_block(args, dev, with_oracle: bool):
                    "tensor_tflops_A": pairs * MLP_FLOP_PER_PAIR / m_a / 1e9},
            "s_per_recon_iter_full_360_views": {"quad": (q_a + q_at) / 1e3 * wl.geometry.n_views / len(views),
                                                "mlp": (m_a + m_at) / 1e3 * wl.geometry.n_views / len(views)},
-           "train_steps": args.mlp_steps, "train_batch": 8192, "train_samples": 1 << 22, "train_s": t2 - t1,
-           "dataset_s": t1 - t0,
+           "train": "Algorithm 1, support-masked, importance-sampled, two rounds of hard-example mining "
+                    "(learn.RECIPE; step counts x %.3g)" % (args.mlp_steps / learn.RECIPE["steps"]),
+           "train_steps": args.mlp_steps, "train_batch": 8192, "train_samples_final": data.count, "train_s": t2 - t1,
+           "footprint_held_out": "%d samples of Algorithm 1's distribution, errors where the exact footprint is "
+                                 "evaluated (masked by the exact support, as in the projector)" % val.count,
            "footprint_max_abs_over_peak": acc["max_abs_rel_peak"], "footprint_rms": acc["rms"],
            "A_rel_l2_vs_exact": float((ym - yq).norm() / yq.norm()),
            "AT_rel_l2_vs_exact": float((cm - cq).norm() / cq.norm())}
+    if recon is not None:
+        out["recon_psnr"] = recon
     if with_oracle:
         import oracle
 
@@ -746,9 +759,11 @@ def run_profile_views(args):
 
     B.build()
     spl.lib()
-    a, b = (int(v) for v in args.profile_views.split(":"))
+    parts = [int(v) for v in args.profile_views.split(":")]
+    a, b = parts[0], parts[1]
+    step = parts[2] if len(parts) > 2 else 1
     wl = I.workload_helical()
-    geom = spl.Geometry(wl.dims, wl.origin, wl.geometry.subset_views(np.arange(a, b)))
+    geom = spl.Geometry(wl.dims, wl.origin, wl.geometry.subset_views(np.arange(a, b, step)))
     bas = spl.basis(3, adjoint=spl.SPL_ADJ_GATHER if args.adjoint == "gather" else spl.SPL_ADJ_SCATTER)
     c = torch.tensor(wl.coeffs, device="cuda")
     y = torch.empty(geom.n_rays, device="cuda")
@@ -764,7 +779,7 @@ def run_profile_views(args):
     torch.cuda.synchronize()
     geom.status()
     a_ms, at_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    print(json.dumps({"profile_views": [a, b], "workload": wl.name + "-cubic", "A_ms": a_ms, "AT_ms": at_ms,
+    print(json.dumps({"profile_views": [a, b, step], "workload": wl.name + "-cubic", "A_ms": a_ms, "AT_ms": at_ms,
                       "pairs": pairs, "pieces": pieces, "A_gcontrib_s": pairs / a_ms / 1e6,
                       "AT_gcontrib_s": pairs / at_ms / 1e6, "csrc_sha16": csrc_sha16()}), flush=True)
     return 0

@@ -256,9 +256,11 @@ static int axis_interval(int n, double p, double w, double *lo, double *hi)
 
 static void index_range(double xlo, double xhi, double W, double org, int nk, int *k0, int *k1)
 {
-    /* candidate k with |x - org - k| < W for some x in [xlo, xhi] */
+    /* candidate k with |x - org - k| < W for some x in [xlo, xhi], one more
+     * on each side: xlo and xhi are rounded, and the interval test of
+     * for_each_pair alone must decide which bases count */
     double a = xlo - org - W, b = xhi - org + W;
-    double fa = floor(a), fb = ceil(b);
+    double fa = floor(a) - 1.0, fb = ceil(b) + 1.0;
     if (fa < 0) fa = 0;
     if (fa > nk) fa = nk;
     if (fb > nk - 1) fb = nk - 1;

@@ -111,6 +111,45 @@ def train(mlp: "spl.Mlp", data: FootprintSet, steps: int, batch: int = 8192, lr0
     return hist
 
 
+def add_hardest(mlp: "spl.Mlp", data: FootprintSet, pool: FootprintSet, count: int, copies: int = 2):
+    """Append to the training set the `count` samples of `pool` on which
+    f_theta (as the tensor-core kernel evaluates it) errs most, `copies`
+    times each (hard-example mining: more weight where the network is
+    worst)."""
+    out = torch.empty_like(pool.label)
+    spl.footprint(spl.basis(pool.degree, spl.SPL_FP_MLP, mlp), pool.omega, pool.p, out)
+    idx = torch.topk((out - pool.label).abs(), min(int(count), pool.count)).indices
+    data.feat = torch.cat([data.feat] + [pool.feat.index_select(0, idx)] * copies)
+    data.label = torch.cat([data.label] + [pool.label.index_select(0, idx)] * copies)
+    data.count = int(data.label.numel())
+
+
+# The training recipe of the measurements: Algorithm 1's samples kept inside
+# the exact support, half of the directions near the coordinate axes and
+# offsets drawn toward the peak; 200 000 Adam steps, then two rounds of
+# hard-example mining (the 2^19 worst of 2^23 fresh in-support samples added
+# twice, 150 000 more steps each).
+RECIPE = {"set": dict(support_only=True, axis_fraction=0.5, axis_scale=12.0, center_power=3.0),
+          "steps": 200000, "lr0": 3e-3, "lr_min": 1e-5, "mine_rounds": 2, "mine_pool": 1 << 23,
+          "mine_count": 1 << 19, "mine_steps": 150000, "mine_lr0": 1e-3}
+
+
+def train_recipe(mlp: "spl.Mlp", degree: int, count: int = 1 << 22, seed: int = 31, scale: float = 1.0,
+                 device="cuda") -> FootprintSet:
+    """Train f_theta with RECIPE (step counts times `scale`); returns the
+    final training set."""
+    r = RECIPE
+    data = FootprintSet(degree, count, seed=seed, device=device, **r["set"])
+    train(mlp, data, steps=max(1, int(r["steps"] * scale)), batch=8192, lr0=r["lr0"], lr_min=r["lr_min"])
+    for k in range(r["mine_rounds"]):
+        pool = FootprintSet(degree, r["mine_pool"], seed=seed + 1000 + k, device=device, support_only=True)
+        add_hardest(mlp, data, pool, r["mine_count"])
+        del pool
+        train(mlp, data, steps=max(1, int(r["mine_steps"] * scale)), batch=8192, lr0=r["mine_lr0"], lr_min=1e-6,
+              seed=k + 1)
+    return data
+
+
 def save(mlp: "spl.Mlp", path: str):
     """Checkpoint of the training state (spl_mlp_save: header with the
     network's shape, degree, dtype, seed and Adam step; master parameters and
