@@ -248,12 +248,33 @@ spl_status spl_adjoint(const spl_geometry *g, const spl_basis_desc *basis, const
                        void *stream);
 
 /* Work of one forward projection, added to count_dev (uint64 [3], device):
- * count_dev[0] += number of (ray, basis) pairs with a nonzero footprint (the
- * contributions of Eq. 4); count_dev[1] += integrated pieces of rays with
- * three nonzero direction components (one Gauss-Legendre rule of
- * ceil((3n+1)/2) nodes each); count_dev[2] += pieces of rays with a zero
- * component (n+1 nodes each: the third factor is constant along the ray). */
+ * count_dev[0] += number of contributions of Eq. 4: (ray, basis) pairs whose
+ * line meets the open support cube of the basis in a segment of positive
+ * length, decided exactly as spl_count_pairs_per_ray does;
+ * count_dev[1] += pieces the march integrates with the full Gauss-Legendre
+ * rule of ceil((3n+1)/2) nodes (rays with three nonzero direction
+ * components, and every cone ray); count_dev[2] += pieces of parallel and
+ * explicit rays with a zero component (n+1 nodes each: the third factor is
+ * constant along the ray). */
 spl_status spl_count_pairs(const spl_geometry *g, int degree, unsigned long long *count_dev, void *stream);
+
+/* The contributions of Eq. 4 ray by ray: per_ray_dev[r] (uint32, n_rays,
+ * nullable) = the number of bases k of the grid whose open support cube
+ * [k - W, k + W]^3 (W = (n+1)/2) the line of ray r meets in a segment of
+ * positive length, and *total_dev (uint64, device) += their sum.  The
+ * decision is made in FP64 with the plain definition's operations, each
+ * rounded separately (no fused multiply-add): the ray is rebuilt from the
+ * caller's arrays as given (pixel centre (det_center + a det_u) + b det_v,
+ * direction over sqrt((d0 d0 + d1 d1) + d2 d2)); along each axis e with
+ * w_e != 0, p = s_e - (origin_e + k_e) and the line is inside the support
+ * slab for t between (-W - p)/w_e and (W - p)/w_e; along an axis with
+ * w_e = 0, k_e is admitted when the truncated-power B-spline sum
+ * (1/n!) sum_j (-1)^j C(n+1,j) (W - |p| - j)_+^n is positive (degree 0:
+ * -1/2 <= p < 1/2); a pair counts when the largest lower end is below the
+ * smallest upper end.  Errors: SPL_ERR_ARG; the geometry's error flag
+ * (SPL_ERR_STEPCAP) if a ray's interval queue overflowed (not expected). */
+spl_status spl_count_pairs_per_ray(const spl_geometry *g, int degree, unsigned *per_ray_dev,
+                                   unsigned long long *total_dev, void *stream);
 
 /* Footprint Pphi(w, p) (Eq. 4's contribution) of the basis at the origin for
  * `count` (direction, offset) pairs.

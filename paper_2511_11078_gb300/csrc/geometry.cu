@@ -404,10 +404,40 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
     }
 
     cudaGetDevice(&g->device);
-    const size_t flag_off = (payload + 255) & ~(size_t)255;
+    // the caller's arrays as given (the exact pair count rebuilds rays from them)
+    const size_t raw_off = (payload + 255) & ~(size_t)255;
+    const size_t raw_bytes = d.kind == SPL_RAYS ? (size_t)d.n_rays * 6 * sizeof(double)
+                                                : (size_t)d.n_views * 12 * sizeof(double);
+    double *raw_host = (double *)malloc(raw_bytes > 0 ? raw_bytes : 1);
+    if (!raw_host) {
+        free(ray_host);
+        free(view_order);
+        plane_free(g->plane);
+        free(g->vconst);
+        free(g->views_host);
+        free(g);
+        return fail(SPL_ERR_OOM, "host allocation failed");
+    }
+    if (d.kind == SPL_RAYS) {
+        for (long long r = 0; r < d.n_rays; ++r)
+            for (int e = 0; e < 3; ++e) {
+                raw_host[6 * r + e] = d.ray_omega[3 * r + e];
+                raw_host[6 * r + 3 + e] = d.ray_s[3 * r + e];
+            }
+    } else {
+        for (int k = 0; k < d.n_views; ++k)
+            for (int e = 0; e < 3; ++e) {
+                raw_host[12 * k + e] = d.view_src[3 * k + e];
+                raw_host[12 * k + 3 + e] = d.det_center[3 * k + e];
+                raw_host[12 * k + 6 + e] = d.det_u[3 * k + e];
+                raw_host[12 * k + 9 + e] = d.det_v[3 * k + e];
+            }
+    }
+    const size_t flag_off = (raw_off + raw_bytes + 255) & ~(size_t)255;
     void *blk = nullptr;
     cudaError_t ce = cudaMalloc(&blk, flag_off + 256);
     if (ce != cudaSuccess) {
+        free(raw_host);
         free(ray_host);
         free(view_order);
         plane_free(g->plane);
@@ -423,7 +453,9 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
     if (src_bytes > 0) ce = cudaMemcpy(blk, src, src_bytes, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && view_order && d.n_views > 0)
         ce = cudaMemcpy((char *)blk + order_off, view_order, (size_t)d.n_views * sizeof(int), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && raw_bytes > 0) ce = cudaMemcpy((char *)blk + raw_off, raw_host, raw_bytes, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset((char *)blk + flag_off, 0, 256);
+    free(raw_host);
     free(ray_host);
     free(view_order);
     if (ce != cudaSuccess) {
@@ -441,6 +473,7 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
         dg.views = (const ViewPose *)blk;
         if (d.kind == SPL_PARALLEL) dg.view_order = (const int *)((const char *)blk + order_off);
     }
+    dg.raw = (const double *)((const char *)blk + raw_off);
     dg.err = (int *)((char *)blk + flag_off);
     // The scatter adjoint of a geometry with more than one batch of views
     // (rays) adds the batches in an FP64 accumulator of the grid's size

@@ -329,7 +329,7 @@ __device__ __forceinline__ void march_count(int kind, const RaySetup &rs, const 
     sk.pieces = 0u;
     if (!march_kind<N>(kind, rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
     const bool flat = rs.rb == 0.0f && kind != SPL_CONE;
-    pairs = sk.n;
+    pairs = sk.n;  // (nonzero FP32 footprints; the contributions come from the exact count)
     pieces = flat ? 0u : sk.pieces;
     flat_pieces = flat ? sk.pieces : 0u;
 }
@@ -352,7 +352,6 @@ __global__ void __launch_bounds__(128) k_count_views(DevGeom g, unsigned long lo
     RaySetup rs;
     if (iu < g.nu && iv < g.nv && view_setup<N>(g, grid_of(g), k, iu, iv, rs))
         march_count<N>(g.kind, rs, qr, g.err, v, pc, pf);
-    add_count(count, v);
     add_count(count + 1, pc);
     add_count(count + 2, pf);
 }
@@ -368,7 +367,6 @@ __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long lon
         RaySetup rs;
         if (ray_setup<N>(grid_of(g), s, w, rs)) march_count<N>(SPL_RAYS, rs, qr, g.err, v, pc, pf);
     }
-    add_count(count, v);
     add_count(count + 1, pc);
     add_count(count + 2, pf);
 }
@@ -883,6 +881,8 @@ static spl_status count_pairs(const spl_geometry *g, unsigned long long *count, 
     const DevGeom &dg = g->dev;
     const QuadRule qr = quad_rule(N);
     if (dg.n_rays == 0) return SPL_OK;
+    spl_status s = count_exact(g, N, count, nullptr, st);
+    if (s != SPL_OK) return s;
     if (dg.kind == SPL_RAYS) {
         const long long blocks = (dg.n_rays + 127) / 128;
         k_count_rays<N><<<(unsigned)blocks, 128, 0, st>>>(dg, count, qr);

@@ -91,6 +91,10 @@ QuadRule quad_rule(int degree);
 int set_iter_cap(int cap);
 int quad_nodes(int degree);
 
+// Exact pair count (count.cu): adds to *total, per ray into per_ray (nullable).
+spl_status count_exact(const spl_geometry *g, int degree, unsigned long long *total, unsigned *per_ray,
+                       cudaStream_t st);
+
 // Validate a basis descriptor against a geometry (nullable).
 spl_status check_basis(const spl_basis_desc *b);
 

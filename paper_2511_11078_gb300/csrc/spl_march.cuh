@@ -183,6 +183,10 @@ struct DevGeom {
     int n_flat;             // flat views, the group included (view_order[0 .. n_flat))
     const double *ray_w; // [n_rays][3] unit directions
     const double *ray_s; // [n_rays][3]
+    // the caller's FP64 arrays as given: per view (direction or source,
+    // detector centre, det_u, det_v), per ray (direction, point); the exact
+    // pair count rebuilds each ray from them
+    const double *raw;
     int *err;            // device error flag (bit 0: a loop bound was reached)
 };
 

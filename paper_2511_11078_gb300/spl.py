@@ -63,6 +63,7 @@ _SIGS = {
     "spl_forward": (C.c_int, [_vp, C.POINTER(BasisDesc), _vp, _vp, _vp]),
     "spl_adjoint": (C.c_int, [_vp, C.POINTER(BasisDesc), _vp, _vp, _vp]),
     "spl_count_pairs": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "spl_count_pairs_per_ray": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "spl_footprint": (C.c_int, [C.POINTER(BasisDesc), C.c_longlong, _vp, _vp, _vp, _vp]),
     "spl_features": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp, _vp, _vp]),
     "spl_footprint_samples": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp, _vp, _vp, _vp]),
@@ -251,9 +252,10 @@ def adjoint(geom: Geometry, y, c, bas: BasisDesc, stream=None):
 
 
 def count_work(geom: Geometry, degree: int, stream=None):
-    """(pairs, pieces, flat_pieces) of one forward projection: contributions
-    with a nonzero footprint, integrated pieces with the full Gauss rule and
-    with the (n+1)-node rule of rays with a zero direction component."""
+    """(pairs, pieces, flat_pieces) of one forward projection: the
+    contributions of Eq. 4 (exact pair count), integrated pieces with the
+    full Gauss rule and with the (n+1)-node rule of rays with a zero
+    direction component."""
     import torch
 
     cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
@@ -264,6 +266,16 @@ def count_work(geom: Geometry, degree: int, stream=None):
 
 def count_pairs(geom: Geometry, degree: int, stream=None) -> int:
     return count_work(geom, degree, stream)[0]
+
+
+def count_pairs_per_ray(geom: Geometry, degree: int, stream=None):
+    """(contributions of each ray as a uint32 CUDA tensor, their total)."""
+    import torch
+
+    per = torch.zeros(geom.n_rays, dtype=torch.int32, device="cuda")
+    tot = torch.zeros(1, dtype=torch.int64, device="cuda")
+    check(lib().spl_count_pairs_per_ray(geom.handle, int(degree), _ptr(per), _ptr(tot), _stream(stream)))
+    return per, int(tot.item())
 
 
 def footprint(bas: BasisDesc, omega, p, out, stream=None):

@@ -352,14 +352,63 @@ def test_footprint_exact(env, orc, degree):
 
 @pytest.mark.parametrize("degree", [0, 3])
 def test_pair_count(env, orc, degree):
+    """The contribution count (the metric's denominator) is index work: the
+    GPU count equals the oracle's, ray by ray, on parallel, tilt (a zero
+    direction component), cone and explicit-ray geometries."""
     torch, spl = env
     rng = np.random.default_rng(1900 + degree)
     origin = I.centred_origin(DIMS)
-    geo = parallel_geometry(rng)
+    for geo in (parallel_geometry(rng), tilt_geometry(0), cone_geometry(), ray_geometry(rng, DIMS, origin)):
+        g = spl.Geometry(DIMS, origin, geo)
+        per, tot = spl.count_pairs_per_ray(g, degree)
+        g.status()
+        ref_tot, ref = orc.count_pairs(degree, DIMS, origin, oracle_geom(orc, geo), per_ray=True)
+        assert tot == ref_tot, (geo.kind, tot, ref_tot)
+        np.testing.assert_array_equal(per.cpu().numpy().astype(np.int64), ref)
+        assert spl.count_pairs(g, degree) == ref_tot
+
+
+def grazing_rays(dims, origin, n):
+    """Rays that touch support boundaries: axis-aligned and diagonal lines
+    whose transverse coordinates sit exactly on, or one ulp beside, the
+    faces k +- W of a basis support, lines along support edges, lines
+    through support corners, and lines lying in knot planes."""
+    W = 0.5 * (n + 1)
+    org = np.asarray(origin)
+    ctr = org + (np.asarray(dims) - 1) // 2
+    w, s = [], []
+    for off in (W, -W, np.nextafter(W, 0), np.nextafter(W, 10), 0.5, 1.0, 0.0):
+        for ax in range(3):
+            d = np.zeros(3)
+            d[ax] = 1.0
+            t = [(ax + 1) % 3, (ax + 2) % 3]
+            p = ctr.copy()
+            p[t[0]] += off
+            w.append(d.copy())
+            s.append(p.copy())
+            p[t[1]] += off  # along a support edge
+            w.append(d.copy())
+            s.append(p.copy())
+    for v in ([1, 1, 0], [1, 1, 1], [1, -1, 1], [0, 1, 1], [1, 2, 0]):
+        d = np.asarray(v, dtype=np.float64)
+        for off in (W, np.nextafter(W, 0), 0.0):
+            p = ctr + np.array([off, 0.0, 0.0])  # passes through support corners / edges
+            w.append(d.copy())
+            s.append(p)
+    return I.RayGeometry(np.array(w), np.array(s))
+
+
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_pair_count_grazing_and_face_rays(env, orc, degree):
+    torch, spl = env
+    origin = I.centred_origin(DIMS)
+    geo = grazing_rays(DIMS, origin, degree)
     g = spl.Geometry(DIMS, origin, geo)
-    got = spl.count_pairs(g, degree)
-    ref = orc.count_pairs(degree, DIMS, origin, oracle_geom(orc, geo))
-    assert abs(got - ref) <= 1e-5 * ref, (got, ref)
+    per, tot = spl.count_pairs_per_ray(g, degree)
+    g.status()
+    ref_tot, ref = orc.count_pairs(degree, DIMS, origin, oracle_geom(orc, geo), per_ray=True)
+    np.testing.assert_array_equal(per.cpu().numpy().astype(np.int64), ref)
+    assert tot == ref_tot
 
 
 def test_kahan_off_still_accurate(env, orc):
@@ -513,6 +562,9 @@ def full_size_check(env, orc, wl, class_views, seed):
     spl.forward(g, ct, y, spl.basis(3))
     g.status()
     yh = y.cpu().numpy().astype(np.float64)
+    per, _ = spl.count_pairs_per_ray(g, 3)
+    g.status()
+    per = per.cpu().numpy().astype(np.int64)
     for name, views in class_views.items():
         rays = stratified_rays(geo, views, N_RAYS, seed)
         assert rays.size >= N_RAYS * 0.97
@@ -520,6 +572,8 @@ def full_size_check(env, orc, wl, class_views, seed):
         assert pairs.sum() > 0, name
         err = rel_l2(yh[rays], yref)
         assert err <= TOL, (name, err)
+        # the contribution count of every sampled ray, exactly
+        np.testing.assert_array_equal(per[rays], pairs)
     # mixed signs, as a CG residual: the hard case for the adjoint's sums
     rng = np.random.default_rng(seed + 1)
     yv = rng.normal(size=g.n_rays).astype(np.float32)
@@ -537,12 +591,16 @@ def full_size_check(env, orc, wl, class_views, seed):
 
 def test_full_size_tilt128(env, orc):
     """128^3 cubic, 244 parallel views of 192x192: the 180 slice-separable
-    tilt views (plane matrices) and the 64 general views (piece march)."""
+    tilt views (plane matrices) and the 64 general views (piece march); the
+    whole workload's contribution count equals the oracle's."""
+    torch, spl = env
     wl = I.workload_tilt(3)
     src = np.asarray(wl.geometry.src)
     flat = np.nonzero(np.any(src == 0.0, axis=1))[0]
     gen = np.nonzero(~np.any(src == 0.0, axis=1))[0]
     full_size_check(env, orc, wl, {"separable": flat, "general": gen}, 2400)
+    g = spl.Geometry(wl.dims, wl.origin, wl.geometry)
+    assert spl.count_pairs(g, 3) == orc.count_pairs(3, wl.dims, wl.origin, oracle_geom(orc, wl.geometry))
 
 
 def test_full_size_cone256(env, orc):
