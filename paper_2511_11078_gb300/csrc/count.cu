@@ -129,20 +129,29 @@ struct Axis {
     }
 };
 
+// An FP64 value as an integer with the same order (-0 and +0 equal): the
+// comparisons of the sweep then run on the integer units (GB300's FP64
+// throughput is a small fraction of its integer throughput).
+__device__ __forceinline__ long long okey(double x)
+{
+    const long long b = __double_as_longlong(__dadd_rn(x, 0.0));  // -0 -> +0
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+
 // a queue of the intervals of one transverse axis (a contiguous run of its
-// indices in traversal order); storage in shared memory
+// indices in traversal order), as order keys; storage in shared memory
 struct Queue {
-    double *lo, *hi;  // kQueue entries each, strided by the block size
+    long long *lo, *hi;  // kQueue entries each, strided by the block size
     int head, len;
-    int next;         // next index to consider (traversal order)
-    bool flat;        // w = 0: a fixed set of indices with (-inf, inf)
-    __device__ __forceinline__ double &L(int i) { return lo[((head + i) & (kQueue - 1)) * kCountThreads]; }
-    __device__ __forceinline__ double &H(int i) { return hi[((head + i) & (kQueue - 1)) * kCountThreads]; }
+    int next;            // next index to consider (traversal order)
+    bool flat;           // w = 0: a fixed set of indices with (-inf, inf)
+    __device__ __forceinline__ long long &L(int i) { return lo[((head + i) & (kQueue - 1)) * kCountThreads]; }
+    __device__ __forceinline__ long long &H(int i) { return hi[((head + i) & (kQueue - 1)) * kCountThreads]; }
 };
 
 // prepare an axis' queue: flat axes get their admitted indices; others
 // start at the first index that may end after t0
-__device__ bool queue_init(Queue &q, const Axis &ax, int deg, double t0, double *slo, double *shi)
+__device__ bool queue_init(Queue &q, const Axis &ax, int deg, double t0, long long *slo, long long *shi)
 {
     q.lo = slo;
     q.hi = shi;
@@ -155,8 +164,8 @@ __device__ bool queue_init(Queue &q, const Axis &ax, int deg, double t0, double 
             if (!(fabs(p) < ax.W + 1.0)) continue;
             if (!bspline_positive(deg, p)) continue;
             if (q.len == kQueue) return false;
-            q.L(q.len) = -INFINITY;
-            q.H(q.len) = INFINITY;
+            q.L(q.len) = okey(-INFINITY);
+            q.H(q.len) = okey(INFINITY);
             ++q.len;
         }
         q.next = -1;
@@ -168,14 +177,15 @@ __device__ bool queue_init(Queue &q, const Axis &ax, int deg, double t0, double 
 
 // bring the queue to the run of intervals overlapping (Ld, Hd): push while
 // the next interval starts before Hd, pop while the first ends at or before Ld
-__device__ bool queue_advance(Queue &q, const Axis &ax, double Ld, double Hd)
+__device__ bool queue_advance(Queue &q, const Axis &ax, long long Ld, long long Hd)
 {
     if (q.flat) return true;
     for (int it = 0; it < 2 * ax.n + 8; ++it) {
         if (!ax.inside(q.next)) break;
         double lo, hi;
         ax.iv(q.next, lo, hi);
-        if (!(lo < Hd)) break;
+        const long long kl = okey(lo);
+        if (!(kl < Hd)) break;
         if (q.len == kQueue) {
             // the front must end before the slab for the run to exceed
             // the capacity; drop it if it does, otherwise give up
@@ -183,8 +193,8 @@ __device__ bool queue_advance(Queue &q, const Axis &ax, double Ld, double Hd)
             q.head = (q.head + 1) & (kQueue - 1);
             --q.len;
         }
-        q.L(q.len) = lo;
-        q.H(q.len) = hi;
+        q.L(q.len) = kl;
+        q.H(q.len) = okey(hi);
         ++q.len;
         q.next += ax.step;
     }
@@ -197,7 +207,7 @@ __device__ bool queue_advance(Queue &q, const Axis &ax, double Ld, double Hd)
 
 template <int DEG>
 __device__ unsigned long long count_ray(const DevGeom &g, const double (&s)[3], const double (&w)[3], bool &ok,
-                                        double *slo, double *shi)
+                                        long long *slo, long long *shi)
 {
     constexpr double W = 0.5 * (DEG + 1);
     // dominant axis d (any axis with w != 0 would do), the others a, b
@@ -233,24 +243,30 @@ __device__ unsigned long long count_ray(const DevGeom &g, const double (&s)[3], 
     unsigned long long count = 0;
     int kd = A[d].start_after(t0);
     for (int it = 0; it < A[d].n + 1 && A[d].inside(kd); ++it, kd += A[d].step) {
-        double Ld, Hd;
-        A[d].iv(kd, Ld, Hd);
+        double ld, hd;
+        A[d].iv(kd, ld, hd);
+        const long long Ld = okey(ld), Hd = okey(hd);
         if (!queue_advance(qa, A[a], Ld, Hd) || !queue_advance(qb, A[b], Ld, Hd)) {
             ok = false;
             return count;
         }
-        // nothing left to meet: both transverse axes exhausted past this slab
+        // nothing left to meet: a transverse axis exhausted past this slab
         if ((qa.len == 0 && !qa.flat && !A[a].inside(qa.next)) || (qb.len == 0 && !qb.flat && !A[b].inside(qb.next)))
             break;
+        // For each a of the run, (L1, H1) = its interval within the slab's;
+        // b counts when lo_b < H1 and hi_b > L1.  Both ends of the b
+        // intervals increase along the run, so the b with lo_b < H1 form a
+        // prefix, those with hi_b <= L1 a shorter prefix, and the count is
+        // the difference; L1 and H1 increase with a, so both prefix ends
+        // only move forward.
+        int jl = 0, jh = 0;
         for (int i = 0; i < qa.len; ++i) {
-            const double la = qa.L(i), ha = qa.H(i);
-            const double L1 = la > Ld ? la : Ld, H1 = ha < Hd ? ha : Hd;
+            const long long la = qa.L(i), ha = qa.H(i);
+            const long long L1 = la > Ld ? la : Ld, H1 = ha < Hd ? ha : Hd;
             if (!(H1 > L1)) continue;
-            for (int j = 0; j < qb.len; ++j) {
-                const double lb = qb.L(j), hb = qb.H(j);
-                const double L2 = lb > L1 ? lb : L1, H2 = hb < H1 ? hb : H1;
-                count += (H2 > L2) ? 1u : 0u;
-            }
+            while (jl < qb.len && qb.L(jl) < H1) ++jl;
+            while (jh < qb.len && qb.H(jh) <= L1) ++jh;
+            count += jl > jh ? (unsigned long long)(jl - jh) : 0ull;
         }
     }
     return count;
@@ -261,7 +277,7 @@ template <int DEG>
 __global__ void __launch_bounds__(kCountThreads) k_count_exact(DevGeom g, unsigned long long *total,
                                                                unsigned *per_ray)
 {
-    __shared__ double qlo[2 * kQueue * kCountThreads], qhi[2 * kQueue * kCountThreads];
+    __shared__ long long qlo[2 * kQueue * kCountThreads], qhi[2 * kQueue * kCountThreads];
     const long long r = (long long)blockIdx.x * kCountThreads + threadIdx.x;
     unsigned long long c = 0;
     if (r < g.n_rays) {
