@@ -32,8 +32,11 @@ Besides the headline the line carries:
 
 --impl reference times the FP64 CPU oracle (as it stands) on the host cores,
 each step a bounded sample of the same workload.  Under torchrun (N > 1)
-every rank runs an independent replica of the workload on its own GPU
-(weak scaling); rank 0 prints the JSON line with the max-over-ranks time.
+the workload's views are split across the ranks, one GPU each (strong
+scaling): A needs no exchange, A^T one all-reduce of the coefficients per
+iteration and the FP64 inner products scalar all-reduces (NCCL); rank 0
+prints the JSON line with the max-over-ranks step time and the whole job's
+contributions.
 """
 from __future__ import annotations
 
@@ -112,7 +115,7 @@ def dist_env():
 
 def max_over_ranks(value: float, ws: int, device=None) -> float:
     """The largest of the ranks' values (the step time of the slowest
-    replica); the value itself at one rank."""
+    rank); the value itself at one rank."""
     if ws <= 1:
         return float(value)
     import torch
@@ -123,11 +126,11 @@ def max_over_ranks(value: float, ws: int, device=None) -> float:
     return float(t.item())
 
 
-def replica_value(ws: int, contributions_per_step: float, ms: float) -> float:
-    """Whole-job throughput of ws independent replicas (weak scaling): the
-    contributions all ranks processed per second at the slowest rank's step
-    time, in G-contributions/s."""
-    return ws * contributions_per_step / (ms * 1e-3) / 1e9
+def job_value(contributions_per_step: float, ms: float) -> float:
+    """Whole-job throughput: the contributions all ranks together processed
+    in one step, per second of the slowest rank's step time, in
+    G-contributions/s."""
+    return contributions_per_step / (ms * 1e-3) / 1e9
 
 
 def measured_peaks():
@@ -366,7 +369,7 @@ def fp32_peak(dev, local):
 # --------------------------------------------------------------------------
 # oracle leg: error of the timed operators and the CPU baseline
 # --------------------------------------------------------------------------
-def oracle_leg(args, wl, geom, proj, c_true, dev):
+def oracle_leg(args, wl, geom, ops, c_true, dev):
     """A c_true and A^T (y on a ray sample, zero elsewhere) by the timed GPU
     operators against the FP64 oracle on the same sample; the oracle's time
     is the CPU baseline."""
@@ -382,11 +385,11 @@ def oracle_leg(args, wl, geom, proj, c_true, dev):
     ys = np.random.default_rng(2027).uniform(0.0, 1.0, rays.size).astype(np.float32)
     # GPU side (the operators as timed)
     yg = torch.empty(geom.n_rays, dtype=torch.float32, device=dev)
-    proj.forward(c_true, out=yg)
+    ops.forward(c_true, yg)
     ymask = torch.zeros(geom.n_rays, dtype=torch.float32, device=dev)
     ymask[torch.tensor(rays, device=dev)] = torch.tensor(ys, device=dev)
     cg = torch.empty_like(c_true)
-    proj.adjoint(ymask, out=cg)
+    ops.adjoint(ymask, cg)
     torch.cuda.synchronize()
     geom.status()
     ya = yg.cpu().numpy()[rays].astype(np.float64)
@@ -615,8 +618,7 @@ def run_ours(args):
 
     from paper_2511_11078_gb300 import build as B
     from paper_2511_11078_gb300 import inputs as I
-    from paper_2511_11078_gb300 import spl
-    from paper_2511_11078_gb300.recon import CGLS, Projector
+    from paper_2511_11078_gb300 import shard, spl
 
     B.build()
     spl.lib()
@@ -624,21 +626,29 @@ def run_ours(args):
     t0 = time.perf_counter()
     wl = I.workload_helical()
     workload_s = time.perf_counter() - t0
-    geom = spl.Geometry(wl.dims, wl.origin, wl.geometry)
     form = spl.SPL_ADJ_GATHER if args.adjoint == "gather" else spl.SPL_ADJ_SCATTER
-    proj = Projector(geom, n)
-    proj.basis = spl.basis(n, adjoint=form)
+    # the views of the workload split across the ranks (all of them at one
+    # rank): A on a rank's views needs no exchange, A^T one sum over ranks
+    ops = shard.ShardedProjector(wl.dims, wl.origin, wl.geometry, rank, ws, n, spl.basis(n, adjoint=form))
+    geom = ops.geom
     c_true = torch.tensor(wl.coeffs, device=dev)
-    y_clean = proj.forward(c_true)
+    y_clean = torch.empty(geom.n_rays, dtype=torch.float32, device=dev)
+    ops.forward(c_true, y_clean)
+    ymax = torch.tensor([float(y_clean.max())], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(ymax, op=torch.distributed.ReduceOp.MAX)
     gen = torch.Generator(device=dev)
-    gen.manual_seed(I.SEED_BASE + 5)
-    sigma = 0.01 * float(y_clean.max())
+    gen.manual_seed(I.SEED_BASE + 5 + 1000 * rank)
+    sigma = 0.01 * float(ymax.item())
     y = y_clean + sigma * torch.randn(y_clean.shape, generator=gen, device=dev)
     del y_clean
-    pairs, pieces, flat_pieces = spl.count_work(geom, n)
+    work = torch.tensor(spl.count_work(geom, n), dtype=torch.float64, device=dev)
     geom.status()
+    if ws > 1:
+        torch.distributed.all_reduce(work)
+    pairs, pieces, flat_pieces = (int(v) for v in work.tolist())
 
-    cg = CGLS(proj, y)
+    cg = shard.ShardedCGLS(ops, y, c_true.shape)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         cg.step()
@@ -654,19 +664,7 @@ def run_ours(args):
     time.sleep(0.3)
     t_wall0 = time.perf_counter()
     for k in range(args.steps):
-        e0, e1, e2, e3, e4 = ev[k]
-        e0.record(stream)
-        proj.forward(cg.p, out=cg.q)                       # A
-        e1.record(stream)
-        spl.dot_f64(cg.q, cg.q, cg.qq, cg.work)
-        spl.cg_step_x(cg.x, cg.p, cg.r, cg.q, cg.gamma, cg.qq)
-        e2.record(stream)
-        proj.adjoint(cg.r, out=cg.s)                       # A^T
-        e3.record(stream)
-        spl.dot_f64(cg.s, cg.s, cg.gamma_new, cg.work)
-        spl.cg_step_p(cg.p, cg.s, cg.gamma_new, cg.gamma)
-        cg.gamma, cg.gamma_new = cg.gamma_new, cg.gamma
-        e4.record(stream)
+        cg.step(lambda i, k=k: ev[k][i].record(stream))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     if ws > 1:
@@ -677,21 +675,23 @@ def run_ours(args):
     fwd = statistics.median([ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)])
     adj = statistics.median([ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)])
     ms = max_over_ranks(sum(step_ms) / args.steps, ws, dev)
-    contrib_step = 2 * pairs  # A and A^T visit the same pairs
-    value = replica_value(ws, contrib_step, ms)
+    contrib_step = 2 * pairs  # A and A^T visit the same pairs (all ranks together)
+    value = job_value(contrib_step, ms)
     clocks = sampler.summary()
 
     # end to end: the same iteration with host-resident state
     e2e_steps = max(1, min(args.steps, 2))
     e2e_ms, h2d, d2h, e2e_ok = e2e_leg(cg, e2e_steps, stream)
+    e2e_ms = max_over_ranks(e2e_ms, ws, dev)
     geom.status()
 
     peak = fp32_peak(dev, local)
     # dominant kernel: the slower of A (k_forward_views) and A^T
     # (k_adjoint_views_scatter) on the cone views; its algorithmic FP32 work
-    # is the nodes it integrates plus one FMA per contribution
+    # is the nodes it integrates plus one FMA per contribution (this rank's
+    # share of the work: the launch covers its views)
     flops = (pieces * NODES_PER_PIECE[n] * FLOP_PER_NODE[n] + flat_pieces * (n + 1) * FLOP_PER_FLAT_NODE[n]
-             + pairs * FLOP_PER_PAIR)
+             + pairs * FLOP_PER_PAIR) / ws
     if fwd >= adj:
         kname, dom_ms = "k_forward_views", fwd
     else:
@@ -706,7 +706,7 @@ def run_ours(args):
                 "algorithmic_flop_per_launch": flops, "launch_ms": dom_ms, "csrc_sha16": csrc_sha16()}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_tag, "degree": n, "footprint": "exact quadrature",
                        "adjoint": args.adjoint, "coeffs": list(wl.dims), "views": wl.geometry.n_views,
@@ -714,11 +714,12 @@ def run_ours(args):
                        "SOD 1000, SDD 1500, detector pitch 0.8",
                        "contributions_per_A": pairs, "pieces_per_A": pieces, "flat_pieces_per_A": flat_pieces,
                        "l2": "inputs larger than L2 (c 512 MB, y 1.7 GB); no flush",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": ("views sharded over %d GPUs (A: no exchange; A^T: one all-reduce of c; "
+                                       "FP64 dots: scalar all-reduces)" % ws) if ws > 1 else "single GPU"},
             "s_per_recon_iter": ms / 1e3,
             "A_ms": fwd, "AT_ms": adj,
             "A_gcontrib_s": pairs / (fwd * 1e-3) / 1e9, "AT_gcontrib_s": pairs / (adj * 1e-3) / 1e9,
-            "e2e": {"value": replica_value(ws, contrib_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_value(contrib_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
                     "what": "the CGLS iteration with x, r, p in pinned host memory: uploaded before and "
                             "downloaded (with gamma) after every step", "finite": e2e_ok},
@@ -732,10 +733,10 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        err, cpu = oracle_leg(args, wl, geom, proj, c_true, dev)
+        err, cpu = oracle_leg(args, wl, geom, ops, c_true, dev)
         line["rel_l2_vs_oracle"] = err
         line["cpu_baseline"] = cpu
-    del c_true, y, geom, proj
+    del c_true, y, geom, ops
     torch.cuda.empty_cache()
     if not args.no_secondary:
         line["secondary"] = secondary_tilt(dev)

@@ -1,7 +1,6 @@
-"""The benchmark's multi-process path on CPU (gloo, world size 2): every rank
-runs its own replica, the step time is the maximum over ranks, the value is
-the whole job's throughput at that time, and the reference arm runs on rank 0
-only."""
+"""The benchmark's multi-process bookkeeping on CPU (gloo, world size 2): the
+step time is the maximum over ranks, the value is the whole job's
+contributions over that time, and the reference arm runs on rank 0 only."""
 import os
 import socket
 import subprocess
@@ -28,7 +27,7 @@ def _worker(rank, ws, port, times, out):
 
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     ms = bench.max_over_ranks(times[rank], ws)
-    out.put((rank, ms, bench.replica_value(ws, 1e9, ms)))
+    out.put((rank, ms, bench.job_value(2e9, ms)))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -48,8 +47,8 @@ def test_max_over_ranks_and_value_with_two_gloo_ranks():
         p.join(timeout=60)
         assert p.exitcode == 0
     for rank, ms, value in res:
-        assert ms == 20.0  # the slowest replica's step time on every rank
-        assert value == pytest.approx(2 * 1e9 / 20e-3 / 1e9)  # both replicas' work over that time
+        assert ms == 20.0  # the slowest rank's step time on every rank
+        assert value == pytest.approx(2e9 / 20e-3 / 1e9)  # the whole job's work over that time
 
 
 def test_one_rank_keeps_its_own_time():
@@ -57,7 +56,7 @@ def test_one_rank_keeps_its_own_time():
     import bench
 
     assert bench.max_over_ranks(7.0, 1) == 7.0
-    assert bench.replica_value(1, 2e9, 10.0) == pytest.approx(200.0)
+    assert bench.job_value(2e9, 10.0) == pytest.approx(200.0)
 
 
 def test_reference_arm_runs_on_rank_zero_only():
