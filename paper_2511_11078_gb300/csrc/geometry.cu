@@ -296,6 +296,14 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
                 free(g->views_host); free(g);
                 return fail(SPL_ERR_NONFINITE, "view %d is not finite", k);
             }
+            // neighbouring lanes of a warp hold neighbouring detector
+            // columns, so their rays lie side by side along det_u: the
+            // scatter adjoint of a cone view reduces into a copy of c whose
+            // contiguous axis is det_u's largest component (ties: lowest
+            // axis), where the lanes' reductions share L2 sectors
+            P.lay = 0;
+            for (int e = 1; e < 3; ++e)
+                if (fabs(P.du[e]) > fabs(P.du[P.lay])) P.lay = e;
             double n[3];
             cross3(P.du, P.dv, n);
             const double nn = sqrt(dot3(n, n));
@@ -494,6 +502,29 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
             return fail(SPL_ERR_OOM, "cudaMalloc of the adjoint accumulator (%lld doubles) failed", nk);
         }
     }
+    // targets of the scatter adjoint's cone views in the y-fast and z-fast
+    // layouts (folded into c after each batch)
+    g->lay[0] = g->lay[1] = g->lay[2] = nullptr;
+    if (d.kind == SPL_CONE && dg.n_rays > 0) {
+        bool need[3] = {false, false, false};
+        for (int k = 0; k < d.n_views; ++k) need[g->views_host[k].lay] = true;
+        for (int L = 1; L < 3; ++L) {
+            if (!need[L]) continue;
+            ce = cudaMalloc((void **)&g->lay[L], (size_t)nk * sizeof(float));
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                g->lay[L] = nullptr;
+                if (g->lay[1]) cudaFree(g->lay[1]);
+                if (g->acc64) cudaFree(g->acc64);
+                cudaFree(blk);
+                plane_free(g->plane);
+                free(g->vconst);
+                free(g->views_host);
+                free(g);
+                return fail(SPL_ERR_OOM, "cudaMalloc of the adjoint's layout target (%lld floats) failed", nk);
+            }
+        }
+    }
     *out = g;
     return SPL_OK;
 }
@@ -505,6 +536,8 @@ extern "C" void spl_destroy_geometry(spl_geometry *g)
     table_free(g->table);
     free(g->vconst);
     if (g->acc64) cudaFree(g->acc64);
+    for (int L = 1; L < 3; ++L)
+        if (g->lay[L]) cudaFree(g->lay[L]);
     if (g->dev_block) cudaFree(g->dev_block);
     free(g->views_host);
     free(g);

@@ -407,10 +407,15 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
 }
 
 // view geometries, scatter form: the forward's thread mapping, float
-// atomics; views v0 + blockIdx.z
+// atomics; views v0 + blockIdx.z.  A view reduces into the target of its
+// layout (ViewPose::lay): c itself (x fast), c1 = [z][x][y] (y fast) or
+// c2 = [y][x][z] (z fast), so that the lanes of a warp, whose rays lie
+// side by side along det_u, reduce into neighbouring addresses; the
+// targets are folded into c after the launch (k_fold_transpose).
 template <int N>
 __global__ void __launch_bounds__(128, 3)
-    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr, int v0)
+    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, float *__restrict__ c1,
+                            float *__restrict__ c2, QuadRule qr, int v0)
 {
     int iu, iv;
     tile_pixel(iu, iv);
@@ -418,8 +423,46 @@ __global__ void __launch_bounds__(128, 3)
     if (iu >= g.nu || iv >= g.nv) return;
     const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
     if (yr == 0.0f) return;
+    const int L = g.views[k].lay;
+    GridBox gb = grid_of(g);
+    float *t = c;
+    if (L == 1) {
+        gb.stride[0] = g.n[1];
+        gb.stride[1] = 1;
+        t = c1;
+    } else if (L == 2) {
+        gb.stride[0] = g.n[2];
+        gb.stride[1] = g.n[0] * g.n[2];
+        gb.stride[2] = 1;
+        t = c2;
+    }
     RaySetup rs;
-    if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) scatter_ray<N, VM_CONE>(rs, yr, c, qr, g.err, ncoef_of(g));
+    if (view_setup<N>(g, gb, k, iu, iv, rs)) scatter_ray<N, VM_CONE>(rs, yr, t, qr, g.err, ncoef_of(g));
+}
+
+// out[s][r][q] += in[s][q][r] for slabs s of a Q x R row-major array: the
+// fold of a layout target into c.  y fast: slabs z, Q = nx, R = ny; z fast:
+// one slab, Q = nx ny, R = nz.  32 x 32 tiles through shared memory, both
+// sides coalesced.
+__global__ void __launch_bounds__(256)
+    k_fold_transpose(float *__restrict__ out, const float *__restrict__ in, long long Q, long long R, long long slabs)
+{
+    __shared__ float t[32][33];
+    const long long q0 = (long long)blockIdx.x * 32, r0 = (long long)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (long long sl = blockIdx.z; sl < slabs; sl += gridDim.z) {
+        const size_t base = (size_t)sl * (size_t)Q * (size_t)R;
+        for (int j = ty; j < 32; j += 8) {
+            const long long q = q0 + j, r = r0 + tx;
+            t[j][tx] = (q < Q && r < R) ? in[base + (size_t)q * R + r] : 0.0f;
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const long long r = r0 + j, q = q0 + tx;
+            if (q < Q && r < R) out[base + (size_t)r * Q + q] += t[tx][j];
+        }
+        __syncthreads();
+    }
 }
 
 template <int N, int VM>
@@ -853,10 +896,24 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
             if (s != SPL_OK) return s;
         } else {
             const int per_launch = batched ? kAdjBatchViews : dg.n_views;
+            const long long nx = dg.n[0], ny = dg.n[1], nz = dg.n[2];
             for (int k0 = 0; k0 < dg.n_views; k0 += per_launch) {
                 const int nview = dg.n_views - k0 < per_launch ? dg.n_views - k0 : per_launch;
                 if ((s = begin_batch()) != SPL_OK) return s;
-                k_adjoint_views_scatter<N><<<dim3(gx, gy, nview), 128, 0, st>>>(dg, y, c, qr, k0);
+                bool used[3] = {false, false, false};
+                for (int k = k0; k < k0 + nview; ++k) used[g->views_host[k].lay] = true;
+                for (int L = 1; L < 3; ++L)
+                    if (used[L] && (s = cuda_check(cudaMemsetAsync(g->lay[L], 0, nc * sizeof(float), st),
+                                                   "adjoint layout clear")) != SPL_OK)
+                        return s;
+                k_adjoint_views_scatter<N><<<dim3(gx, gy, nview), 128, 0, st>>>(dg, y, c, g->lay[1], g->lay[2], qr, k0);
+                if (used[1])
+                    k_fold_transpose<<<dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 31) / 32),
+                                            (unsigned)(nz < 65535 ? nz : 65535)),
+                                       256, 0, st>>>(c, g->lay[1], nx, ny, nz);
+                if (used[2])
+                    k_fold_transpose<<<dim3((unsigned)((nx * ny + 31) / 32), (unsigned)((nz + 31) / 32), 1), 256, 0,
+                                       st>>>(c, g->lay[2], nx * ny, nz, 1);
                 end_batch();
             }
             if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);

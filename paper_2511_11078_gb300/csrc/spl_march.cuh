@@ -169,6 +169,8 @@ struct ViewPose {
     double ud[3], vd[3]; // dual axes: a = <P - dc, ud>, b = <P - dc, vd> for P on the plane
     DirSetup dir;        // parallel views: direction set-up shared by all rays of the view
     double e1[3], e2[3]; // parallel views: orthonormal frame of H_w of the footprint tables
+    int lay;             // cone views: array axis kept contiguous by the scatter adjoint's
+                         // target (the largest |det_u| component; see AdjLayout)
 };
 
 struct DevGeom {
