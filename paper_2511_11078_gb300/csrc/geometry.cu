@@ -296,14 +296,6 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
                 free(g->views_host); free(g);
                 return fail(SPL_ERR_NONFINITE, "view %d is not finite", k);
             }
-            // neighbouring lanes of a warp hold neighbouring detector
-            // columns, so their rays lie side by side along det_u: the
-            // scatter adjoint of a cone view reduces into a copy of c whose
-            // contiguous axis is det_u's largest component (ties: lowest
-            // axis), where the lanes' reductions share L2 sectors
-            P.lay = 0;
-            for (int e = 1; e < 3; ++e)
-                if (fabs(P.du[e]) > fabs(P.du[P.lay])) P.lay = e;
             double n[3];
             cross3(P.du, P.dv, n);
             const double nn = sqrt(dot3(n, n));
@@ -502,14 +494,13 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
             return fail(SPL_ERR_OOM, "cudaMalloc of the adjoint accumulator (%lld doubles) failed", nk);
         }
     }
-    // targets of the scatter adjoint's cone views in the y-fast and z-fast
-    // layouts (folded into c after each batch)
+    // the scatter adjoint reduces each piece-marched ray into the copy of c
+    // whose contiguous axis is the ray's b axis: the y-fast and z-fast
+    // copies are scratch of the geometry (folded into c after each batch);
+    // parallel geometries need them only for views outside the flat class
     g->lay[0] = g->lay[1] = g->lay[2] = nullptr;
-    if (d.kind == SPL_CONE && dg.n_rays > 0) {
-        bool need[3] = {false, false, false};
-        for (int k = 0; k < d.n_views; ++k) need[g->views_host[k].lay] = true;
+    if (dg.n_rays > 0 && (d.kind != SPL_PARALLEL || dg.n_flat < dg.n_views)) {
         for (int L = 1; L < 3; ++L) {
-            if (!need[L]) continue;
             ce = cudaMalloc((void **)&g->lay[L], (size_t)nk * sizeof(float));
             if (ce != cudaSuccess) {
                 cudaGetLastError();

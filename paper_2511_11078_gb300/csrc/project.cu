@@ -57,6 +57,7 @@ struct FwdSink {
     {
         if (bx.holds(ld, la, lb)) acc[0] = fmaf(__ldg(c + (ld * S0 + la * S1 + lb * S2)), v, acc[0]);
     }
+    __device__ __forceinline__ float wscale() const { return 1.0f; }
     __device__ __forceinline__ void put(unsigned o, bool in, float v, int slot)
     {
         if (in) acc[slot & 3] = fmaf(__ldg(c + o), v, acc[slot & 3]);
@@ -87,6 +88,7 @@ struct CountSink {
     {
         n += (bx.holds(ld, la, lb) && v > 0.0f) ? 1u : 0u;
     }
+    __device__ __forceinline__ float wscale() const { return 1.0f; }
     __device__ __forceinline__ void put(unsigned, bool in, float v, int) { n += (in && v > 0.0f) ? 1u : 0u; }
     __device__ __forceinline__ void cell_end() {}
 };
@@ -141,20 +143,20 @@ struct AtomicSink {
             if (vec && (SX == 1u || SX == 0xffffffffu)) {
 #pragma unroll
                 for (int y = 0; y <= N; ++y)
-                    row4(base + (unsigned)y * SY, SX == 1u, yv * v[0][y], yv * v[1][y], yv * v[2][y], yv * v[3][y]);
+                    row4(base + (unsigned)y * SY, SX == 1u, v[0][y], v[1][y], v[2][y], v[3][y]);
                 return;
             }
             if (vec && (SY == 1u || SY == 0xffffffffu)) {
 #pragma unroll
                 for (int x = 0; x <= N; ++x)
-                    row4(base + (unsigned)x * SX, SY == 1u, yv * v[x][0], yv * v[x][1], yv * v[x][2], yv * v[x][3]);
+                    row4(base + (unsigned)x * SX, SY == 1u, v[x][0], v[x][1], v[x][2], v[x][3]);
                 return;
             }
         }
 #pragma unroll
         for (int x = 0; x <= N; ++x)
 #pragma unroll
-            for (int y = 0; y <= N; ++y) atomicAdd(c + (base + (unsigned)x * SX + (unsigned)y * SY), yv * v[x][y]);
+            for (int y = 0; y <= N; ++y) atomicAdd(c + (base + (unsigned)x * SX + (unsigned)y * SY), v[x][y]);
     }
     __device__ __forceinline__ void piece() {}
     __device__ __forceinline__ bool relevant(int d0, int d1, int a0, int a1, int b0, int b1) const
@@ -165,9 +167,12 @@ struct AtomicSink {
     {
         if (bx.holds(ld, la, lb)) atomicAdd(c + (ld * S0 + la * S1 + lb * S2), yv * v);
     }
+    // the piece march scales its Gauss weights by y_r (wscale), so the
+    // window values that reach put and put_face already carry the factor
+    __device__ __forceinline__ float wscale() const { return yv; }
     __device__ __forceinline__ void put(unsigned o, bool in, float v, int)
     {
-        if (in) atomicAdd(c + o, yv * v);
+        if (in) atomicAdd(c + o, v);
     }
     __device__ __forceinline__ void cell_end() {}
 };
@@ -191,6 +196,7 @@ struct BrickSink {
     {
         if (bx.holds(ld, la, lb)) atomicAdd(part + (unsigned)(ld * S0 + la * S1 + lb * S2 + (int)off), yv * v);
     }
+    __device__ __forceinline__ float wscale() const { return 1.0f; }
     __device__ __forceinline__ void put(unsigned o, bool in, float v, int)
     {
         if (in) atomicAdd(part + o, yv * v);
@@ -391,10 +397,40 @@ __device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float 
     if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
 }
 
-// rays r0 .. r1-1
+// The copy of c a scatter ray reduces into: the one whose contiguous axis
+// is the ray's b axis (its smallest direction component), c itself (x
+// fast), c1 = [z][x][y] (y fast) or c2 = [y][x][z] (z fast); rs.S is
+// re-pointed at that layout.  The faces that leave the window on d and a
+// events (all but the rare b events) then contain rows along b and go out
+// as 16-byte vector reductions, and the lanes of a warp, whose rays lie
+// side by side, reduce into neighbouring addresses.  The copies are folded
+// into c after the launch (k_fold_transpose).
+__device__ __forceinline__ float *b_fast_target(const DevGeom &g, RaySetup &rs, float *c, float *c1, float *c2)
+{
+    if (rs.ax[2] == 0) return c;
+    int st[3];
+    float *t;
+    if (rs.ax[2] == 1) {
+        st[0] = g.n[1];
+        st[1] = 1;
+        st[2] = g.n[0] * g.n[1];
+        t = c1;
+    } else {
+        st[0] = g.n[2];
+        st[1] = g.n[0] * g.n[2];
+        st[2] = 1;
+        t = c2;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) rs.S[q] = rs.sg[q] * st[rs.ax[q]];
+    return t;
+}
+
+// rays r0 .. r1-1 (into the b-fast copies of c)
 template <int N>
 __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__restrict__ y, float *__restrict__ c,
-                                                      QuadRule qr, long long r0, long long r1)
+                                                      float *__restrict__ c1, float *__restrict__ c2, QuadRule qr,
+                                                      long long r0, long long r1)
 {
     const long long r = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= r1) return;
@@ -403,15 +439,13 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
     double s[3], w[3];
     explicit_ray(g, r, s, w);
     RaySetup rs;
-    if (ray_setup<N>(grid_of(g), s, w, rs)) scatter_ray<N, VM_RAYS>(rs, yr, c, qr, g.err, ncoef_of(g));
+    if (!ray_setup<N>(grid_of(g), s, w, rs)) return;
+    float *t = b_fast_target(g, rs, c, c1, c2);
+    scatter_ray<N, VM_RAYS>(rs, yr, t, qr, g.err, ncoef_of(g));
 }
 
 // view geometries, scatter form: the forward's thread mapping, float
-// atomics; views v0 + blockIdx.z.  A view reduces into the target of its
-// layout (ViewPose::lay): c itself (x fast), c1 = [z][x][y] (y fast) or
-// c2 = [y][x][z] (z fast), so that the lanes of a warp, whose rays lie
-// side by side along det_u, reduce into neighbouring addresses; the
-// targets are folded into c after the launch (k_fold_transpose).
+// atomics into the b-fast copies of c; views v0 + blockIdx.z
 template <int N>
 __global__ void __launch_bounds__(128, 3)
     k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, float *__restrict__ c1,
@@ -423,21 +457,10 @@ __global__ void __launch_bounds__(128, 3)
     if (iu >= g.nu || iv >= g.nv) return;
     const float yr = __ldg(y + ((long long)k * g.nv + iv) * g.nu + iu);
     if (yr == 0.0f) return;
-    const int L = g.views[k].lay;
-    GridBox gb = grid_of(g);
-    float *t = c;
-    if (L == 1) {
-        gb.stride[0] = g.n[1];
-        gb.stride[1] = 1;
-        t = c1;
-    } else if (L == 2) {
-        gb.stride[0] = g.n[2];
-        gb.stride[1] = g.n[0] * g.n[2];
-        gb.stride[2] = 1;
-        t = c2;
-    }
     RaySetup rs;
-    if (view_setup<N>(g, gb, k, iu, iv, rs)) scatter_ray<N, VM_CONE>(rs, yr, t, qr, g.err, ncoef_of(g));
+    if (!view_setup<N>(g, grid_of(g), k, iu, iv, rs)) return;
+    float *t = b_fast_target(g, rs, c, c1, c2);
+    scatter_ray<N, VM_CONE>(rs, yr, t, qr, g.err, ncoef_of(g));
 }
 
 // out[s][r][q] += in[s][q][r] for slabs s of a Q x R row-major array: the
@@ -465,10 +488,13 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// parallel views of one class; the general class (piece march) reduces
+// into the view's b-fast copy of c (ViewConst::lay, Sb), the flat class
+// (cell march, scalar reductions) into c
 template <int N, int VM>
 __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
-    k_adjoint_pviews_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, QuadRule qr,
-                             const __grid_constant__ ViewChunk vc)
+    k_adjoint_pviews_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, float *__restrict__ c1,
+                             float *__restrict__ c2, QuadRule qr, const __grid_constant__ ViewChunk vc)
 {
     int iu, iv;
     tile_pixel(iu, iv);
@@ -480,7 +506,15 @@ __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
     RaySetup rs;
     if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) {
         use_view_const(V, rs);
-        scatter_ray<N, VM>(rs, yr, c, qr, g.err, ncoef_of(g));
+        float *t = c;
+        if constexpr (VM == VM_GENERAL) {
+            if (V.lay != 0) {
+                t = V.lay == 1 ? c1 : c2;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) rs.S[q] = V.Sb[q];
+            }
+        }
+        scatter_ray<N, VM>(rs, yr, t, qr, g.err, ncoef_of(g));
     }
 }
 
@@ -863,11 +897,31 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
         // it enters the total first
         if (v0 > 0 && !overlap) end_batch();
     }
+    // the b-fast copies of c (see b_fast_target): cleared before and folded
+    // into c after each launch that reduces into them
+    const long long nx = dg.n[0], ny = dg.n[1], nz = dg.n[2];
+    auto lay_clear = [&]() -> spl_status {
+        spl_status e = SPL_OK;
+        for (int L = 1; L < 3 && e == SPL_OK; ++L)
+            if (g->lay[L]) e = cuda_check(cudaMemsetAsync(g->lay[L], 0, nc * sizeof(float), st), "adjoint layout clear");
+        return e;
+    };
+    auto lay_fold = [&]() {
+        if (g->lay[1])
+            k_fold_transpose<<<dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 31) / 32),
+                                    (unsigned)(nz < 65535 ? nz : 65535)),
+                               256, 0, st>>>(c, g->lay[1], nx, ny, nz);
+        if (g->lay[2])
+            k_fold_transpose<<<dim3((unsigned)((nx * ny + 31) / 32), (unsigned)((nz + 31) / 32), 1), 256, 0, st>>>(
+                c, g->lay[2], nx * ny, nz, 1);
+    };
     if (dg.kind == SPL_RAYS) {
         for (long long r0 = 0; r0 < dg.n_rays; r0 += kAdjBatchRays) {
             const long long r1 = r0 + kAdjBatchRays < dg.n_rays ? r0 + kAdjBatchRays : dg.n_rays;
-            if ((s = begin_batch()) != SPL_OK) return s;
-            k_adjoint_rays<N><<<(unsigned)((r1 - r0 + 127) / 128), 128, 0, st>>>(dg, y, c, qr, r0, r1);
+            if ((s = begin_batch()) != SPL_OK || (s = lay_clear()) != SPL_OK) return s;
+            k_adjoint_rays<N><<<(unsigned)((r1 - r0 + 127) / 128), 128, 0, st>>>(dg, y, c, g->lay[1], g->lay[2], qr,
+                                                                                  r0, r1);
+            lay_fold();
             end_batch();
         }
         if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);
@@ -879,12 +933,15 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
         if (dg.kind == SPL_PARALLEL) {
             for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
                 if (s == SPL_OK) s = begin_batch();
-                k_adjoint_pviews_scatter<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
+                k_adjoint_pviews_scatter<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, nullptr, nullptr, qr, ch);
                 end_batch();
             }, per);
             for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
                 if (s == SPL_OK) s = begin_batch();
-                k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, qr, ch);
+                if (s == SPL_OK) s = lay_clear();
+                k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, g->lay[1], g->lay[2],
+                                                                                       qr, ch);
+                lay_fold();
                 end_batch();
             }, per);
             if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);
@@ -896,24 +953,11 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
             if (s != SPL_OK) return s;
         } else {
             const int per_launch = batched ? kAdjBatchViews : dg.n_views;
-            const long long nx = dg.n[0], ny = dg.n[1], nz = dg.n[2];
             for (int k0 = 0; k0 < dg.n_views; k0 += per_launch) {
                 const int nview = dg.n_views - k0 < per_launch ? dg.n_views - k0 : per_launch;
-                if ((s = begin_batch()) != SPL_OK) return s;
-                bool used[3] = {false, false, false};
-                for (int k = k0; k < k0 + nview; ++k) used[g->views_host[k].lay] = true;
-                for (int L = 1; L < 3; ++L)
-                    if (used[L] && (s = cuda_check(cudaMemsetAsync(g->lay[L], 0, nc * sizeof(float), st),
-                                                   "adjoint layout clear")) != SPL_OK)
-                        return s;
+                if ((s = begin_batch()) != SPL_OK || (s = lay_clear()) != SPL_OK) return s;
                 k_adjoint_views_scatter<N><<<dim3(gx, gy, nview), 128, 0, st>>>(dg, y, c, g->lay[1], g->lay[2], qr, k0);
-                if (used[1])
-                    k_fold_transpose<<<dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 31) / 32),
-                                            (unsigned)(nz < 65535 ? nz : 65535)),
-                                       256, 0, st>>>(c, g->lay[1], nx, ny, nz);
-                if (used[2])
-                    k_fold_transpose<<<dim3((unsigned)((nx * ny + 31) / 32), (unsigned)((nz + 31) / 32), 1), 256, 0,
-                                       st>>>(c, g->lay[2], nx * ny, nz, 1);
+                lay_fold();
                 end_batch();
             }
             if (batched) k_acc_store<<<stream_grid(nc), 256, 0, st>>>(nc, g->acc64, c);

@@ -25,6 +25,7 @@ struct PointSink {
             return n == 0 && d0 == 0 && a0 == 0 && b0 == 0;
         }
     } bx;
+    __device__ __forceinline__ float wscale() const { return 1.0f; }
     __device__ __forceinline__ void put(unsigned, bool in, float val, int)
     {
         if (in) v = val;

@@ -22,8 +22,8 @@ struct spl_geometry {
     spl::ViewConst *vconst;       // parallel geometries: per-view constants in view_order order (host)
     spl::TableSet *table;         // footprint tables (SPL_FP_TABLE), built by spl_prepare, or NULL
     double *acc64;                // FP64 accumulator of the scatter adjoint's batches (nx*ny*nz), or NULL
-    float *lay[3];                // scatter adjoint targets in the y-fast [1] and z-fast [2] layouts
-                                  // (nx*ny*nz each, cone views whose lay selects them), or NULL; [0] unused
+    float *lay[3];                // cone geometries: the scatter adjoint's copies of c in the y-fast [1] and
+                                  // z-fast [2] layouts (nx*ny*nz floats each), else NULL; [0] unused
 };
 
 namespace spl {

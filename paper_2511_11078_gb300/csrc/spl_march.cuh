@@ -120,8 +120,12 @@ struct ViewConst {
     // footprint-table frame (e1, e2) of H_w in the mirrored (d, a, b) frame,
     // as double-float pairs: E1[q] = sg_q e1[ax_q]
     float E1h[3], E1l[3], E2h[3], E2l[3];
+    // the scatter adjoint's copy of c: the layout whose contiguous axis is
+    // b (0 x, 1 y, 2 z fast) and the strides of (d, a, b) in it
+    int lay;
+    int Sb[3];
 };
-constexpr int kViewChunk = 192;  // views per launch (23.25 KB of parameters)
+constexpr int kViewChunk = 192;  // views per launch (26.25 KB of parameters)
 struct ViewChunk {
     ViewConst v[kViewChunk];
 };
@@ -139,9 +143,13 @@ __host__ __device__ inline void view_const(const DirSetup &ds, int view, const i
     vc.rbh = ds.rbh;
     vc.rbl = ds.rbl;
     vc.view = view;
+    // b-fast layouts: x fast [z][y][x], y fast [z][x][y], z fast [y][x][z]
+    const int sb[3][3] = {{1, n[0], n[0] * n[1]}, {n[1], 1, n[0] * n[1]}, {n[2], n[0] * n[2], 1}};
+    vc.lay = ds.ax[2];
     for (int q = 0; q < 3; ++q) {
         const int e = ds.ax[q];
         vc.S[q] = ds.sg[q] * stride[e];
+        vc.Sb[q] = ds.sg[q] * sb[vc.lay][e];
         vc.lo[q] = ds.sg[q] > 0 ? 0 : -(n[e] - 1);
         vc.hi[q] = ds.sg[q] > 0 ? n[e] - 1 : 0;
     }
@@ -169,8 +177,6 @@ struct ViewPose {
     double ud[3], vd[3]; // dual axes: a = <P - dc, ud>, b = <P - dc, vd> for P on the plane
     DirSetup dir;        // parallel views: direction set-up shared by all rays of the view
     double e1[3], e2[3]; // parallel views: orthonormal frame of H_w of the footprint tables
-    int lay;             // cone views: array axis kept contiguous by the scatter adjoint's
-                         // target (the largest |det_u| component; see AdjLayout)
 };
 
 struct DevGeom {
@@ -826,7 +832,8 @@ __device__ __forceinline__ bool cell_march(const RaySetup &rs, int cf, int cl, c
 // and the sink has Sink::face, through one sink.put_face(base, SX, SY, F)
 // of the face's (N+1)^2 values at base + x SX + y SY -- and the window shifted
 // with selects along the event's axis.  Only the set-up of the next cell
-// is a branch.
+// is a branch.  The Gauss weights carry the factor sink.wscale() (1, or the
+// adjoint's y_r), so the values the sink receives already include it.
 template <int N, class Sink>
 __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, const QuadRule &qr, Sink &sink)
 {
@@ -859,7 +866,7 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
     while (true) {
         const float t1 = fminf(fminf(ta, tb), 1.0f);
         if (t1 > t0 && sink.relevant(c - N, c, QA - N, QA, QB - N, QB)) {
-            const float half = 0.5f * (t1 - t0), mid = 0.5f * (t0 + t1);
+            const float half = 0.5f * (t1 - t0), mid = 0.5f * (t0 + t1), hs = half * sink.wscale();
 #pragma unroll
             for (int q = 0; q < M; ++q) {
                 const float t = fmaf(half, qr.x[q], mid);
@@ -867,7 +874,7 @@ __device__ __forceinline__ bool piece_march(const RaySetup &rs, int cf, int cl, 
                 bweights<N>(t, wd);
                 bweights<N>(fmaf(rs.ra, t, ga), wa);
                 bweights<N>(fmaf(rs.rb, t, gb), wb);
-                const float cw = half * qr.w[q];
+                const float cw = hs * qr.w[q];
 #pragma unroll
                 for (int d = 0; d <= N; ++d) wd[d] *= cw;
                 window_update<N>(acc, wd, wa, wb);
