@@ -73,8 +73,23 @@ FLOP_PER_FLAT_NODE = {0: 8, 1: 17, 2: 40, 3: 71}
 MLP_FLOP_PER_PAIR = 2 * (5 * 64 + 2 * 64 * 64 + 64)
 FLOP_PER_PAIR = 2
 NODES_PER_PIECE = {0: 1, 1: 2, 2: 4, 3: 5}
-# ours: A, two dot kernels, x/r update, A^T, two dot kernels, p update
-LAUNCHES_PER_CG_STEP_CONE = 8
+# views per batch of the scatter adjoint (FP32 atomics within a batch, FP64
+# totals across batches when a geometry has more views than this)
+ADJ_BATCH_VIEWS = 48
+
+
+def launches_per_cg_step(n_views: int, scatter: bool = True) -> int:
+    """Kernels of the library launched by one CGLS iteration on a cone
+    geometry of n_views views: A (one launch), two FP64 dots (two kernels
+    each), the x/r and p updates, and A^T: per batch of 48 views the scatter
+    and the folds of its two layout copies, plus the batch's FP64 total
+    (and the final rounding) when there is more than one batch; the brick
+    gather is one launch."""
+    if not scatter:
+        return 1 + 4 + 2 + 1
+    batched = n_views > ADJ_BATCH_VIEWS
+    batches = -(-n_views // ADJ_BATCH_VIEWS) if batched else 1
+    return 1 + 4 + 2 + batches * (3 + (1 if batched else 0)) + (1 if batched else 0)
 
 
 def parse():
@@ -723,7 +738,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
                     "what": "the CGLS iteration with x, r, p in pinned host memory: uploaded before and "
                             "downloaded (with gamma) after every step", "finite": e2e_ok},
-            "gpu_launches": args.steps * LAUNCHES_PER_CG_STEP_CONE,
+            "gpu_launches": args.steps * launches_per_cg_step(ops.v1 - ops.v0, args.adjoint == "scatter"),
             "clocks": clocks,
             "roofline": roofline,
             "fp32_probe": peak,

@@ -160,10 +160,11 @@ typedef struct {
  * owns a CUDA stream and two events on which spl_forward / spl_adjoint run
  * the plane path beside the march of the other views (the caller's stream
  * waits for it, so each call stays one ordered operation on that stream).
- * Scratch of the scatter adjoint, allocated here: two copies of the
- * coefficient array (2 x 4 nx ny nz bytes; not for a parallel geometry
- * whose views are all in the flat class) and, for more than 48 views or
- * 2^22 explicit rays, an FP64 accumulator (8 nx ny nz bytes).
+ * Scratch of the scatter adjoint, allocated here: the coefficient array in
+ * three layouts (x, y and z fast) of four shifted copies each (about
+ * 48 nx ny nz bytes; not for a parallel geometry whose views are all in the
+ * flat class) and, for more than 48 views or 2^22 explicit rays, an FP64
+ * accumulator (8 nx ny nz bytes).
  * Uses the current CUDA device.
  * Errors: SPL_ERR_ARG, SPL_ERR_NONFINITE, SPL_ERR_UNSUPPORTED, SPL_ERR_OOM,
  * SPL_ERR_CUDA; *out is NULL on error. */
@@ -244,9 +245,9 @@ spl_status spl_forward(const spl_geometry *g, const spl_basis_desc *basis, const
  * ray-driven scatter with float atomics (the default) or a gather over
  * coefficient bricks that loops over views and the detector window of the
  * brick (no global atomics); explicit rays always scatter.  The scatter
- * reduces each ray into the geometry's copy of c whose contiguous axis is
- * the ray's smallest direction component and folds the copies into c_dev
- * (so two calls on one geometry must not overlap on the GPU).  Slice-separable
+ * reduces each ray into the geometry's layout of c whose contiguous axis
+ * is the ray's smallest direction component and folds the layouts into
+ * c_dev (so two calls on one geometry must not overlap on the GPU).  Slice-separable
  * views of a parallel geometry are gathered through the transposed plane
  * matrix (no atomics; see spl_prepare) and the other views added to them.
  *   y_dev: n_rays float32 (read only);  c_dev: [nz][ny][nx] float32,

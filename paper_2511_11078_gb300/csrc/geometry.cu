@@ -494,25 +494,29 @@ extern "C" spl_status spl_make_geometry(const spl_geometry_desc *desc, spl_geome
             return fail(SPL_ERR_OOM, "cudaMalloc of the adjoint accumulator (%lld doubles) failed", nk);
         }
     }
-    // the scatter adjoint reduces each piece-marched ray into the copy of c
-    // whose contiguous axis is the ray's b axis: the y-fast and z-fast
-    // copies are scratch of the geometry (folded into c after each batch);
-    // parallel geometries need them only for views outside the flat class
+    // the scatter adjoint reduces each piece-marched ray into the layout of
+    // c whose contiguous axis is the ray's b axis, kept as four copies
+    // shifted by 0..3 floats (copy stride lay_cs, a multiple of 4 that
+    // holds nk + 3 floats): scratch of the geometry, folded into c after
+    // each batch; parallel geometries need it only for views outside the
+    // flat class
     g->lay[0] = g->lay[1] = g->lay[2] = nullptr;
+    g->dev.lay_cs = ((size_t)nk + 6) & ~(size_t)3;
     if (dg.n_rays > 0 && (d.kind != SPL_PARALLEL || dg.n_flat < dg.n_views)) {
-        for (int L = 1; L < 3; ++L) {
-            ce = cudaMalloc((void **)&g->lay[L], (size_t)nk * sizeof(float));
+        for (int L = 0; L < 3; ++L) {
+            ce = cudaMalloc((void **)&g->lay[L], 4 * g->dev.lay_cs * sizeof(float));
+            if (ce == cudaSuccess) ce = cudaMemset(g->lay[L], 0, 4 * g->dev.lay_cs * sizeof(float));
             if (ce != cudaSuccess) {
                 cudaGetLastError();
-                g->lay[L] = nullptr;
-                if (g->lay[1]) cudaFree(g->lay[1]);
+                for (int M = 0; M <= L; ++M)
+                    if (g->lay[M]) cudaFree(g->lay[M]);
                 if (g->acc64) cudaFree(g->acc64);
                 cudaFree(blk);
                 plane_free(g->plane);
                 free(g->vconst);
                 free(g->views_host);
                 free(g);
-                return fail(SPL_ERR_OOM, "cudaMalloc of the adjoint's layout target (%lld floats) failed", nk);
+                return fail(SPL_ERR_OOM, "cudaMalloc of the adjoint's layout copies (4 x %lld floats) failed", nk);
             }
         }
     }
@@ -527,7 +531,7 @@ extern "C" void spl_destroy_geometry(spl_geometry *g)
     table_free(g->table);
     free(g->vconst);
     if (g->acc64) cudaFree(g->acc64);
-    for (int L = 1; L < 3; ++L)
+    for (int L = 0; L < 3; ++L)
         if (g->lay[L]) cudaFree(g->lay[L]);
     if (g->dev_block) cudaFree(g->dev_block);
     free(g->views_host);

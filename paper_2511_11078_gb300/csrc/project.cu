@@ -94,59 +94,45 @@ struct CountSink {
 };
 
 // adjoint, scatter: y_r / |w_d| * F_l added to c_l with a float atomic.
-// A face whose rows run along the x axis (unit stride) is added with 16-byte
-// vector atomics instead: a row of N+1 = 4 consecutive floats spans at most
-// two aligned groups of 4, each added with one atomic whose other entries
-// are zero (adding +0 leaves them unchanged).  That halves the L2 requests
-// of such faces (the adjoint's bound); vec is false when c is not 16-byte
-// aligned, and a row whose second group would pass the array's end (n
-// floats) is added entry by entry.
+// The target of a piece-marched ray is a set of four shifted copies of a
+// layout of c (copy j holds coefficient i at position j * cs + i + j, cs a
+// multiple of 4): a face row of N+1 = 4 consecutive floats starting at
+// index lo goes, as one 16-byte vector atomic, to the copy j = -lo mod 4 in
+// which it starts a 16-byte group.  Faces without such a row, the cell
+// march's flushes and the last window take scalar atomics into copy 0.
+// The copies are summed into c afterwards (k_fold_copies*).
 struct AtomicSink {
     static constexpr bool plane = false;
     static constexpr bool face = true;
-    float *__restrict__ c;
+    float *__restrict__ c;  // copy 0 (or c itself where no vector row is written)
+    size_t cs;              // copy stride in floats
     int S0, S1, S2;
     unsigned off;
     SinkBox bx;
     float yv;
-    bool vec;
-    unsigned n;
     // w0..w3 (already scaled) at p, p + s, p + 2 s, p + 3 s, s = +-1
     __device__ __forceinline__ void row4(unsigned p, bool up, float w0, float w1, float w2, float w3)
     {
         const unsigned lo = up ? p : p - 3u;
-        const float a0 = up ? w0 : w3, a1 = up ? w1 : w2, a2 = up ? w2 : w1, a3 = up ? w3 : w0;
-        const unsigned g = lo & ~3u, k = lo & 3u;
-        if (g + 8u > n) {
-            atomicAdd(c + lo, a0);
-            atomicAdd(c + lo + 1u, a1);
-            atomicAdd(c + lo + 2u, a2);
-            atomicAdd(c + lo + 3u, a3);
-            return;
-        }
-        float4 f, h;
-        f.x = k == 0u ? a0 : 0.0f;
-        f.y = k == 0u ? a1 : (k == 1u ? a0 : 0.0f);
-        f.z = k == 0u ? a2 : (k == 1u ? a1 : (k == 2u ? a0 : 0.0f));
-        f.w = k == 0u ? a3 : (k == 1u ? a2 : (k == 2u ? a1 : a0));
-        h.x = k == 1u ? a3 : (k == 2u ? a2 : a1);
-        h.y = k == 2u ? a3 : (k == 3u ? a2 : 0.0f);
-        h.z = k == 3u ? a3 : 0.0f;
-        h.w = 0.0f;
-        atomicAdd(reinterpret_cast<float4 *>(c + g), f);
-        if (k != 0u) atomicAdd(reinterpret_cast<float4 *>(c + g + 4u), h);
+        const unsigned j = (0u - lo) & 3u;
+        float4 f;
+        f.x = up ? w0 : w3;
+        f.y = up ? w1 : w2;
+        f.z = up ? w2 : w1;
+        f.w = up ? w3 : w0;
+        atomicAdd(reinterpret_cast<float4 *>(c + ((size_t)j * cs + (size_t)(lo + j))), f);
     }
     template <int N>
     __device__ __forceinline__ void put_face(unsigned base, unsigned SX, unsigned SY, const float (&v)[N + 1][N + 1])
     {
         if constexpr (N == 3) {
-            if (vec && (SX == 1u || SX == 0xffffffffu)) {
+            if (SX == 1u || SX == 0xffffffffu) {
 #pragma unroll
                 for (int y = 0; y <= N; ++y)
                     row4(base + (unsigned)y * SY, SX == 1u, v[0][y], v[1][y], v[2][y], v[3][y]);
                 return;
             }
-            if (vec && (SY == 1u || SY == 0xffffffffu)) {
+            if (SY == 1u || SY == 0xffffffffu) {
 #pragma unroll
                 for (int x = 0; x <= N; ++x)
                     row4(base + (unsigned)x * SX, SY == 1u, v[x][0], v[x][1], v[x][2], v[x][3]);
@@ -378,58 +364,57 @@ __global__ void __launch_bounds__(128) k_count_rays(DevGeom g, unsigned long lon
 }
 
 // ---------------------------------------------------------------- adjoint: ray-driven scatter
-__device__ __forceinline__ unsigned ncoef_of(const DevGeom &g) { return (unsigned)(g.n[0] * g.n[1] * g.n[2]); }
 
 template <int N, int VM>
-__device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float *__restrict__ c, const QuadRule &qr,
-                                            int *err, unsigned ncoef)
+__device__ __forceinline__ void scatter_ray(const RaySetup &rs, float yr, float *__restrict__ c, size_t cs,
+                                            const QuadRule &qr, int *err)
 {
     AtomicSink sk;
     sk.c = c;
+    sk.cs = cs;
     sk.S0 = rs.S[0];
     sk.S1 = rs.S[1];
     sk.S2 = rs.S[2];
     sk.off = 0u;
     sk.bx = make_box(rs.lo, rs.hi);
     sk.yv = yr * rs.inv_wd;
-    sk.vec = ((size_t)c & 15u) == 0u;
-    sk.n = ncoef;
     if (!march_vm<N, VM>(rs, rs.c0, rs.c1, qr, sk)) atomicOr(err, 1);
 }
 
-// The copy of c a scatter ray reduces into: the one whose contiguous axis
-// is the ray's b axis (its smallest direction component), c itself (x
-// fast), c1 = [z][x][y] (y fast) or c2 = [y][x][z] (z fast); rs.S is
-// re-pointed at that layout.  The faces that leave the window on d and a
-// events (all but the rare b events) then contain rows along b and go out
-// as 16-byte vector reductions, and the lanes of a warp, whose rays lie
-// side by side, reduce into neighbouring addresses.  The copies are folded
-// into c after the launch (k_fold_transpose).
-__device__ __forceinline__ float *b_fast_target(const DevGeom &g, RaySetup &rs, float *c, float *c1, float *c2)
+// The layout a piece-marched scatter ray reduces into: the one whose
+// contiguous axis is the ray's b axis (its smallest direction component),
+// l0 = [z][y][x] (x fast), l1 = [z][x][y] (y fast) or l2 = [y][x][z] (z
+// fast), each as four shifted copies (AtomicSink); rs.S is re-pointed at
+// that layout.  The faces that leave the window on d and a events (all but
+// the rare b events) then contain rows along b and go out as one 16-byte
+// vector atomic per row, and the lanes of a warp, whose rays lie side by
+// side, reduce into neighbouring addresses.  The copies are folded into c
+// after the launch.
+__device__ __forceinline__ float *b_fast_target(const DevGeom &g, RaySetup &rs, float *l0, float *l1, float *l2)
 {
-    if (rs.ax[2] == 0) return c;
+    if (rs.ax[2] == 0) return l0;
     int st[3];
     float *t;
     if (rs.ax[2] == 1) {
         st[0] = g.n[1];
         st[1] = 1;
         st[2] = g.n[0] * g.n[1];
-        t = c1;
+        t = l1;
     } else {
         st[0] = g.n[2];
         st[1] = g.n[0] * g.n[2];
         st[2] = 1;
-        t = c2;
+        t = l2;
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) rs.S[q] = rs.sg[q] * st[rs.ax[q]];
     return t;
 }
 
-// rays r0 .. r1-1 (into the b-fast copies of c)
+// rays r0 .. r1-1
 template <int N>
-__global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__restrict__ y, float *__restrict__ c,
-                                                      float *__restrict__ c1, float *__restrict__ c2, QuadRule qr,
+__global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__restrict__ y, float *__restrict__ l0,
+                                                      float *__restrict__ l1, float *__restrict__ l2, QuadRule qr,
                                                       long long r0, long long r1)
 {
     const long long r = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -440,16 +425,16 @@ __global__ void __launch_bounds__(128) k_adjoint_rays(DevGeom g, const float *__
     explicit_ray(g, r, s, w);
     RaySetup rs;
     if (!ray_setup<N>(grid_of(g), s, w, rs)) return;
-    float *t = b_fast_target(g, rs, c, c1, c2);
-    scatter_ray<N, VM_RAYS>(rs, yr, t, qr, g.err, ncoef_of(g));
+    float *t = b_fast_target(g, rs, l0, l1, l2);
+    scatter_ray<N, VM_RAYS>(rs, yr, t, g.lay_cs, qr, g.err);
 }
 
-// view geometries, scatter form: the forward's thread mapping, float
-// atomics into the b-fast copies of c; views v0 + blockIdx.z
+// view geometries, scatter form: the forward's thread mapping; views
+// v0 + blockIdx.z
 template <int N>
 __global__ void __launch_bounds__(128, 3)
-    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, float *__restrict__ c1,
-                            float *__restrict__ c2, QuadRule qr, int v0)
+    k_adjoint_views_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ l0, float *__restrict__ l1,
+                            float *__restrict__ l2, QuadRule qr, int v0)
 {
     int iu, iv;
     tile_pixel(iu, iv);
@@ -459,42 +444,56 @@ __global__ void __launch_bounds__(128, 3)
     if (yr == 0.0f) return;
     RaySetup rs;
     if (!view_setup<N>(g, grid_of(g), k, iu, iv, rs)) return;
-    float *t = b_fast_target(g, rs, c, c1, c2);
-    scatter_ray<N, VM_CONE>(rs, yr, t, qr, g.err, ncoef_of(g));
+    float *t = b_fast_target(g, rs, l0, l1, l2);
+    scatter_ray<N, VM_CONE>(rs, yr, t, g.lay_cs, qr, g.err);
 }
 
-// out[s][r][q] += in[s][q][r] for slabs s of a Q x R row-major array: the
-// fold of a layout target into c.  y fast: slabs z, Q = nx, R = ny; z fast:
-// one slab, Q = nx ny, R = nz.  32 x 32 tiles through shared memory, both
-// sides coalesced.
-__global__ void __launch_bounds__(256)
-    k_fold_transpose(float *__restrict__ out, const float *__restrict__ in, long long Q, long long R, long long slabs)
+// c[i] += sum_j l0[j cs + i + j]: the fold of the x-fast copies into c
+__global__ void k_fold_copies(float *__restrict__ c, const float *__restrict__ in, long long n, long long cs)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        c[i] += (in[i] + in[cs + i + 1]) + (in[2 * cs + i + 2] + in[3 * cs + i + 3]);
+}
+
+// out[s][r][q] += sum_j in[j cs + (s Q + q) R + r + j]: the fold of the
+// shifted copies of a Q x R row-major layout into c, slab by slab.  y fast:
+// slabs z, Q = nx, R = ny; z fast: one slab, Q = nx ny, R = nz.  32 x 32
+// tiles through shared memory, both sides coalesced.
+__global__ void __launch_bounds__(256) k_fold_copies_transpose(float *__restrict__ out, const float *__restrict__ in,
+                                                               long long Q, long long R, long long slabs, long long cs)
 {
     __shared__ float t[32][33];
     const long long q0 = (long long)blockIdx.x * 32, r0 = (long long)blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (long long sl = blockIdx.z; sl < slabs; sl += gridDim.z) {
-        const size_t base = (size_t)sl * (size_t)Q * (size_t)R;
+        const long long base = sl * Q * R;
         for (int j = ty; j < 32; j += 8) {
             const long long q = q0 + j, r = r0 + tx;
-            t[j][tx] = (q < Q && r < R) ? in[base + (size_t)q * R + r] : 0.0f;
+            float v = 0.0f;
+            if (q < Q && r < R) {
+                const long long i = base + q * R + r;
+                v = (in[i] + in[cs + i + 1]) + (in[2 * cs + i + 2] + in[3 * cs + i + 3]);
+            }
+            t[j][tx] = v;
         }
         __syncthreads();
         for (int j = ty; j < 32; j += 8) {
             const long long r = r0 + j, q = q0 + tx;
-            if (q < Q && r < R) out[base + (size_t)r * Q + q] += t[tx][j];
+            if (q < Q && r < R) out[base + r * Q + q] += t[tx][j];
         }
         __syncthreads();
     }
 }
 
 // parallel views of one class; the general class (piece march) reduces
-// into the view's b-fast copy of c (ViewConst::lay, Sb), the flat class
-// (cell march, scalar reductions) into c
+// into the view's b-fast layout (ViewConst::lay, Sb), the flat class (cell
+// march, scalar atomics) into c
 template <int N, int VM>
 __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
-    k_adjoint_pviews_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, float *__restrict__ c1,
-                             float *__restrict__ c2, QuadRule qr, const __grid_constant__ ViewChunk vc)
+    k_adjoint_pviews_scatter(DevGeom g, const float *__restrict__ y, float *__restrict__ c, float *__restrict__ l0,
+                             float *__restrict__ l1, float *__restrict__ l2, QuadRule qr,
+                             const __grid_constant__ ViewChunk vc)
 {
     int iu, iv;
     tile_pixel(iu, iv);
@@ -506,15 +505,14 @@ __global__ void __launch_bounds__(128, ViewBlocks<VM>::value)
     RaySetup rs;
     if (view_setup<N>(g, grid_of(g), k, iu, iv, rs)) {
         use_view_const(V, rs);
-        float *t = c;
         if constexpr (VM == VM_GENERAL) {
-            if (V.lay != 0) {
-                t = V.lay == 1 ? c1 : c2;
+            float *t = V.lay == 0 ? l0 : (V.lay == 1 ? l1 : l2);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) rs.S[q] = V.Sb[q];
-            }
+            for (int q = 0; q < 3; ++q) rs.S[q] = V.Sb[q];
+            scatter_ray<N, VM>(rs, yr, t, g.lay_cs, qr, g.err);
+        } else {
+            scatter_ray<N, VM>(rs, yr, c, 0, qr, g.err);
         }
-        scatter_ray<N, VM>(rs, yr, t, qr, g.err, ncoef_of(g));
     }
 }
 
@@ -897,30 +895,30 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
         // it enters the total first
         if (v0 > 0 && !overlap) end_batch();
     }
-    // the b-fast copies of c (see b_fast_target): cleared before and folded
-    // into c after each launch that reduces into them
-    const long long nx = dg.n[0], ny = dg.n[1], nz = dg.n[2];
+    // the b-fast layouts (see b_fast_target), four shifted copies each:
+    // cleared before and folded into c after each launch that reduces into
+    // them
+    const long long nx = dg.n[0], ny = dg.n[1], nz = dg.n[2], cs = (long long)dg.lay_cs;
     auto lay_clear = [&]() -> spl_status {
         spl_status e = SPL_OK;
-        for (int L = 1; L < 3 && e == SPL_OK; ++L)
-            if (g->lay[L]) e = cuda_check(cudaMemsetAsync(g->lay[L], 0, nc * sizeof(float), st), "adjoint layout clear");
+        for (int L = 0; L < 3 && e == SPL_OK; ++L)
+            e = cuda_check(cudaMemsetAsync(g->lay[L], 0, 4 * dg.lay_cs * sizeof(float), st), "adjoint layout clear");
         return e;
     };
     auto lay_fold = [&]() {
-        if (g->lay[1])
-            k_fold_transpose<<<dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 31) / 32),
-                                    (unsigned)(nz < 65535 ? nz : 65535)),
-                               256, 0, st>>>(c, g->lay[1], nx, ny, nz);
-        if (g->lay[2])
-            k_fold_transpose<<<dim3((unsigned)((nx * ny + 31) / 32), (unsigned)((nz + 31) / 32), 1), 256, 0, st>>>(
-                c, g->lay[2], nx * ny, nz, 1);
+        k_fold_copies<<<stream_grid(nc), 256, 0, st>>>(c, g->lay[0], nc, cs);
+        k_fold_copies_transpose<<<dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + 31) / 32),
+                                       (unsigned)(nz < 65535 ? nz : 65535)),
+                                  256, 0, st>>>(c, g->lay[1], nx, ny, nz, cs);
+        k_fold_copies_transpose<<<dim3((unsigned)((nx * ny + 31) / 32), (unsigned)((nz + 31) / 32), 1), 256, 0, st>>>(
+            c, g->lay[2], nx * ny, nz, 1, cs);
     };
     if (dg.kind == SPL_RAYS) {
         for (long long r0 = 0; r0 < dg.n_rays; r0 += kAdjBatchRays) {
             const long long r1 = r0 + kAdjBatchRays < dg.n_rays ? r0 + kAdjBatchRays : dg.n_rays;
             if ((s = begin_batch()) != SPL_OK || (s = lay_clear()) != SPL_OK) return s;
-            k_adjoint_rays<N><<<(unsigned)((r1 - r0 + 127) / 128), 128, 0, st>>>(dg, y, c, g->lay[1], g->lay[2], qr,
-                                                                                  r0, r1);
+            k_adjoint_rays<N><<<(unsigned)((r1 - r0 + 127) / 128), 128, 0, st>>>(dg, y, g->lay[0], g->lay[1],
+                                                                                  g->lay[2], qr, r0, r1);
             lay_fold();
             end_batch();
         }
@@ -933,14 +931,15 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
         if (dg.kind == SPL_PARALLEL) {
             for_view_chunks(g, v0, dg.n_flat - v0, [&](const ViewChunk &ch, int n) {
                 if (s == SPL_OK) s = begin_batch();
-                k_adjoint_pviews_scatter<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, nullptr, nullptr, qr, ch);
+                k_adjoint_pviews_scatter<N, VM_FLAT><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, nullptr, nullptr,
+                                                                                    nullptr, qr, ch);
                 end_batch();
             }, per);
             for_view_chunks(g, dg.n_flat, dg.n_views - dg.n_flat, [&](const ViewChunk &ch, int n) {
                 if (s == SPL_OK) s = begin_batch();
                 if (s == SPL_OK) s = lay_clear();
-                k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, g->lay[1], g->lay[2],
-                                                                                       qr, ch);
+                k_adjoint_pviews_scatter<N, VM_GENERAL><<<dim3(gx, gy, n), 128, 0, st>>>(dg, y, c, g->lay[0], g->lay[1],
+                                                                                       g->lay[2], qr, ch);
                 lay_fold();
                 end_batch();
             }, per);
@@ -956,7 +955,8 @@ static spl_status adjoint_quad(const spl_geometry *g, const spl_basis_desc *b, c
             for (int k0 = 0; k0 < dg.n_views; k0 += per_launch) {
                 const int nview = dg.n_views - k0 < per_launch ? dg.n_views - k0 : per_launch;
                 if ((s = begin_batch()) != SPL_OK || (s = lay_clear()) != SPL_OK) return s;
-                k_adjoint_views_scatter<N><<<dim3(gx, gy, nview), 128, 0, st>>>(dg, y, c, g->lay[1], g->lay[2], qr, k0);
+                k_adjoint_views_scatter<N><<<dim3(gx, gy, nview), 128, 0, st>>>(dg, y, g->lay[0], g->lay[1], g->lay[2],
+                                                                                 qr, k0);
                 lay_fold();
                 end_batch();
             }

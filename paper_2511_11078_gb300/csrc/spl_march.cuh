@@ -196,6 +196,7 @@ struct DevGeom {
     // pair count rebuilds each ray from them
     const double *raw;
     int *err;            // device error flag (bit 0: a loop bound was reached)
+    size_t lay_cs;       // copy stride (floats) of the scatter adjoint's shifted layout copies
 };
 
 // ------------------------------------------------------------------ B-splines

@@ -105,3 +105,16 @@ def test_ncu_traffic_only_for_current_sources(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k_foo", "wl-a") == 1.5e9
     assert bench.ncu_traffic("k_foo", "wl-b") is None
     assert bench.ncu_traffic("k_bar", "wl-a") is None  # stale: another source hash
+
+
+def test_launch_count_follows_the_adjoint_batches():
+    """The claimed kernel launches per CGLS iteration: A, two dots of two
+    kernels, two updates, and A^T as scatter + two layout folds per batch of
+    48 views, with the FP64 batch totals and final rounding once batched."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.launches_per_cg_step(48) == 1 + 4 + 2 + 3
+    assert bench.launches_per_cg_step(49) == 1 + 4 + 2 + 2 * 4 + 1
+    assert bench.launches_per_cg_step(720) == 1 + 4 + 2 + 15 * 4 + 1
+    assert bench.launches_per_cg_step(720, scatter=False) == 8
