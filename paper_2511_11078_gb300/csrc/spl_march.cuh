@@ -561,6 +561,28 @@ __device__ __forceinline__ void window_update(float (&acc)[N + 1][N + 1][N + 1],
                                               const float (&wa)[N + 1], const float (&wb)[N + 1])
 {
     constexpr int K2 = (N + 1) / 2;
+    if constexpr (N == 3) {
+        // pairs (3, 0) and (1, 2): the register pairs bweights<3> produces
+        const float2 b30 = make_float2(wb[3], wb[0]), b12 = make_float2(wb[1], wb[2]);
+#pragma unroll
+        for (int i = 0; i <= N; ++i) {
+            const float2 a2 = make_float2(wa[i], wa[i]);
+            const float2 p30 = __fmul2_rn(a2, b30), p12 = __fmul2_rn(a2, b12);
+#pragma unroll
+            for (int d = 0; d <= N; ++d) {
+                const float2 w2 = make_float2(wd[d], wd[d]);
+                float2 u = make_float2(acc[d][i][3], acc[d][i][0]);
+                u = __ffma2_rn(w2, p30, u);
+                acc[d][i][3] = u.x;
+                acc[d][i][0] = u.y;
+                float2 v = make_float2(acc[d][i][1], acc[d][i][2]);
+                v = __ffma2_rn(w2, p12, v);
+                acc[d][i][1] = v.x;
+                acc[d][i][2] = v.y;
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i <= N; ++i) {
         float2 pk[K2 > 0 ? K2 : 1];
