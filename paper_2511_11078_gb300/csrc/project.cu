@@ -110,32 +110,34 @@ struct AtomicSink {
     unsigned off;
     SinkBox bx;
     float yv;
-    // w0..w3 (already scaled) at p, p + s, p + 2 s, p + 3 s, s = +-1
-    __device__ __forceinline__ void row4(unsigned p, bool up, float w0, float w1, float w2, float w3)
+    // w0..w3 (already scaled) at p, p + s, p + 2 s, p + 3 s with s = +1 (UP)
+    // or -1: one aligned 16-byte atomic into the copy where the run starts
+    // a group
+    template <bool UP>
+    __device__ __forceinline__ void row4(unsigned p, float w0, float w1, float w2, float w3)
     {
-        const unsigned lo = up ? p : p - 3u;
+        const unsigned lo = UP ? p : p - 3u;
         const unsigned j = (0u - lo) & 3u;
-        float4 f;
-        f.x = up ? w0 : w3;
-        f.y = up ? w1 : w2;
-        f.z = up ? w2 : w1;
-        f.w = up ? w3 : w0;
+        const float4 f = UP ? make_float4(w0, w1, w2, w3) : make_float4(w3, w2, w1, w0);
         atomicAdd(reinterpret_cast<float4 *>(c + ((size_t)j * cs + (size_t)(lo + j))), f);
     }
+    // the face's (N+1)^2 values at base + x SX + y SY.  In the layout of a
+    // piece-marched ray the b axis is contiguous (S2 = +-1), so the faces of
+    // d and a events (SY = S2) have rows along y; the faces of b events
+    // (SY = S1) take scalar atomics.  The sign of S2 is the ray's and
+    // mostly the warp's, so the two row directions are branches.
     template <int N>
     __device__ __forceinline__ void put_face(unsigned base, unsigned SX, unsigned SY, const float (&v)[N + 1][N + 1])
     {
         if constexpr (N == 3) {
-            if (SX == 1u || SX == 0xffffffffu) {
+            if (SY == 1u) {
 #pragma unroll
-                for (int y = 0; y <= N; ++y)
-                    row4(base + (unsigned)y * SY, SX == 1u, v[0][y], v[1][y], v[2][y], v[3][y]);
+                for (int x = 0; x <= N; ++x) row4<true>(base + (unsigned)x * SX, v[x][0], v[x][1], v[x][2], v[x][3]);
                 return;
             }
-            if (SY == 1u || SY == 0xffffffffu) {
+            if (SY == 0xffffffffu) {
 #pragma unroll
-                for (int x = 0; x <= N; ++x)
-                    row4(base + (unsigned)x * SX, SY == 1u, v[x][0], v[x][1], v[x][2], v[x][3]);
+                for (int x = 0; x <= N; ++x) row4<false>(base + (unsigned)x * SX, v[x][0], v[x][1], v[x][2], v[x][3]);
                 return;
             }
         }
