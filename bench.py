@@ -435,25 +435,43 @@ def oracle_leg(args, wl, geom, ops, c_true, dev):
 def e2e_leg(cg, steps, stream):
     """Each step uploads the CGLS state (x, r, p) from pinned host memory,
     runs the iteration through the library's entry points, and downloads the
-    updated x, r and p (and the FP64 scalar gamma)."""
+    updated x, r and p (and the FP64 scalar gamma).  p is needed by A at the
+    start and rewritten at the end, so its copies stand in the step; x and r
+    are first used after A (the x/r update) and final after it, so their
+    upload runs on a copy stream beside A and their download beside A^T."""
     import torch
-
-    from paper_2511_11078_gb300 import spl
 
     hx, hr, hp = (t.cpu().pin_memory() for t in (cg.x, cg.r, cg.p))
     hg = torch.zeros(1, dtype=torch.float64).pin_memory()
+    copy = torch.cuda.Stream()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        cg.x.copy_(hx, non_blocking=True)
-        cg.r.copy_(hr, non_blocking=True)
+        # x, r: the previous step is done with them (A^T read r)
+        copy.wait_stream(stream)
+        with torch.cuda.stream(copy):
+            cg.x.copy_(hx, non_blocking=True)
+            cg.r.copy_(hr, non_blocking=True)
+        up = torch.cuda.Event()
+        up.record(copy)
         cg.p.copy_(hp, non_blocking=True)
-        cg.step()
-        hx.copy_(cg.x, non_blocking=True)
-        hr.copy_(cg.r, non_blocking=True)
+
+        def mark(i):
+            if i == 1:  # after A, before the x/r update
+                stream.wait_event(up)
+            elif i == 2:  # x and r final for this step
+                done = torch.cuda.Event()
+                done.record(stream)
+                copy.wait_event(done)
+                with torch.cuda.stream(copy):
+                    hx.copy_(cg.x, non_blocking=True)
+                    hr.copy_(cg.r, non_blocking=True)
+
+        cg.step(mark)
         hp.copy_(cg.p, non_blocking=True)
         hg.copy_(cg.gamma, non_blocking=True)
+    stream.wait_stream(copy)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
@@ -736,8 +754,9 @@ def run_ours(args):
             "A_gcontrib_s": pairs / (fwd * 1e-3) / 1e9, "AT_gcontrib_s": pairs / (adj * 1e-3) / 1e9,
             "e2e": {"value": job_value(contrib_step, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
-                    "what": "the CGLS iteration with x, r, p in pinned host memory: uploaded before and "
-                            "downloaded (with gamma) after every step", "finite": e2e_ok},
+                    "what": "the CGLS iteration with x, r, p in pinned host memory, uploaded and downloaded "
+                            "(with gamma) in every step: p before A and after the p update, x and r on a copy "
+                            "stream beside A (upload) and beside A^T (download)", "finite": e2e_ok},
             "gpu_launches": args.steps * launches_per_cg_step(ops.v1 - ops.v0, args.adjoint == "scatter"),
             "clocks": clocks,
             "roofline": roofline,

@@ -196,6 +196,38 @@ def test_adjoint_explicit_rays(env, orc, degree):
     assert rel_l2(c, cref) <= TOL, rel_l2(c, cref)
 
 
+def b_axis_rays(rng, dims, origin, axis, count):
+    """Rays whose smallest direction component is along `axis` (the b axis
+    the scatter adjoint keeps contiguous), with both signs of every
+    component, through the middle of the grid."""
+    w = rng.normal(size=(count, 3))
+    w[:, axis] *= 0.15
+    w *= np.where(rng.uniform(size=(count, 3)) < 0.5, -1.0, 1.0)
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    ctr = origin + (np.asarray(dims) - 1) / 2.0
+    s = ctr + rng.uniform(-5, 5, (count, 3))
+    return w, s
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2, -1])
+def test_adjoint_layout_per_b_axis(env, orc, axis):
+    """The scatter adjoint reduces each ray into the layout of c whose
+    contiguous axis is the ray's b axis (x, y or z fast, four shifted copies
+    each) and folds the layouts back: rays of each b axis alone, and all
+    three mixed (axis -1), on a grid whose sizes are not multiples of 4."""
+    rng = np.random.default_rng(2600 + axis)
+    dims = (19, 22, 13)
+    origin = I.centred_origin(dims)
+    axes = [axis] if axis >= 0 else [0, 1, 2]
+    parts = [b_axis_rays(rng, dims, origin, a, 120) for a in axes]
+    geo = I.RayGeometry(np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]))
+    y = rng.normal(size=geo.n_rays).astype(np.float32).astype(np.float64)
+    c = gpu_adjoint(env, dims, origin, geo, y, 3)
+    cref = orc.adjoint(3, dims, origin, y, oracle_geom(orc, geo))
+    assert np.isfinite(c).all()
+    assert rel_l2(c, cref) <= TOL, rel_l2(c, cref)
+
+
 @pytest.mark.parametrize("kind", ["parallel", "cone"])
 @pytest.mark.parametrize("degree", [1, 3])
 def test_adjoint_scatter_form(env, orc, kind, degree):
