@@ -22,8 +22,9 @@ struct spl_geometry {
     spl::ViewConst *vconst;       // parallel geometries: per-view constants in view_order order (host)
     spl::TableSet *table;         // footprint tables (SPL_FP_TABLE), built by spl_prepare, or NULL
     double *acc64;                // FP64 accumulator of the scatter adjoint's batches (nx*ny*nz), or NULL
-    float *lay[3];                // cone geometries: the scatter adjoint's copies of c in the y-fast [1] and
-                                  // z-fast [2] layouts (nx*ny*nz floats each), else NULL; [0] unused
+    float *lay[3];                // the scatter adjoint's targets: c in the x-fast [0], y-fast [1] and z-fast [2]
+                                  // layouts, four copies each shifted by 0..3 floats (4 * dev.lay_cs floats),
+                                  // or NULL (no rays; parallel geometries whose views are all flat)
 };
 
 namespace spl {
